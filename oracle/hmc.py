@@ -1,0 +1,108 @@
+"""Leapfrog integrator and HMC sampler, straight from Sec. 1.1 and Sec. 3.2.
+
+Test infrastructure only (see ``oracle/__init__.py``).  FP64 throughout.
+
+One leapfrog update (Eqs. hmc1-hmc3): a half step of eps/2 for the momentum
+along grad log K, a full step of eps for the coefficients, a second half step
+for the momentum at the new coefficients.  One proposal applies it L times
+(Sec. 1.1: L gradient evaluations per proposal, then one log-kernel
+evaluation for the accept test).  The gradient at the end of one update is
+the gradient at the start of the next, so it is computed once and reused:
+the values are identical to recomputing it.
+
+Metropolis test with momentum (Eq. accept, with the kinetic energy read as
+eta.eta / 2 for eta ~ N(0, I) and unit-mass dynamics):
+    H = -log K(beta) + eta.eta / 2,   accept  iff  log u < (H0 - H1) / T
+with T = 1 while sampling and T = T_t during annealed burn-in (Sec. 3.2:
+accept with probability alpha^(1/T_t), T_t = max(1, r T_{t-1})).
+A proposal whose H1 is not finite is rejected and counted as divergent.
+The accept test is strict; u comes from ``philox.accept_uniform`` and is
+never 0.
+"""
+import numpy as np
+
+from . import model, philox
+
+
+def leapfrog(X, y, beta, eta, eps, L, kind, scale, grad0=None):
+    """Apply L leapfrog updates (Eqs. hmc1-hmc3) to (beta, eta).
+
+    beta, eta: arrays of shape (K-1, p).  Returns (beta', eta', log K(beta'),
+    grad log K(beta')).
+    """
+    beta = np.array(beta, dtype=np.float64, copy=True)
+    eta = np.array(eta, dtype=np.float64, copy=True)
+    g = model.grad_log_kernel(X, y, beta, kind, scale) if grad0 is None else np.array(grad0, dtype=np.float64)
+    for _ in range(L):
+        eta = eta + (eps / 2.0) * g          # Eq. hmc1
+        beta = beta + eps * eta              # theta update between hmc1 and hmc3
+        g = model.grad_log_kernel(X, y, beta, kind, scale)
+        eta = eta + (eps / 2.0) * g          # Eq. hmc3
+    return beta, eta, model.log_kernel(X, y, beta, kind, scale), g
+
+
+def hamiltonian(logk, eta):
+    """H = -log K + eta.eta / 2 (Eq. accept, kinetic energy with the factor 1/2)."""
+    eta = np.asarray(eta, dtype=np.float64)
+    return -float(logk) + 0.5 * float(np.sum(eta * eta))
+
+
+def annealing_temperatures(burn_in, t0=1.0e3, r=0.9):
+    """T_t = max(1, r T_{t-1}) for burn-in iterations t = 1..burn_in, T_0 = t0 (Sec. 3.2)."""
+    temps = np.empty(burn_in)
+    t = float(t0)
+    for i in range(burn_in):
+        t = max(1.0, r * t)
+        temps[i] = t
+    return temps
+
+
+def sample(X, y, K, kind, scale, chains, L, eps, iters, seed,
+           beta0=None, iter0=0, temps=None):
+    """Run `chains` independent HMC chains for `iters` iterations.
+
+    eps   : scalar or per-iteration array of step sizes.
+    beta0 : (chains, K-1, p) start, zeros if None.
+    iter0 : RNG iteration index of the first iteration (counter word 1).
+    temps : per-iteration acceptance temperatures (None -> all 1).
+
+    Returns a dict with samples (iters, chains, K-1, p), accept (iters, chains),
+    dH = H1 - H0, logk (log K of the state kept), diverged, and the final
+    state (beta, grad, logk).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    p = X.shape[1]
+    km1 = K - 1
+    eps_t = np.broadcast_to(np.asarray(eps, dtype=np.float64), (iters,))
+    temp_t = np.ones(iters) if temps is None else np.asarray(temps, dtype=np.float64)
+    if beta0 is None:
+        beta = np.zeros((chains, km1, p))
+    else:
+        beta = np.array(beta0, dtype=np.float64).reshape(chains, km1, p).copy()
+    logk = np.array([model.log_kernel(X, y, beta[c], kind, scale) for c in range(chains)])
+    grad = np.stack([model.grad_log_kernel(X, y, beta[c], kind, scale) for c in range(chains)])
+
+    out_samples = np.empty((iters, chains, km1, p))
+    out_acc = np.zeros((iters, chains), dtype=bool)
+    out_dh = np.empty((iters, chains))
+    out_logk = np.empty((iters, chains))
+    out_div = np.zeros((iters, chains), dtype=bool)
+    for t in range(iters):
+        it = iter0 + t
+        for c in range(chains):
+            eta0 = philox.momentum_normals(seed, it, c, km1 * p).reshape(km1, p)
+            h0 = hamiltonian(logk[c], eta0)
+            b1, e1, lk1, g1 = leapfrog(X, y, beta[c], eta0, eps_t[t], L, kind, scale, grad0=grad[c])
+            h1 = hamiltonian(lk1, e1)
+            u = philox.accept_uniform(seed, it, c)
+            finite = np.isfinite(h1)
+            acc = bool(finite and np.log(u) < (h0 - h1) / temp_t[t])
+            out_div[t, c] = not finite
+            out_dh[t, c] = h1 - h0
+            if acc:
+                beta[c], grad[c], logk[c] = b1, g1, lk1
+            out_acc[t, c] = acc
+            out_samples[t, c] = beta[c]
+            out_logk[t, c] = logk[c]
+    return dict(samples=out_samples, accept=out_acc, dH=out_dh, logk=out_logk,
+                diverged=out_div, beta=beta, grad=grad, logk_final=logk)
