@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the HMC hot path on GB300: prints ONE JSON line.
+
+A step is one HMC iteration over the synthetic workload: momentum draw, L
+leapfrog updates (each one fused log-posterior + gradient pass over X, then
+the fixed-order split-K reduction and the leapfrog update), the Metropolis
+test and the keep/restore select -- all on the device, replayed from one
+CUDA graph.  ``value`` is gradient evaluations per second (chains * L per
+step) with X resident in HBM; ``e2e`` is the same metric through the C ABI
+with host buffers (the chain state uploaded and the sample read back every
+step); ``roofline`` is the fused kernel's X-stream bandwidth against the
+measured HBM copy bandwidth; ``cpu_baseline`` is the FP64 oracle on the
+host cores on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload highdim_fp32|plain_fp64|precision|batched|autodiff]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gradient evals/s"
+UNIT = "grad_evals/s"
+XBYTES = {"f64": 8, "f32": 4, "bf16": 2, "fp8": 1}
+KERNEL_SOURCES = ["paper_1402_4089_gb300/csrc/lpg_simt.cuh", "paper_1402_4089_gb300/csrc/device_common.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="highdim_fp32")
+    ap.add_argument("--xdtype", default=None, help="override the workload's X storage (f32, bf16, fp8, f64)")
+    ap.add_argument("--chains", type=int, default=None)
+    ap.add_argument("--L", type=int, default=None)
+    ap.add_argument("--tile", default=None, help="S,BM,NT,NSTAGE override")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_spec(args):
+    from paper_1402_4089_gb300 import synthetic
+    spec = dict(synthetic.WORKLOADS[args.workload])
+    if args.xdtype:
+        spec["xdtype"] = args.xdtype
+    if args.chains:
+        spec["chains"] = args.chains
+    if args.L:
+        spec["L"] = args.L
+    return spec
+
+
+def config_of(args, spec, xbytes_total):
+    return {
+        "workload": f"{args.workload}: n={spec['n']} p={spec['p']} K={spec['K']} chains={spec['chains']} "
+                    f"L={spec['L']} eps={spec['eps']} prior=N(0,{spec['prior'][1]}^2) X={spec['xdtype']}",
+        "n": spec["n"], "p": spec["p"], "K": spec["K"], "chains": spec["chains"], "L": spec["L"],
+        "eps": spec["eps"], "x_storage": spec["xdtype"],
+        "l2": f"inputs larger than L2: X is {xbytes_total / 1e6:.0f} MB > 129 MB L2, re-streamed every gradient"
+        if xbytes_total > 129e6 else "X smaller than L2 (129 MB): no flush between steps",
+        "step": "one HMC iteration: momentum draw, L fused gradient passes + split-K reduce/leapfrog, accept, select",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid, enabled=True):
+        self.uuid = uuid
+        self.enabled = enabled
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        if not self.enabled:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.uuid, "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.enabled or self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ measurements
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per fused launch from a committed ncu summary, if it was taken on the
+    current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("source_sha") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def cpu_baseline(X64, y, spec, seconds):
+    """The FP64 oracle as it stands: leapfrog steps (one gradient each) on the host."""
+    from oracle import hmc as ohmc
+    from oracle import model
+    kind, scale = spec["prior"]
+    K = spec["K"]
+    rng = np.random.default_rng(0)
+    beta = np.zeros((K - 1, X64.shape[1]))
+    eta = rng.standard_normal(beta.shape)
+    t0 = time.perf_counter()
+    g = model.grad_log_kernel(X64, y, beta, kind, scale)
+    t_one = time.perf_counter() - t0
+    steps = max(1, int(seconds / max(t_one, 1e-6)))
+    t0 = time.perf_counter()
+    ohmc.leapfrog(X64, y, beta, eta, spec["eps"], steps, kind, scale, grad0=g)
+    el = time.perf_counter() - t0
+    cores = os.cpu_count()
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            cores = int(os.environ[var])
+    return {"value": steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 leapfrog steps (one gradient each) of the full workload in {el:.1f} s, "
+                      f"numpy/BLAS on the host"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_1402_4089_gb300 import build, hmc, synthetic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+
+    spec = workload_spec(args)
+    X, y, btrue, _ = synthetic.make_workload(args.workload)
+    n, p, K = spec["n"], spec["p"], spec["K"]
+    chains, L, eps = spec["chains"], spec["L"], spec["eps"]
+    kind, scale = spec["prior"]
+    xdt = spec["xdtype"]
+    state = "f64" if xdt == "f64" else "f32"
+    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
+    stream = torch.cuda.Stream(device=dev)
+    h = hmc.create(X if xdt != "f64" else X.astype(np.float64), y, K, kind, scale, x_storage=xdt, state=state,
+                   max_chains=chains, stream=stream, tile=tile)
+    desc = h.describe()["problems"][0]
+    tdt = torch.float64 if state == "f64" else torch.float32
+    seed = 20140217
+    zeros = torch.zeros((chains, K - 1, p), dtype=tdt, device=dev)
+
+    # warm-up (includes graph capture)
+    h.sample(chains, L, eps, args.warmup, seed, beta0=zeros)
+    torch.cuda.synchronize()
+
+    # timed region: K iterations from the cached graph, fused-kernel events on
+    h.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    with Clocks(uuid, enabled=not args.no_clocks) as clk:
+        ev0.record(stream)
+        stats = h.sample(chains, L, eps, args.steps, seed)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    fused_ms, fused_n = h.fused_kernel_time()
+    h.set_timing(False)
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    grads = chains * L * args.steps
+    value = world * grads / elapsed
+    groups = -(-chains // desc["group_chains"])
+    launches_per_step = 1 + L * (groups + 1) + 1
+
+    # roofline of the fused pass (X streamed once per gradient)
+    xb = XBYTES[xdt]
+    c_launch = min(chains, desc["group_chains"]) * (K - 1)
+    alg_bytes = n * p * xb + 4 * n + 8 * p * c_launch
+    avg_launch_s = (fused_ms / 1e3) / max(fused_n, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
+            "kernel": f"lpg_kernel<{xdt},{c_launch}>", "avg_launch_us": round(avg_launch_s * 1e6, 2),
+            "launches_timed": fused_n, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.zeros((chains, K - 1, p), dtype=tdt).pin_memory()
+        hs = torch.empty((1, chains, K - 1, p), dtype=tdt).pin_memory()
+        hbn, hsn = hb.numpy(), hs.numpy()
+        h.sample(chains, L, eps, 1, seed, beta0=hbn, samples=hsn)   # warm (graph for host samples)
+        steps_e2e = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(steps_e2e):
+            h.sample(chains, L, eps, 1, seed + 1 + t, beta0=hbn, samples=hsn)
+            hbn[...] = hsn[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        el = e0.elapsed_time(e1) / 1e3
+        if dist:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nbytes = chains * (K - 1) * p * (8 if state == "f64" else 4)
+        e2e = {"value": round(world * chains * L * steps_e2e / el, 2), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes + chains * 40,
+               "note": "per step: upload the chain state (pinned host), one HMC iteration from it (plus the "
+                       "gradient at the uploaded state), read the sample back"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        X64 = X.astype(np.float64)
+        cpu = cpu_baseline(X64, y, spec, args.cpu_seconds)
+
+    acc = sum(s["accepted"] for s in stats) / max(1, sum(s["iterations"] for s in stats))
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": xdt, "data": "synthetic (seeded, shaped like the paper's "
+        "high-dimensional multinomial setting)", "config": config_of(args, spec, n * p * xb),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "xpass_gbs": round(achieved, 1), "accept_rate": round(acc, 4), "impl": "ours",
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args):
+    """The FP64 oracle, timed as it stands on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import hmc as ohmc
+    from oracle import model
+    from paper_1402_4089_gb300 import synthetic
+
+    spec = workload_spec(args)
+    X, y, _, _ = synthetic.make_workload(args.workload)
+    X64 = np.asarray(X, dtype=np.float64)
+    kind, scale = spec["prior"]
+    K = spec["K"]
+    rng = np.random.default_rng(0)
+    beta = np.zeros((K - 1, X64.shape[1]))
+    eta = rng.standard_normal(beta.shape)
+    t0 = time.perf_counter()
+    g = model.grad_log_kernel(X64, y, beta, kind, scale)
+    t_one = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)        # whole run within a few minutes
+    per_step = max(1, min(spec["L"], int(budget / max(t_one, 1e-6))))
+    for _ in range(args.warmup):
+        ohmc.leapfrog(X64, y, beta, eta, spec["eps"], per_step, kind, scale, grad0=g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        beta, eta, _, g = ohmc.leapfrog(X64, y, beta, eta, spec["eps"], per_step, kind, scale, grad0=g)
+    el = time.perf_counter() - t0
+    value = args.steps * per_step / el
+    cores = os.cpu_count()
+    sample = (f"each step: {per_step} FP64 leapfrog steps (one gradient each) of the full workload "
+              f"(a bounded sample of one {spec['L']}-step HMC iteration)")
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, spec, X64.nbytes // 2), "impl": "reference",
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

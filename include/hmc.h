@@ -1,0 +1,216 @@
+/*
+ * hmc.h -- C ABI of libhmc: Hamiltonian Monte Carlo for Bayesian multinomial
+ * (softmax) regression on one GB300 GPU (sm_103a).
+ *
+ * Method: Beam, Ghosh & Doyle, "Fast Hamiltonian Monte Carlo Using GPU
+ * Computing" (arXiv 1402.4089).  The library keeps X, the labels, the
+ * coefficients, momenta and gradients as persistent device state (Sec. 2.1,
+ * last paragraph) and evaluates, for every leapfrog step, the log-posterior
+ * kernel (Eq. logkernel / logkernelGPU) and its gradient (Eq. gradient /
+ * fullgrad) in one fused pass over X.
+ *
+ * Conventions shared by every call
+ *  - Every call returns hmc_status and never aborts the process.  A message
+ *    for the last failure of the calling thread is in hmc_last_error().
+ *  - Argument errors are detected before any device work: HMC_EINVAL.
+ *  - The caller keeps ownership of every pointer it passes; the library
+ *    copies what it keeps.  The handle owns all device memory it allocates.
+ *  - "host or device" pointers are classified with cudaPointerGetAttributes;
+ *    host buffers are copied through the handle's stream and the call
+ *    synchronises that stream before it returns.  Calls given only device
+ *    buffers are asynchronous on the handle's stream (opts.stream) unless
+ *    stated otherwise; results are valid after that stream is synchronised.
+ *  - A handle is not thread safe: one thread at a time per handle.
+ *  - Coefficient layout ("beta layout"): for `chains` chains of a problem
+ *    with p features and K classes, a dense array [chains][K-1][p] of the
+ *    handle's state type (double for HMC_F64, float for HMC_F32).  Row k of
+ *    chain c is beta_{k+1} of that chain; beta_K = 0 is implied (Sec. 2.1,
+ *    identifiability) and never stored.  For a batch handle the problems'
+ *    blocks follow one another in problem order.
+ *  - Every device-side wait is bounded (opts.spin_limit); when a bound runs
+ *    out the kernel stops, the call returns HMC_ETIMEOUT and the handle stays
+ *    usable.
+ */
+#ifndef HMC_H
+#define HMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hmc_ctx* hmc_handle;
+
+typedef enum {
+  HMC_OK = 0,
+  HMC_EINVAL = 1,        /* bad argument (detected before any launch)          */
+  HMC_ENOMEM = 2,        /* device or pinned-host allocation failed            */
+  HMC_ECUDA = 3,         /* a CUDA runtime call failed; see hmc_last_error()   */
+  HMC_ETIMEOUT = 4,      /* a bounded device wait ran out                      */
+  HMC_ENONFINITE = 5,    /* non-finite value in X or a label outside [0, K)    */
+  HMC_EUNSUPPORTED = 6   /* valid request this build or device cannot run      */
+} hmc_status;
+
+/* Prior on each free coefficient.  Sec. 2.1 uses the standard Cauchy
+ * (scale 1): log kernel -log(1 + b^2/s^2).  The Gaussian N(0, s^2) has log
+ * kernel -b^2/(2 s^2).  No normalising constants (Sec. 1.1). */
+typedef enum { HMC_PRIOR_GAUSSIAN = 0, HMC_PRIOR_CAUCHY = 1 } hmc_prior_kind;
+
+/* Element types.  X may be stored as HMC_F64, HMC_F32, HMC_BF16 (round to
+ * nearest even) or HMC_FP8E4M3 (per-column scale s_j = max_i|x_ij|/448,
+ * x_ij/s_j rounded to nearest even, saturating).  The chain state (beta,
+ * eta, grad) is HMC_F64 or HMC_F32. */
+typedef enum { HMC_F64 = 0, HMC_F32 = 1, HMC_BF16 = 2, HMC_FP8E4M3 = 3 } hmc_dtype;
+
+typedef struct {
+  hmc_dtype x_storage;    /* storage type of X on the device (default HMC_F32)   */
+  hmc_dtype state;        /* HMC_F64 or HMC_F32 (default HMC_F32)                */
+  int32_t max_chains;     /* largest `chains` any later call may pass (default 1) */
+  int32_t engine;         /* 0 auto, 1 CUDA-core fused kernel, 2 tensor-core fused kernel */
+  int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
+  void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
+  int32_t tile[4];        /* {cluster size, rows per tile, threads, stages}; 0 = autotuned */
+} hmc_opts;
+
+/* Per-chain counters of hmc_sample (host memory, one entry per chain). */
+typedef struct {
+  int64_t iterations;     /* proposals made                                   */
+  int64_t accepted;       /* proposals accepted (Eq. accept)                  */
+  int64_t diverged;       /* proposals with non-finite H (rejected)           */
+  double sum_abs_dH;      /* sum over proposals of |H1 - H0|                  */
+  double logpost;         /* log K of the chain's current state               */
+} hmc_chain_stats;
+
+/* Fill *opts with the defaults listed above. */
+void hmc_default_opts(hmc_opts* opts);
+
+/* Library version string (static storage). */
+const char* hmc_version(void);
+
+/* Message of the last failing call made by this thread ("" if none). */
+const char* hmc_last_error(void);
+
+/*
+ * hmc_create -- upload one regression problem (Sec. 2.1): X (n x p), labels
+ * y (n; y_i in [0, K) stands for the one-hot row of Y), K classes, prior.
+ *   X        host or device, row-major n x p of x_dtype (HMC_F64 or HMC_F32);
+ *            converted on the device to opts->x_storage and padded.
+ *   y        host or device int32[n].
+ *   n >= 0 (n = 0: prior only), p >= 1, 2 <= K <= 1024.
+ *   prior_scale > 0.
+ * Errors: HMC_EINVAL (shapes, dtypes, null pointers, scale), HMC_ENONFINITE
+ * (label out of range or non-finite X, checked on the device), HMC_ENOMEM.
+ * Synchronous.
+ */
+hmc_status hmc_create(const void* X, hmc_dtype x_dtype, const int32_t* y, int64_t n, int64_t p,
+                      int32_t K, hmc_prior_kind prior, double prior_scale, const hmc_opts* opts,
+                      hmc_handle* out);
+
+/*
+ * hmc_create_batch -- several independent regression problems in one handle
+ * (each with its own n_b, p_b, K_b; same prior and options).  The fused pass
+ * runs over all problems in one launch; the beta layout concatenates the
+ * problems.  Arguments are arrays of length nprob with the meaning of
+ * hmc_create's.  Synchronous.
+ */
+hmc_status hmc_create_batch(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
+                            const int32_t* const* y, const int64_t* n, const int64_t* p,
+                            const int32_t* K, hmc_prior_kind prior, double prior_scale,
+                            const hmc_opts* opts, hmc_handle* out);
+
+/* Release every resource of the handle (NULL is accepted).  Synchronous. */
+hmc_status hmc_destroy(hmc_handle h);
+
+/* Total free coefficients of one chain (sum over problems of (K_b-1) p_b). */
+int64_t hmc_chain_size(hmc_handle h);
+
+/*
+ * hmc_logpost_grad -- log K (Eq. logkernel) and its gradient (Eq. gradient,
+ * prior term with the sign of the derivative of the prior's log kernel) at
+ * `chains` coefficient states.
+ *   beta     host or device, beta layout (state type).
+ *   logpost  host or device double[nprob * chains] (index b * chains + c
+ *            for problem b, chain c), or NULL.
+ *   grad     host or device, beta layout, or NULL.
+ * 1 <= chains <= opts.max_chains.
+ */
+hmc_status hmc_logpost_grad(hmc_handle h, const void* beta, int32_t chains, double* logpost,
+                            void* grad);
+
+/*
+ * hmc_leapfrog -- L leapfrog updates (Eqs. hmc1-hmc3) in place, no accept
+ * test.  beta, eta: host or device, beta layout.  grad: in, the gradient at
+ * beta, or NULL (then computed first); out, the gradient at the new beta.
+ * logpost: out, log K at the new beta (as in hmc_logpost_grad), or NULL.
+ * eps is the step size, L >= 0.
+ */
+hmc_status hmc_leapfrog(hmc_handle h, void* beta, void* eta, void* grad, double* logpost,
+                        int32_t chains, int32_t L, double eps);
+
+/*
+ * hmc_sample -- `iters` HMC iterations of `chains` independent chains
+ * (Sec. 1.1): draw eta ~ N(0, I) (Philox4x64-10, key (seed, 0), counter
+ * (block, iteration, chain, 0)), L leapfrog updates, accept iff
+ * log u < (H0 - H1) / T with H = -log K + eta.eta / 2 and T = 1 (Eq. accept;
+ * u from counter (0, iteration, chain, 1)), else keep the old state.  A
+ * non-finite H1 is rejected and counted as divergent.
+ *   beta0    host or device beta layout: (re)start every chain there and
+ *            reset the iteration counter to 0; NULL: continue from the
+ *            handle's chain state (zeros on first use), counter continuing.
+ *   samples  host or device [iters/thin][chains][...beta layout...] of the
+ *            state type (the state after iterations thin-1, 2 thin-1, ...),
+ *            or NULL.
+ *   thin >= 1.  stats: host [nprob * chains] (index b * chains + c, filled
+ *            on return) or NULL.
+ * The chain state is the handle's; it persists across calls.  Synchronous.
+ */
+hmc_status hmc_sample(hmc_handle h, int32_t chains, int32_t L, double eps, int64_t iters,
+                      uint64_t seed, const void* beta0, void* samples, int32_t thin,
+                      hmc_chain_stats* stats);
+
+/*
+ * hmc_sample_tempered -- hmc_sample with a per-iteration acceptance
+ * temperature (annealed burn-in of Sec. 3.2: accept with probability
+ * alpha^(1/T_t)).  temps: host double[iters], every T_t >= 1; NULL means all 1.
+ */
+hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double eps, int64_t iters,
+                               uint64_t seed, const void* beta0, void* samples, int32_t thin,
+                               hmc_chain_stats* stats, const double* temps);
+
+/*
+ * hmc_get_state -- copy the handle's chain state: beta and grad (beta layout,
+ * host or device, or NULL), logpost (double[nprob * chains], host or device,
+ * or NULL) and the next iteration index (host, or NULL).  Synchronous.
+ */
+hmc_status hmc_get_state(hmc_handle h, int32_t chains, void* beta, void* grad, double* logpost,
+                         int64_t* next_iteration);
+
+/*
+ * hmc_get_x -- copy the device-resident X of problem b as stored (after
+ * conversion): row-major n x p elements of opts.x_storage (8, 4, 2 or 1
+ * bytes each), unpadded, into host or device memory `dst`; for HMC_FP8E4M3
+ * also the p float column scales into `scales` (host or device, or NULL).
+ * Synchronous.
+ */
+hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales);
+
+/*
+ * hmc_describe -- JSON text (static per handle) describing the chosen
+ * engine, tile configuration, padded sizes and device buffers.
+ */
+const char* hmc_describe(hmc_handle h);
+
+/*
+ * hmc_last_launch_stats -- device time of the fused kernel over the most
+ * recent call, measured with CUDA events on the handle's stream when
+ * enabled with hmc_set_timing(h, 1): total milliseconds and launches.
+ */
+hmc_status hmc_set_timing(hmc_handle h, int32_t enable);
+hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMC_H */

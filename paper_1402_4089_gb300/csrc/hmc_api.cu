@@ -1,0 +1,907 @@
+// C ABI of libhmc (include/hmc.h): handle life cycle, uploads, and the
+// orchestration of the fused log-posterior/gradient pass, the split-K
+// reduction + leapfrog update, and the momentum / accept / select kernels.
+// One HMC iteration (Sec. 1.1: draw eta, L leapfrog updates, accept test) is
+// captured once as a CUDA graph and replayed `iters` times; the iteration
+// index the generator needs lives in device memory, so every replay is the
+// same graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+using namespace hmc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hmc_status fail(hmc_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define HMC_CUDA(call)                                                                                  \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) {                                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? HMC_ENOMEM : HMC_ECUDA,                             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                   \
+    }                                                                                                   \
+  } while (0)
+
+#define HMC_TRY(expr)            \
+  do {                           \
+    hmc_status s_ = (expr);      \
+    if (s_ != HMC_OK) return s_; \
+  } while (0)
+
+int dtype_bytes(int t) { return t == HMC_F64 ? 8 : t == HMC_F32 ? 4 : t == HMC_BF16 ? 2 : 1; }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct StateSet {
+  void* beta = nullptr;
+  void* eta = nullptr;
+  void* grad = nullptr;
+  void* beta0 = nullptr;
+  void* grad0 = nullptr;
+};
+
+struct Problem {
+  int64_t n = 0;
+  int32_t p = 0, p_pad = 0, K = 0, Km1 = 0;
+  void* X = nullptr;
+  int32_t* y = nullptr;
+  float* xscale = nullptr;
+  // fused-pass configuration
+  int S = 1, BM = 32, NT = 32, NSTAGE = 2, PC = 32, nclusters = 1, ct_launch = 1, group_chains = 1;
+  size_t smem = 0;
+  int64_t ntiles = 0;
+  void* gpart = nullptr;
+  double* lpart = nullptr;
+  StateSet cs, us;  // chain state (hmc_sample) and user-call scratch
+  double* logk = nullptr;  // [2][max_chains]: chain state, user scratch
+  double* logk0 = nullptr;
+  double* h0 = nullptr;
+  double* scal = nullptr;  // [max_chains][nblk][2]
+  unsigned int* tickets = nullptr;  // [max_chains] + 1 (select)
+  int* accept = nullptr;
+  void* stats = nullptr;
+  int64_t* iter = nullptr;  // [3]: global iteration, local iteration, generator seed
+  int nblk = 1;
+  int64_t state_elems = 0;  // max_chains * Km1 * p_pad
+};
+
+struct FusedTimer {
+  std::vector<cudaEvent_t> ev;  // pairs
+  size_t used = 0;
+};
+
+}  // namespace
+
+struct hmc_ctx {
+  int xt = HMC_F32, st = HMC_F32, prior_kind = 0;
+  double prior_scale = 1.0;
+  int max_chains = 1, engine = 1;
+  long long spin_limit = 1ll << 22;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture / replay
+  std::vector<Problem> probs;
+  int* err_d = nullptr;
+  int chains_init = 0;  // chains whose state has been initialised
+  double* temps_d = nullptr;
+  int64_t temps_cap = 0;
+  void* staging[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t staging_cap[4] = {0, 0, 0, 0};
+  bool timing = false;
+  double timing_ms = 0.0;
+  int64_t timing_launches = 0;
+  FusedTimer timer;
+  std::string desc;
+  int64_t chain_size = 0;
+  int tile[4] = {0, 0, 0, 0};
+  bool inject_timeout = false;  // HMC_FAULT=timeout at creation: first fused launch times out
+  // Cached graph of one HMC iteration and the parameters baked into it.
+  cudaGraphExec_t gexec = nullptr;
+  int g_chains = 0, g_L = 0, g_thin = 0;
+  double g_eps = 0.0;
+  const void* g_samples = nullptr;
+  bool g_temps = false, g_timing = false;
+  const double* g_temps_ptr = nullptr;
+  cudaStream_t g_stream = nullptr;
+  size_t g_pairs = 0;
+  std::vector<cudaEvent_t> g_events;  // timing events baked into the cached graph
+};
+
+namespace {
+
+size_t state_bytes(const hmc_ctx* h) { return size_t(dtype_bytes(h->st)); }
+
+hmc_status grow_staging(hmc_ctx* h, int slot, size_t bytes, void** out) {
+  if (h->staging_cap[slot] < bytes) {
+    if (h->staging[slot]) cudaFree(h->staging[slot]);
+    h->staging[slot] = nullptr;
+    h->staging_cap[slot] = 0;
+    HMC_CUDA(cudaMalloc(&h->staging[slot], bytes));
+    h->staging_cap[slot] = bytes;
+  }
+  *out = h->staging[slot];
+  return HMC_OK;
+}
+
+// Device view of a user input buffer (copied to staging when on the host).
+hmc_status dev_in(hmc_ctx* h, int slot, const void* user, size_t bytes, const void** dev) {
+  if (!user || is_device_ptr(user)) {
+    *dev = user;
+    return HMC_OK;
+  }
+  void* d = nullptr;
+  HMC_TRY(grow_staging(h, slot, bytes, &d));
+  HMC_CUDA(cudaMemcpyAsync(d, user, bytes, cudaMemcpyHostToDevice, h->stream));
+  *dev = d;
+  return HMC_OK;
+}
+
+// Device destination for a user output buffer; *host says a copy-back is needed.
+hmc_status dev_out(hmc_ctx* h, int slot, void* user, size_t bytes, void** dev, bool* host) {
+  *host = false;
+  if (!user || is_device_ptr(user)) {
+    *dev = user;
+    return HMC_OK;
+  }
+  *host = true;
+  return grow_staging(h, slot, bytes, dev);
+}
+
+hmc_status check_device_error(hmc_ctx* h) {
+  int e = 0;
+  HMC_CUDA(cudaMemcpyAsync(&e, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  if (e) {
+    HMC_CUDA(cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream));
+    HMC_CUDA(cudaStreamSynchronize(h->stream));
+    if (e & (ERR_TIMEOUT_STAGE | ERR_TIMEOUT_EXCHANGE | ERR_TIMEOUT_SLOT | ERR_TIMEOUT_MMA))
+      return fail(HMC_ETIMEOUT, "a bounded device wait ran out (error bits " + std::to_string(e) + ")");
+    if (e & (ERR_BAD_LABEL | ERR_NONFINITE_X))
+      return fail(HMC_ENONFINITE, "label outside [0, K) or non-finite X (error bits " + std::to_string(e) + ")");
+    return fail(HMC_ECUDA, "device error bits " + std::to_string(e));
+  }
+  return HMC_OK;
+}
+
+// ------------------------------------------------------------- configuration
+struct TileChoice {
+  int S, BM, NT, NSTAGE, PC;
+  size_t smem;
+};
+
+int round_up(int64_t v, int64_t m) { return int((v + m - 1) / m * m); }
+
+hmc_status choose_simt(hmc_ctx* h, Problem& P, int ct_cols, TileChoice* out) {
+  int dev = 0, smem_max = 0;
+  HMC_CUDA(cudaGetDevice(&dev));
+  HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int Ss[] = {1, 2, 4, 8, 16};
+  const int BMs[] = {32, 16, 8};
+  const int NSs[] = {3, 2};
+  bool found = false;
+  TileChoice best{};
+  double best_score = -1.0;
+  for (int S : Ss) {
+    if (h->tile[0] && S != h->tile[0]) continue;
+    int PC = round_up((P.p + S - 1) / S, 32);
+    if (PC < 32) PC = 32;
+    int NT = round_up(std::max(32, PC / 4), 32);
+    if (h->tile[2]) NT = std::max(NT, round_up(h->tile[2], 32));
+    if (NT > kSimtMaxThreads || PC > 4 * NT) continue;
+    for (int BM : BMs) {
+      if (h->tile[1] && BM != h->tile[1]) continue;
+      for (int NS : NSs) {
+        if (h->tile[3] && NS != h->tile[3]) continue;
+        const size_t smem = simt_smem_bytes(h->xt, h->st, ct_cols, PC, BM, S, NT, NS);
+        if (smem > size_t(smem_max)) continue;
+        // Prefer few CTAs per cluster, then tall tiles, then deep pipelines.
+        const double score = 1000.0 / S + BM + NS;
+        if (score > best_score) {
+          best_score = score;
+          best = TileChoice{S, BM, NT, NS, PC, smem};
+          found = true;
+        }
+      }
+    }
+  }
+  if (!found) return fail(HMC_EUNSUPPORTED, "no CUDA-core tile configuration fits this problem (p too large for the cluster sizes available)");
+  *out = best;
+  return HMC_OK;
+}
+
+hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, const int32_t* y) {
+  const int xb = dtype_bytes(h->xt);
+  const int maxct = simt_max_ct(h->xt);
+  if (P.Km1 > maxct)
+    return fail(HMC_EUNSUPPORTED, "K-1 = " + std::to_string(P.Km1) + " exceeds the CUDA-core kernel's class bound " +
+                                      std::to_string(maxct));
+  P.group_chains = std::max(1, std::min(h->max_chains, maxct / P.Km1));
+  P.ct_launch = P.group_chains * P.Km1;
+  TileChoice tc{};
+  HMC_TRY(choose_simt(h, P, P.ct_launch, &tc));
+  P.S = tc.S;
+  P.BM = tc.BM;
+  P.NT = tc.NT;
+  P.NSTAGE = tc.NSTAGE;
+  P.PC = tc.PC;
+  P.smem = tc.smem;
+  P.p_pad = P.S * P.PC;
+  P.ntiles = (P.n + P.BM - 1) / P.BM;
+  HMC_CUDA(simt_prepare(h->xt, h->st, P.ct_launch, P.smem, P.S));
+  int maxclu = 0;
+  HMC_CUDA(simt_max_active_clusters(h->xt, h->st, P.ct_launch, P.smem, P.S, P.NT, &maxclu));
+  if (maxclu < 1) return fail(HMC_EUNSUPPORTED, "the fused kernel cannot be resident with this tile configuration");
+  P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>(maxclu, P.ntiles)));
+
+  // X: convert on the device into the storage type, zero-padded columns.
+  const size_t in_bytes = size_t(P.n) * P.p * (x_dtype == HMC_F64 ? 8 : 4);
+  const void* Xd = X;
+  void* tmp = nullptr;
+  if (P.n > 0 && !is_device_ptr(X)) {
+    HMC_CUDA(cudaMalloc(&tmp, in_bytes));
+    HMC_CUDA(cudaMemcpyAsync(tmp, X, in_bytes, cudaMemcpyHostToDevice, h->stream));
+    Xd = tmp;
+  }
+  HMC_CUDA(cudaMalloc(&P.X, std::max<size_t>(16, size_t(P.n) * P.p_pad * xb)));
+  if (h->xt == HMC_FP8E4M3) {
+    HMC_CUDA(cudaMalloc(&P.xscale, size_t(P.p_pad) * sizeof(float)));
+    HMC_CUDA(launch_fp8_scales(x_dtype, Xd, P.xscale, P.n, P.p, P.p_pad, h->stream));
+  }
+  if (P.n > 0) HMC_CUDA(launch_convert_x(x_dtype, Xd, h->xt, P.X, P.xscale, P.n, P.p, P.p_pad, h->err_d, h->stream));
+  HMC_CUDA(cudaMalloc(&P.y, std::max<size_t>(16, size_t(P.n) * sizeof(int32_t))));
+  if (P.n > 0)
+    HMC_CUDA(cudaMemcpyAsync(P.y, y, size_t(P.n) * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  HMC_CUDA(launch_check_labels(P.y, P.n, P.K, h->err_d, h->stream));
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  if (tmp) cudaFree(tmp);
+  HMC_TRY(check_device_error(h));
+
+  // Partials, chain state and scalars.
+  const size_t sb = state_bytes(h);
+  P.state_elems = int64_t(h->max_chains) * P.Km1 * P.p_pad;
+  HMC_CUDA(cudaMalloc(&P.gpart, size_t(P.nclusters) * P.state_elems * sb));
+  HMC_CUDA(cudaMalloc(&P.lpart, size_t(P.nclusters) * h->max_chains * sizeof(double)));
+  for (StateSet* s : {&P.cs, &P.us}) {
+    for (void** q : {&s->beta, &s->eta, &s->grad, &s->beta0, &s->grad0}) {
+      HMC_CUDA(cudaMalloc(q, size_t(P.state_elems) * sb));
+      HMC_CUDA(cudaMemsetAsync(*q, 0, size_t(P.state_elems) * sb, h->stream));
+    }
+  }
+  P.nblk = update_blocks_per_chain(int64_t(P.Km1) * P.p_pad);
+  HMC_CUDA(cudaMalloc(&P.logk, 2 * h->max_chains * sizeof(double)));
+  HMC_CUDA(cudaMalloc(&P.logk0, h->max_chains * sizeof(double)));
+  HMC_CUDA(cudaMalloc(&P.h0, h->max_chains * sizeof(double)));
+  HMC_CUDA(cudaMalloc(&P.scal, size_t(h->max_chains) * P.nblk * 2 * sizeof(double)));
+  HMC_CUDA(cudaMalloc(&P.tickets, (h->max_chains + 1) * sizeof(unsigned int)));
+  HMC_CUDA(cudaMemsetAsync(P.tickets, 0, (h->max_chains + 1) * sizeof(unsigned int), h->stream));
+  HMC_CUDA(cudaMalloc(&P.accept, h->max_chains * sizeof(int)));
+  HMC_CUDA(cudaMalloc(&P.stats, h->max_chains * sizeof(hmc_chain_stats)));
+  HMC_CUDA(cudaMalloc(&P.iter, 3 * sizeof(int64_t)));
+  HMC_CUDA(cudaMemsetAsync(P.iter, 0, 3 * sizeof(int64_t), h->stream));
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  return HMC_OK;
+}
+
+void free_problem(Problem& P) {
+  void* ptrs[] = {P.X, P.y, P.xscale, P.gpart, P.lpart, P.cs.beta, P.cs.eta, P.cs.grad, P.cs.beta0, P.cs.grad0,
+                  P.us.beta, P.us.eta, P.us.grad, P.us.beta0, P.us.grad0, P.logk, P.logk0, P.h0, P.scal,
+                  P.tickets, P.accept, P.stats, P.iter};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+// ----------------------------------------------------------------- launches
+hmc_status timer_pair(hmc_ctx* h, cudaEvent_t* a, cudaEvent_t* b) {
+  FusedTimer& T = h->timer;
+  while (T.ev.size() < 2 * (T.used + 1)) {
+    cudaEvent_t e;
+    HMC_CUDA(cudaEventCreate(&e));
+    T.ev.push_back(e);
+  }
+  *a = T.ev[2 * T.used];
+  *b = T.ev[2 * T.used + 1];
+  T.used += 1;
+  return HMC_OK;
+}
+
+// Harvest (synchronously) the fused-kernel durations recorded since the last harvest.
+hmc_status timer_harvest(hmc_ctx* h) {
+  FusedTimer& T = h->timer;
+  if (T.used == 0) return HMC_OK;
+  HMC_CUDA(cudaEventSynchronize(T.ev[2 * T.used - 1]));
+  for (size_t i = 0; i < T.used; ++i) {
+    float ms = 0.f;
+    HMC_CUDA(cudaEventElapsedTime(&ms, T.ev[2 * i], T.ev[2 * i + 1]));
+    h->timing_ms += ms;
+    h->timing_launches += 1;
+  }
+  T.used = 0;
+  return HMC_OK;
+}
+
+hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t stream) {
+  if (P.n == 0) return HMC_OK;
+  const size_t sb = state_bytes(h);
+  for (int c0 = 0; c0 < chains; c0 += P.group_chains) {
+    const int c1 = std::min(chains, c0 + P.group_chains);
+    LpgArgs a{};
+    a.X = P.X;
+    a.y = P.y;
+    a.xscale = P.xscale;
+    a.beta = static_cast<const char*>(S.beta) + size_t(c0) * P.Km1 * P.p_pad * sb;
+    a.gpart = static_cast<char*>(P.gpart) + size_t(c0) * P.Km1 * P.p_pad * sb;
+    a.gpart_cstride = P.state_elems;
+    a.lpart = P.lpart + c0;
+    a.lpart_cstride = h->max_chains;
+    a.err = h->err_d;
+    a.n = P.n;
+    a.p_pad = P.p_pad;
+    a.PC = P.PC;
+    a.C = (c1 - c0) * P.Km1;
+    a.Km1 = P.Km1;
+    a.chains = c1 - c0;
+    a.BM = P.BM;
+    a.S = P.S;
+    a.NT = P.NT;
+    a.NSTAGE = P.NSTAGE;
+    a.nclusters = P.nclusters;
+    a.ntiles = P.ntiles;
+    a.spin_limit = h->spin_limit;
+    a.inject_timeout = h->inject_timeout ? 1 : 0;
+    h->inject_timeout = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing) {
+      HMC_TRY(timer_pair(h, &e0, &e1));
+      HMC_CUDA(cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal));
+    }
+    HMC_CUDA(simt_launch(h->xt, h->st, a, P.smem, stream));
+    if (h->timing) HMC_CUDA(cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal));
+  }
+  return HMC_OK;
+}
+
+UpdateArgs make_update(hmc_ctx* h, Problem& P, StateSet& S, int which_logk, int chains, double eps, int b) {
+  UpdateArgs u{};
+  u.beta = S.beta;
+  u.eta = S.eta;
+  u.grad = S.grad;
+  u.beta0 = S.beta0;
+  u.grad0 = S.grad0;
+  u.gpart = P.gpart;
+  u.gpart_cstride = P.state_elems;
+  u.nparts = P.n > 0 ? P.nclusters : 0;
+  u.lpart = P.lpart;
+  u.lpart_cstride = h->max_chains;
+  u.logk = P.logk + which_logk * h->max_chains;
+  u.logk0 = P.logk0;
+  u.h0 = P.h0;
+  u.scal = P.scal;
+  u.tickets = P.tickets;
+  u.accept = P.accept;
+  u.stats = P.stats;
+  u.temps = nullptr;
+  u.iter = P.iter;
+  u.local_iter = P.iter + 1;
+  u.samples = nullptr;
+  u.thin = 1;
+  u.sample_slot_stride = 0;
+  u.chains_word_hi = b;
+  u.err = h->err_d;
+  u.p = P.p;
+  u.p_pad = P.p_pad;
+  u.Km1 = P.Km1;
+  u.chains = chains;
+  u.nblk = P.nblk;
+  u.prior_kind = h->prior_kind;
+  u.prior_scale = h->prior_scale;
+  u.eps = eps;
+  u.seed = reinterpret_cast<const uint64_t*>(P.iter + 2);
+  return u;
+}
+
+hmc_status validate_opts(const hmc_opts* o) {
+  if (!o) return HMC_OK;
+  if (o->x_storage < HMC_F64 || o->x_storage > HMC_FP8E4M3) return fail(HMC_EINVAL, "opts.x_storage out of range");
+  if (o->state != HMC_F64 && o->state != HMC_F32) return fail(HMC_EINVAL, "opts.state must be HMC_F64 or HMC_F32");
+  if ((o->x_storage == HMC_F64) != (o->state == HMC_F64))
+    return fail(HMC_EINVAL, "HMC_F64 storage of X goes with HMC_F64 state, and only with it");
+  if (o->max_chains < 1 || o->max_chains > 4096) return fail(HMC_EINVAL, "opts.max_chains must be in [1, 4096]");
+  if (o->engine < 0 || o->engine > 2) return fail(HMC_EINVAL, "opts.engine must be 0, 1 or 2");
+  if (o->spin_limit < 0) return fail(HMC_EINVAL, "opts.spin_limit must be >= 0");
+  const int* t = o->tile;
+  if (t[0] != 0 && t[0] != 1 && t[0] != 2 && t[0] != 4 && t[0] != 8 && t[0] != 16)
+    return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be 0, 1, 2, 4, 8 or 16");
+  if (t[1] != 0 && t[1] != 8 && t[1] != 16 && t[1] != 32)
+    return fail(HMC_EINVAL, "opts.tile[1] (rows per tile) must be 0, 8, 16 or 32");
+  if (t[2] < 0 || t[2] > 384) return fail(HMC_EINVAL, "opts.tile[2] (threads) must be in [0, 384]");
+  if (t[3] != 0 && t[3] != 2 && t[3] != 3) return fail(HMC_EINVAL, "opts.tile[3] (stages) must be 0, 2 or 3");
+  return HMC_OK;
+}
+
+void build_description(hmc_ctx* h) {
+  std::string s = "{\"engine\": \"simt\", \"x_storage\": " + std::to_string(h->xt) +
+                  ", \"state\": " + std::to_string(h->st) + ", \"max_chains\": " + std::to_string(h->max_chains) +
+                  ", \"problems\": [";
+  for (size_t b = 0; b < h->probs.size(); ++b) {
+    const Problem& P = h->probs[b];
+    char buf[512];
+    std::snprintf(buf, sizeof(buf),
+                  "%s{\"n\": %lld, \"p\": %d, \"K\": %d, \"p_pad\": %d, \"S\": %d, \"BM\": %d, \"NT\": %d, "
+                  "\"NSTAGE\": %d, \"PC\": %d, \"nclusters\": %d, \"smem\": %zu, \"group_chains\": %d, \"ct\": %d}",
+                  b ? ", " : "", (long long)P.n, P.p, P.K, P.p_pad, P.S, P.BM, P.NT, P.NSTAGE, P.PC, P.nclusters,
+                  P.smem, P.group_chains, P.ct_launch);
+    s += buf;
+  }
+  s += "]}";
+  h->desc = s;
+}
+
+hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype, const int32_t* const* y,
+                         const int64_t* n, const int64_t* p, const int32_t* K, hmc_prior_kind prior,
+                         double prior_scale, const hmc_opts* opts, hmc_handle* out) {
+  g_last_error.clear();
+  if (!out) return fail(HMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || nprob > 4096) return fail(HMC_EINVAL, "nprob must be in [1, 4096]");
+  if (!X || !y || !n || !p || !K) return fail(HMC_EINVAL, "NULL array argument");
+  if (x_dtype != HMC_F64 && x_dtype != HMC_F32) return fail(HMC_EINVAL, "x_dtype must be HMC_F64 or HMC_F32");
+  if (prior != HMC_PRIOR_GAUSSIAN && prior != HMC_PRIOR_CAUCHY) return fail(HMC_EINVAL, "unknown prior kind");
+  if (!(prior_scale > 0.0) || !std::isfinite(prior_scale)) return fail(HMC_EINVAL, "prior_scale must be finite and > 0");
+  hmc_opts o;
+  hmc_default_opts(&o);
+  if (opts) o = *opts;
+  HMC_TRY(validate_opts(&o));
+  if (o.engine == 2) return fail(HMC_EUNSUPPORTED, "tensor-core engine not available for this configuration");
+  for (int b = 0; b < nprob; ++b) {
+    if (n[b] < 0 || n[b] > (int64_t(1) << 40)) return fail(HMC_EINVAL, "n out of range");
+    if (p[b] < 1 || p[b] > (int64_t(1) << 24)) return fail(HMC_EINVAL, "p out of range");
+    if (K[b] < 2 || K[b] > 1024) return fail(HMC_EINVAL, "K must be in [2, 1024]");
+    if (n[b] > 0 && (!X[b] || !y[b])) return fail(HMC_EINVAL, "NULL X or y with n > 0");
+  }
+  hmc_ctx* h = new hmc_ctx();
+  h->xt = o.x_storage;
+  h->st = o.state;
+  h->prior_kind = prior;
+  h->prior_scale = prior_scale;
+  h->max_chains = o.max_chains;
+  h->engine = 1;
+  h->spin_limit = o.spin_limit > 0 ? o.spin_limit : (1ll << 22);
+  h->stream = static_cast<cudaStream_t>(o.stream);
+  for (int i = 0; i < 4; ++i) h->tile[i] = o.tile[i];
+  if (const char* f = std::getenv("HMC_FAULT")) h->inject_timeout = std::strcmp(f, "timeout") == 0;
+  auto cleanup = [&](hmc_status s) {
+    hmc_destroy(h);
+    return s;
+  };
+  if (cudaMalloc(&h->err_d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(HMC_ENOMEM, "cudaMalloc of the error word failed");
+  }
+  if (cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream) != cudaSuccess) return cleanup(fail(HMC_ECUDA, "memset"));
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cleanup(fail(HMC_ECUDA, "cudaStreamCreateWithFlags failed"));
+  h->probs.resize(nprob);
+  for (int b = 0; b < nprob; ++b) {
+    Problem& P = h->probs[b];
+    P.n = n[b];
+    P.p = int32_t(p[b]);
+    P.K = K[b];
+    P.Km1 = K[b] - 1;
+    hmc_status s = setup_problem(h, P, X[b], x_dtype, y[b]);
+    if (s != HMC_OK) return cleanup(s);
+    h->chain_size += int64_t(P.Km1) * P.p;
+  }
+  build_description(h);
+  *out = h;
+  return HMC_OK;
+}
+
+int64_t block_offset(const hmc_ctx* h, int b, int chains) {
+  int64_t off = 0;
+  for (int q = 0; q < b; ++q) off += int64_t(chains) * h->probs[q].Km1 * h->probs[q].p;
+  return off;
+}
+
+// Pack a user beta-layout buffer (device) into the padded state of each problem.
+hmc_status pack_all(hmc_ctx* h, const void* user_dev, int chains, bool chain_state, void* StateSet::*field) {
+  const size_t sb = state_bytes(h);
+  for (size_t b = 0; b < h->probs.size(); ++b) {
+    Problem& P = h->probs[b];
+    StateSet& S = chain_state ? P.cs : P.us;
+    const char* src = static_cast<const char*>(user_dev) + size_t(block_offset(h, int(b), chains)) * sb;
+    HMC_CUDA(launch_pack(h->st, src, S.*field, int64_t(chains) * P.Km1, P.p, P.p_pad, h->stream));
+  }
+  return HMC_OK;
+}
+
+hmc_status unpack_all(hmc_ctx* h, void* user_dev, int chains, bool chain_state, void* StateSet::*field) {
+  const size_t sb = state_bytes(h);
+  for (size_t b = 0; b < h->probs.size(); ++b) {
+    Problem& P = h->probs[b];
+    StateSet& S = chain_state ? P.cs : P.us;
+    char* dst = static_cast<char*>(user_dev) + size_t(block_offset(h, int(b), chains)) * sb;
+    HMC_CUDA(launch_unpack(h->st, S.*field, dst, int64_t(chains) * P.Km1, P.p, P.p_pad, h->stream));
+  }
+  return HMC_OK;
+}
+
+hmc_status copy_logk(hmc_ctx* h, double* user_dev, int chains, int which) {
+  for (size_t b = 0; b < h->probs.size(); ++b)
+    HMC_CUDA(cudaMemcpyAsync(user_dev + b * chains, h->probs[b].logk + which * h->max_chains,
+                             size_t(chains) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return HMC_OK;
+}
+
+hmc_status check_chains(hmc_ctx* h, int chains) {
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  if (chains < 1 || chains > h->max_chains)
+    return fail(HMC_EINVAL, "chains must be in [1, max_chains=" + std::to_string(h->max_chains) + "]");
+  return HMC_OK;
+}
+
+// log K and gradient at the state in `S` for every problem.
+hmc_status eval_state(hmc_ctx* h, bool chain_state, int chains) {
+  for (size_t b = 0; b < h->probs.size(); ++b) {
+    Problem& P = h->probs[b];
+    StateSet& S = chain_state ? P.cs : P.us;
+    HMC_TRY(run_lpg(h, P, S, chains, h->stream));
+    UpdateArgs u = make_update(h, P, S, chain_state ? 0 : 1, chains, 0.0, int(b));
+    HMC_CUDA(launch_reduce_update(h->st, u, UPD_SCALARS, h->stream));
+  }
+  return HMC_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void hmc_default_opts(hmc_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->x_storage = HMC_F32;
+  o->state = HMC_F32;
+  o->max_chains = 1;
+  o->engine = 0;
+  o->spin_limit = 0;
+  o->stream = nullptr;
+}
+
+const char* hmc_version(void) { return "libhmc 0.1 (sm_103a)"; }
+
+const char* hmc_last_error(void) { return g_last_error.c_str(); }
+
+hmc_status hmc_create(const void* X, hmc_dtype x_dtype, const int32_t* y, int64_t n, int64_t p, int32_t K,
+                      hmc_prior_kind prior, double prior_scale, const hmc_opts* opts, hmc_handle* out) {
+  const void* Xs[1] = {X};
+  const int32_t* ys[1] = {y};
+  return create_common(1, Xs, x_dtype, ys, &n, &p, &K, prior, prior_scale, opts, out);
+}
+
+hmc_status hmc_create_batch(int32_t nprob, const void* const* X, hmc_dtype x_dtype, const int32_t* const* y,
+                            const int64_t* n, const int64_t* p, const int32_t* K, hmc_prior_kind prior,
+                            double prior_scale, const hmc_opts* opts, hmc_handle* out) {
+  return create_common(nprob, X, x_dtype, y, n, p, K, prior, prior_scale, opts, out);
+}
+
+hmc_status hmc_destroy(hmc_handle h) {
+  if (!h) return HMC_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (Problem& P : h->probs) free_problem(P);
+  if (h->err_d) cudaFree(h->err_d);
+  if (h->temps_d) cudaFree(h->temps_d);
+  for (void* s : h->staging)
+    if (s) cudaFree(s);
+  for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+  return HMC_OK;
+}
+
+int64_t hmc_chain_size(hmc_handle h) { return h ? h->chain_size : -1; }
+
+hmc_status hmc_logpost_grad(hmc_handle h, const void* beta, int32_t chains, double* logpost, void* grad) {
+  g_last_error.clear();
+  HMC_TRY(check_chains(h, chains));
+  if (!beta) return fail(HMC_EINVAL, "beta is NULL");
+  const size_t bytes = size_t(chains) * h->chain_size * state_bytes(h);
+  const void* bd = nullptr;
+  HMC_TRY(dev_in(h, 0, beta, bytes, &bd));
+  HMC_TRY(pack_all(h, bd, chains, false, &StateSet::beta));
+  HMC_TRY(eval_state(h, false, chains));
+  bool gh = false, lh = false;
+  void* gd = nullptr;
+  void* ld = nullptr;
+  HMC_TRY(dev_out(h, 1, grad, bytes, &gd, &gh));
+  HMC_TRY(dev_out(h, 2, logpost, h->probs.size() * chains * sizeof(double), &ld, &lh));
+  if (gd) HMC_TRY(unpack_all(h, gd, chains, false, &StateSet::grad));
+  if (ld) HMC_TRY(copy_logk(h, static_cast<double*>(ld), chains, 1));
+  if (gh) HMC_CUDA(cudaMemcpyAsync(grad, gd, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (lh)
+    HMC_CUDA(cudaMemcpyAsync(logpost, ld, h->probs.size() * chains * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (gh || lh || beta != bd || h->timing) {
+    HMC_TRY(check_device_error(h));
+    if (h->timing) HMC_TRY(timer_harvest(h));
+  }
+  return HMC_OK;
+}
+
+hmc_status hmc_leapfrog(hmc_handle h, void* beta, void* eta, void* grad, double* logpost, int32_t chains, int32_t L,
+                        double eps) {
+  g_last_error.clear();
+  HMC_TRY(check_chains(h, chains));
+  if (!beta || !eta) return fail(HMC_EINVAL, "beta and eta must not be NULL");
+  if (L < 0) return fail(HMC_EINVAL, "L must be >= 0");
+  if (!std::isfinite(eps)) return fail(HMC_EINVAL, "eps must be finite");
+  const size_t bytes = size_t(chains) * h->chain_size * state_bytes(h);
+  bool bh = false, eh = false, gh = false, lh = false;
+  void *bd = nullptr, *ed = nullptr, *gd = nullptr, *ld = nullptr;
+  HMC_TRY(dev_out(h, 0, beta, bytes, &bd, &bh));
+  HMC_TRY(dev_out(h, 1, eta, bytes, &ed, &eh));
+  HMC_TRY(dev_out(h, 2, grad, bytes, &gd, &gh));
+  HMC_TRY(dev_out(h, 3, logpost, h->probs.size() * chains * sizeof(double), &ld, &lh));
+  if (bh) HMC_CUDA(cudaMemcpyAsync(bd, beta, bytes, cudaMemcpyHostToDevice, h->stream));
+  if (eh) HMC_CUDA(cudaMemcpyAsync(ed, eta, bytes, cudaMemcpyHostToDevice, h->stream));
+  if (gh) HMC_CUDA(cudaMemcpyAsync(gd, grad, bytes, cudaMemcpyHostToDevice, h->stream));
+  HMC_TRY(pack_all(h, bd, chains, false, &StateSet::beta));
+  HMC_TRY(pack_all(h, ed, chains, false, &StateSet::eta));
+  if (gd) {
+    HMC_TRY(pack_all(h, gd, chains, false, &StateSet::grad));
+  }
+  if (!gd || L == 0) HMC_TRY(eval_state(h, false, chains));
+  for (size_t b = 0; b < h->probs.size() && L > 0; ++b) {
+    Problem& P = h->probs[b];
+    UpdateArgs u = make_update(h, P, P.us, 1, chains, eps, int(b));
+    HMC_CUDA(launch_leap_start(h->st, u, h->stream));
+    for (int l = 1; l <= L; ++l) {
+      HMC_TRY(run_lpg(h, P, P.us, chains, h->stream));
+      const int mode = (l < L) ? (UPD_ETA_FULL | UPD_BETA) : (UPD_ETA_HALF | UPD_SCALARS);
+      HMC_CUDA(launch_reduce_update(h->st, u, mode, h->stream));
+    }
+  }
+  HMC_TRY(unpack_all(h, bd, chains, false, &StateSet::beta));
+  HMC_TRY(unpack_all(h, ed, chains, false, &StateSet::eta));
+  if (gd) HMC_TRY(unpack_all(h, gd, chains, false, &StateSet::grad));
+  if (ld) HMC_TRY(copy_logk(h, static_cast<double*>(ld), chains, 1));
+  if (bh) HMC_CUDA(cudaMemcpyAsync(beta, bd, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (eh) HMC_CUDA(cudaMemcpyAsync(eta, ed, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (gh) HMC_CUDA(cudaMemcpyAsync(grad, gd, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (lh)
+    HMC_CUDA(cudaMemcpyAsync(logpost, ld, h->probs.size() * chains * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (bh || eh || gh || lh || h->timing) {
+    HMC_TRY(check_device_error(h));
+    if (h->timing) HMC_TRY(timer_harvest(h));
+  }
+  return HMC_OK;
+}
+
+hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double eps, int64_t iters, uint64_t seed,
+                               const void* beta0, void* samples, int32_t thin, hmc_chain_stats* stats,
+                               const double* temps) {
+  g_last_error.clear();
+  HMC_TRY(check_chains(h, chains));
+  if (L < 1) return fail(HMC_EINVAL, "L must be >= 1");
+  if (iters < 0) return fail(HMC_EINVAL, "iters must be >= 0");
+  if (thin < 1) return fail(HMC_EINVAL, "thin must be >= 1");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HMC_EINVAL, "eps must be finite and > 0");
+  if (temps)
+    for (int64_t t = 0; t < iters; ++t)
+      if (!(temps[t] >= 1.0) || !std::isfinite(temps[t])) return fail(HMC_EINVAL, "every temperature must be finite and >= 1");
+  const size_t sb = state_bytes(h);
+  const size_t bytes = size_t(chains) * h->chain_size * sb;
+  const int nprob = int(h->probs.size());
+
+  // (Re)initialise the chain state.
+  if (beta0 || h->chains_init != chains) {
+    const void* b0 = nullptr;
+    if (beta0) HMC_TRY(dev_in(h, 0, beta0, bytes, &b0));
+    for (Problem& P : h->probs) {
+      if (b0) continue;
+      HMC_CUDA(cudaMemsetAsync(P.cs.beta, 0, size_t(P.state_elems) * sb, h->stream));
+    }
+    if (b0) HMC_TRY(pack_all(h, b0, chains, true, &StateSet::beta));
+    HMC_TRY(eval_state(h, true, chains));
+    for (Problem& P : h->probs) HMC_CUDA(cudaMemsetAsync(P.iter, 0, sizeof(int64_t), h->stream));
+    h->chains_init = chains;
+  }
+  const int64_t seed_word = static_cast<int64_t>(seed);
+  for (Problem& P : h->probs) {
+    HMC_CUDA(cudaMemsetAsync(P.iter + 1, 0, sizeof(int64_t), h->stream));
+    HMC_CUDA(cudaMemcpyAsync(P.iter + 2, &seed_word, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    HMC_CUDA(launch_init_stats(P.stats, chains, h->stream));
+  }
+  if (temps && iters > 0) {
+    if (h->temps_cap < iters) {
+      if (h->temps_d) cudaFree(h->temps_d);
+      h->temps_d = nullptr;
+      h->temps_cap = 0;
+      HMC_CUDA(cudaMalloc(&h->temps_d, size_t(iters) * sizeof(double)));
+      h->temps_cap = iters;
+    }
+    HMC_CUDA(cudaMemcpyAsync(h->temps_d, temps, size_t(iters) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  const int64_t nslots = samples ? iters / thin : 0;
+  const size_t sample_bytes = size_t(nslots) * bytes;
+  bool sh = false;
+  void* sd = nullptr;
+  if (samples && nslots > 0) HMC_TRY(dev_out(h, 3, samples, sample_bytes, &sd, &sh));
+
+  if (iters > 0) {
+    // One iteration as a CUDA graph, cached while its baked parameters hold.
+    cudaStream_t rs_stream = h->stream ? h->stream : h->cap_stream;
+    const bool use_temps = temps != nullptr;
+    const bool timing = h->timing;
+    if (h->gexec && !(h->g_chains == chains && h->g_L == L && h->g_eps == eps && h->g_thin == thin &&
+                      h->g_samples == sd && h->g_temps == use_temps && h->g_temps_ptr == h->temps_d && h->g_timing == timing &&
+                      h->g_stream == rs_stream)) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    if (!h->gexec) {
+      HMC_CUDA(cudaStreamSynchronize(h->stream));
+      cudaGraph_t graph = nullptr;
+      cudaStream_t cst = h->cap_stream;
+      h->timer.used = 0;
+      HMC_CUDA(cudaStreamBeginCapture(cst, cudaStreamCaptureModeThreadLocal));
+      hmc_status cs = HMC_OK;
+      for (int b = 0; b < nprob && cs == HMC_OK; ++b) {
+        Problem& P = h->probs[b];
+        UpdateArgs u = make_update(h, P, P.cs, 0, chains, eps, b);
+        u.temps = use_temps ? h->temps_d : nullptr;
+        u.thin = thin;
+        if (sd) {
+          u.samples = static_cast<char*>(sd) + size_t(block_offset(h, b, chains)) * sb;
+          u.sample_slot_stride = int64_t(chains) * h->chain_size;
+        }
+        if (launch_traj_start(h->st, u, cst) != cudaSuccess) {
+          cs = fail(HMC_ECUDA, "traj_start launch failed");
+          break;
+        }
+        for (int l = 1; l <= L && cs == HMC_OK; ++l) {
+          cs = run_lpg(h, P, P.cs, chains, cst);
+          if (cs != HMC_OK) break;
+          const int mode = (l < L) ? (UPD_ETA_FULL | UPD_BETA) : (UPD_ETA_HALF | UPD_SCALARS | UPD_ACCEPT);
+          if (launch_reduce_update(h->st, u, mode, cst) != cudaSuccess) cs = fail(HMC_ECUDA, "reduce launch failed");
+        }
+        if (cs == HMC_OK && launch_select(h->st, u, P.tickets + h->max_chains, cst) != cudaSuccess)
+          cs = fail(HMC_ECUDA, "select launch failed");
+      }
+      cudaError_t ce = cudaStreamEndCapture(cst, &graph);
+      if (cs != HMC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        h->timer.used = 0;
+        return cs;
+      }
+      HMC_CUDA(ce);
+      ce = cudaGraphInstantiate(&h->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      HMC_CUDA(ce);
+      h->g_chains = chains;
+      h->g_L = L;
+      h->g_eps = eps;
+      h->g_thin = thin;
+      h->g_samples = sd;
+      h->g_temps = use_temps;
+      h->g_temps_ptr = h->temps_d;
+      h->g_timing = timing;
+      h->g_stream = rs_stream;
+      h->g_pairs = h->timer.used;
+      h->timer.used = 0;
+    }
+    if (rs_stream != h->stream) {
+      // The private replay stream starts after the work queued on the handle's stream.
+      HMC_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    hmc_status rs = HMC_OK;
+    for (int64_t t = 0; t < iters; ++t) {
+      if (cudaGraphLaunch(h->gexec, rs_stream) != cudaSuccess) {
+        rs = fail(HMC_ECUDA, "cudaGraphLaunch failed");
+        break;
+      }
+      if (timing) {
+        h->timer.used = h->g_pairs;
+        if ((rs = timer_harvest(h)) != HMC_OK) break;
+      }
+    }
+    h->timer.used = 0;
+    cudaStreamSynchronize(rs_stream);
+    if (rs != HMC_OK) return rs;
+  }
+  HMC_TRY(check_device_error(h));
+  if (sh) HMC_CUDA(cudaMemcpyAsync(samples, sd, sample_bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (stats) {
+    for (int b = 0; b < nprob; ++b)
+      HMC_CUDA(cudaMemcpyAsync(stats + size_t(b) * chains, h->probs[b].stats, size_t(chains) * sizeof(hmc_chain_stats),
+                               cudaMemcpyDeviceToHost, h->stream));
+  }
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  return HMC_OK;
+}
+
+hmc_status hmc_sample(hmc_handle h, int32_t chains, int32_t L, double eps, int64_t iters, uint64_t seed,
+                      const void* beta0, void* samples, int32_t thin, hmc_chain_stats* stats) {
+  return hmc_sample_tempered(h, chains, L, eps, iters, seed, beta0, samples, thin, stats, nullptr);
+}
+
+hmc_status hmc_get_state(hmc_handle h, int32_t chains, void* beta, void* grad, double* logpost,
+                         int64_t* next_iteration) {
+  g_last_error.clear();
+  HMC_TRY(check_chains(h, chains));
+  const size_t bytes = size_t(chains) * h->chain_size * state_bytes(h);
+  bool bh = false, gh = false, lh = false;
+  void *bd = nullptr, *gd = nullptr, *ld = nullptr;
+  HMC_TRY(dev_out(h, 0, beta, bytes, &bd, &bh));
+  HMC_TRY(dev_out(h, 1, grad, bytes, &gd, &gh));
+  HMC_TRY(dev_out(h, 2, logpost, h->probs.size() * chains * sizeof(double), &ld, &lh));
+  if (bd) HMC_TRY(unpack_all(h, bd, chains, true, &StateSet::beta));
+  if (gd) HMC_TRY(unpack_all(h, gd, chains, true, &StateSet::grad));
+  if (ld) HMC_TRY(copy_logk(h, static_cast<double*>(ld), chains, 0));
+  if (bh) HMC_CUDA(cudaMemcpyAsync(beta, bd, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (gh) HMC_CUDA(cudaMemcpyAsync(grad, gd, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (lh)
+    HMC_CUDA(cudaMemcpyAsync(logpost, ld, h->probs.size() * chains * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (next_iteration)
+    HMC_CUDA(cudaMemcpyAsync(next_iteration, h->probs[0].iter, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  return HMC_OK;
+}
+
+hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales) {
+  g_last_error.clear();
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  if (b < 0 || b >= int(h->probs.size())) return fail(HMC_EINVAL, "problem index out of range");
+  if (!dst) return fail(HMC_EINVAL, "dst is NULL");
+  Problem& P = h->probs[b];
+  const size_t xb = dtype_bytes(h->xt);
+  if (P.n > 0)
+    HMC_CUDA(cudaMemcpy2DAsync(dst, size_t(P.p) * xb, P.X, size_t(P.p_pad) * xb, size_t(P.p) * xb, size_t(P.n),
+                               cudaMemcpyDefault, h->stream));
+  if (scales && P.xscale)
+    HMC_CUDA(cudaMemcpyAsync(scales, P.xscale, size_t(P.p) * sizeof(float), cudaMemcpyDefault, h->stream));
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  return HMC_OK;
+}
+
+const char* hmc_describe(hmc_handle h) { return h ? h->desc.c_str() : "{}"; }
+
+hmc_status hmc_set_timing(hmc_handle h, int32_t enable) {
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  h->timing = enable != 0;
+  h->timing_ms = 0.0;
+  h->timing_launches = 0;
+  h->timer.used = 0;
+  return HMC_OK;
+}
+
+hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launches) {
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  if (total_ms) *total_ms = h->timing_ms;
+  if (launches) *launches = h->timing_launches;
+  return HMC_OK;
+}
+
+}  // extern "C"

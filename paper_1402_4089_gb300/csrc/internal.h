@@ -1,0 +1,101 @@
+// Host-side declarations shared by the translation units of libhmc.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hmc.h"
+
+namespace hmc {
+
+// One launch of a fused log-posterior/gradient pass (Eqs. logkernel and
+// gradient): every cluster of S CTAs walks row tiles of BM rows; CTA `rank`
+// of a cluster owns the column slice [rank*PC, (rank+1)*PC) of X and of the
+// coefficients.  Outputs are per-cluster partial sums reduced later in a
+// fixed order (no floating-point atomics).
+struct LpgArgs {
+  const void* X;            // [n][p_pad] storage type, zero-padded columns
+  const int32_t* y;         // [n]
+  const float* xscale;      // [p_pad] FP8 column scales, or nullptr
+  const void* beta;         // [C][p_pad] state type (first column of this launch)
+  void* gpart;              // partial gradient, state type; cluster b at gpart + b*gpart_cstride
+  int64_t gpart_cstride;    // elements between consecutive clusters' partials
+  double* lpart;            // partial log-likelihood per chain; cluster b at lpart + b*lpart_cstride
+  int32_t lpart_cstride;
+  int* err;                 // device error word (bits of hmc::ERR_*)
+  int64_t n;                // rows
+  int32_t p_pad;            // padded columns (= S * PC)
+  int32_t PC;               // columns per CTA
+  int32_t C;                // coefficient columns of this launch (chains * Km1)
+  int32_t Km1;              // K - 1
+  int32_t chains;           // chains of this launch
+  int32_t BM;               // rows per tile (8, 16 or 32)
+  int32_t S;                // cluster size
+  int32_t NT;               // threads per CTA
+  int32_t NSTAGE;           // X tile stages in shared memory
+  int32_t nclusters;        // clusters in the grid
+  int64_t ntiles;           // ceil(n / BM)
+  long long spin_limit;     // probes per bounded wait
+  int32_t inject_timeout;   // 1: wait on a barrier nothing arrives at (host-side fault injection)
+};
+
+// CUDA-core fused kernel (any X storage type, small C).
+constexpr int kSimtMaxThreads = 384;
+int simt_max_ct(int xt);                                     // largest C one launch handles
+size_t simt_smem_bytes(int xt, int st, int C, int PC, int BM, int S, int NT, int NSTAGE);
+cudaError_t simt_prepare(int xt, int st, int C, size_t smem, int S);   // func attributes
+cudaError_t simt_max_active_clusters(int xt, int st, int C, size_t smem, int S, int NT, int* out);
+cudaError_t simt_launch(int xt, int st, const LpgArgs& a, size_t smem, cudaStream_t stream);
+
+// Element-wise / reduction kernels (update.cu).
+struct UpdateArgs {
+  void* beta;  void* eta;  void* grad;          // [chains][Km1][p_pad] state type
+  void* beta0; void* grad0;                     // saved trajectory start
+  const void* gpart; int64_t gpart_cstride; int32_t nparts;   // partial gradients
+  const double* lpart; int32_t lpart_cstride;
+  double* logk;     // [chains] current log K
+  double* logk0;    // [chains] at trajectory start
+  double* h0;       // [chains] H at trajectory start
+  double* scal;     // scratch [chains][nblk][2] block partials
+  unsigned int* tickets;  // [chains] last-block counters (self-resetting)
+  int* accept;      // [chains]
+  void* stats;      // [chains] hmc_chain_stats (device)
+  const double* temps;  // [iters] or nullptr
+  int64_t* iter;    // device iteration counter (global, for the RNG)
+  int64_t* local_iter; // iteration within the current hmc_sample call
+  void* samples; int32_t thin; int64_t sample_slot_stride;  // user layout: [slot][...][chains][Km1][p]
+  int32_t chains_word_hi;  // problem index (high half of the RNG chain word)
+  int* err;
+  int32_t p, p_pad, Km1, chains, nblk;
+  int32_t prior_kind; double prior_scale;
+  double eps;
+  const uint64_t* seed;  // device: generator key of the current hmc_sample call
+};
+
+enum : int {
+  UPD_ETA_HALF = 1,     // eta += eps/2 * g
+  UPD_ETA_FULL = 2,     // eta += eps * g
+  UPD_BETA = 4,         // beta += eps * eta (after the eta update)
+  UPD_SCALARS = 8,      // log K (and kinetic energy) per chain
+  UPD_ACCEPT = 16,      // end of trajectory: Metropolis test
+};
+
+cudaError_t launch_reduce_update(int st, const UpdateArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_traj_start(int st, const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_select(int st, const UpdateArgs& a, unsigned int* ticket_all, cudaStream_t s);
+int update_blocks_per_chain(int64_t per_chain);
+cudaError_t launch_leap_start(int st, const UpdateArgs& a, cudaStream_t s);
+
+// Layout conversion between the user layout [chains][Km1][p] (state type)
+// and the padded device layout [chains][Km1][p_pad].
+cudaError_t launch_pack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s);
+cudaError_t launch_unpack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s);
+
+// X upload: convert float/double rows into the storage type with padding.
+cudaError_t launch_convert_x(int in_dtype, const void* src, int xt, void* dst, const float* scales, int64_t n, int32_t p,
+                             int32_t p_pad, int* err, cudaStream_t s);
+cudaError_t launch_fp8_scales(int in_dtype, const void* src, float* scales, int64_t n, int32_t p, int32_t p_pad,
+                              cudaStream_t s);
+cudaError_t launch_check_labels(const int32_t* y, int64_t n, int32_t K, int* err, cudaStream_t s);
+cudaError_t launch_init_stats(void* stats, int chains, cudaStream_t s);
+
+}  // namespace hmc

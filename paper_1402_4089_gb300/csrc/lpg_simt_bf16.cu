@@ -1,0 +1,28 @@
+// Instantiations of the CUDA-core fused pass for X stored as __nv_bfloat16.
+#include "lpg_simt.cuh"
+
+namespace hmc {
+namespace simt {
+
+using KernelFn = void (*)(const LpgArgs);
+
+int table_bf16(const int** cts, const KernelFn** fns) {
+  static const int kCT[] = {1,2,3,4,6,9,12,16,20};
+  static const KernelFn kFn[] = {
+      lpg_kernel<__nv_bfloat16, float, 1>,
+      lpg_kernel<__nv_bfloat16, float, 2>,
+      lpg_kernel<__nv_bfloat16, float, 3>,
+      lpg_kernel<__nv_bfloat16, float, 4>,
+      lpg_kernel<__nv_bfloat16, float, 6>,
+      lpg_kernel<__nv_bfloat16, float, 9>,
+      lpg_kernel<__nv_bfloat16, float, 12>,
+      lpg_kernel<__nv_bfloat16, float, 16>,
+      lpg_kernel<__nv_bfloat16, float, 20>,
+  };
+  *cts = kCT;
+  *fns = kFn;
+  return int(sizeof(kCT) / sizeof(kCT[0]));
+}
+
+}  // namespace simt
+}  // namespace hmc

@@ -1,0 +1,113 @@
+// Host side of the CUDA-core fused pass: instantiation lookup, shared-memory
+// sizing, function attributes, occupancy query and the cluster launch.
+#include "lpg_simt.cuh"
+
+namespace hmc {
+namespace simt {
+
+using KernelFn = void (*)(const LpgArgs);
+int table_f64(const int** cts, const KernelFn** fns);
+int table_f32(const int** cts, const KernelFn** fns);
+int table_bf16(const int** cts, const KernelFn** fns);
+int table_fp8(const int** cts, const KernelFn** fns);
+
+static int table(int xt, const int** cts, const KernelFn** fns) {
+  switch (xt) {
+    case HMC_F64: return table_f64(cts, fns);
+    case HMC_F32: return table_f32(cts, fns);
+    case HMC_BF16: return table_bf16(cts, fns);
+    default: return table_fp8(cts, fns);
+  }
+}
+
+// Smallest instantiated class bound >= C; returns the kernel (nullptr if none).
+static KernelFn pick(int xt, int C, int* ct) {
+  const int* cts;
+  const KernelFn* fns;
+  const int m = table(xt, &cts, &fns);
+  for (int i = 0; i < m; ++i)
+    if (cts[i] >= C) {
+      *ct = cts[i];
+      return fns[i];
+    }
+  *ct = 0;
+  return nullptr;
+}
+
+}  // namespace simt
+
+int simt_max_ct(int xt) {
+  const int* cts;
+  const simt::KernelFn* fns;
+  const int m = simt::table(xt, &cts, &fns);
+  return cts[m - 1];
+}
+
+size_t simt_smem_bytes(int xt, int /*st*/, int C, int PC, int BM, int S, int NT, int NSTAGE) {
+  int ct = 0;
+  if (!simt::pick(xt, C, &ct)) return ~size_t(0);
+  const int xbytes = xt == HMC_F64 ? 8 : xt == HMC_F32 ? 4 : xt == HMC_BF16 ? 2 : 1;
+  const int abytes = xt == HMC_F64 ? 8 : 4;
+  const int pv = 16 / abytes;
+  const int ctp = ((ct + pv - 1) / pv) * pv;
+  return simt::layout(xbytes, abytes, ct, ctp, PC, BM, S, NT, NSTAGE).total;
+}
+
+cudaError_t simt_prepare(int xt, int /*st*/, int C, size_t smem, int S) {
+  int ct = 0;
+  simt::KernelFn fn = simt::pick(xt, C, &ct);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  if (S > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+static void fill_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int grid, int S, int NT, size_t smem,
+                        cudaStream_t stream) {
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cfg.numAttrs = 0;
+  cfg.attrs = attr;
+  if (S > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.numAttrs = 1;
+  }
+}
+
+cudaError_t simt_max_active_clusters(int xt, int /*st*/, int C, size_t smem, int S, int NT, int* out) {
+  int ct = 0;
+  simt::KernelFn fn = simt::pick(xt, C, &ct);
+  if (!fn) return cudaErrorInvalidValue;
+  if (S == 1) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *out = per_sm * sms;
+    return cudaSuccess;
+  }
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config(cfg, attr, S, S, NT, smem, nullptr);
+  return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
+}
+
+cudaError_t simt_launch(int xt, int /*st*/, const LpgArgs& a, size_t smem, cudaStream_t stream) {
+  int ct = 0;
+  simt::KernelFn fn = simt::pick(xt, a.C, &ct);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config(cfg, attr, a.nclusters * a.S, a.S, a.NT, smem, stream);
+  return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
+}  // namespace hmc

@@ -1,0 +1,442 @@
+// Per-coefficient kernels of the sampler: fixed-order reduction of the fused
+// pass's partial gradients plus the prior term (Eq. gradient), the leapfrog
+// momentum / coefficient updates (Eqs. hmc1-hmc3), the momentum draw, the
+// Metropolis test with momentum (Eq. accept, kinetic energy eta.eta/2), the
+// keep-or-restore select, and the upload / layout conversions.
+//
+// Scalars (log K, kinetic energy) are summed in FP64: per-block partials in
+// fixed slots, combined by the last block of each chain (ticket counter) in
+// block order with Neumaier compensation, so results are bitwise repeatable.
+#include <cmath>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace hmc {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename ST>
+__device__ __forceinline__ double prior_term(ST b, int kind, double s) {
+  const double x = double(b);
+  if (kind == HMC_PRIOR_CAUCHY) return -log1p((x / s) * (x / s));
+  return -(x * x) / (2.0 * s * s);
+}
+
+template <typename ST>
+__device__ __forceinline__ ST prior_deriv(ST b, int kind, double s) {
+  if (kind == HMC_PRIOR_CAUCHY) return ST(-2.0) * b / (ST(s * s) + b * b);
+  return -b / ST(s * s);
+}
+
+// Fixed-order block sum of two doubles; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[kThreads / 32], sb[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = 0.0;
+    b = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+      a += sa[i];
+      b += sb[i];
+    }
+  }
+}
+
+// Ticket: true in exactly one block (the last to finish) of chain c.
+__device__ __forceinline__ bool last_block(unsigned int* ticket, unsigned int nblk) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == nblk - 1u);
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
+}
+
+template <typename ST>
+__global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArgs A, int mode) {
+  const int c = blockIdx.y;
+  const int64_t per_chain = int64_t(A.Km1) * A.p_pad;
+  const size_t base = size_t(c) * per_chain;
+  const ST* gp = static_cast<const ST*>(A.gpart);
+  ST* beta = static_cast<ST*>(A.beta);
+  ST* eta = static_cast<ST*>(A.eta);
+  ST* grad = static_cast<ST*>(A.grad);
+  const ST ce = (mode & UPD_ETA_HALF) ? ST(0.5 * A.eps) : ST(A.eps);
+  const ST eb = ST(A.eps);
+  double prior_s = 0.0, kin_s = 0.0;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < per_chain;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int j = int(e % A.p_pad);
+    if (j >= A.p) continue;  // padding columns stay zero
+    const size_t idx = base + size_t(e);
+    ST g = ST(0);
+    for (int b = 0; b < A.nparts; ++b) g += gp[size_t(b) * A.gpart_cstride + idx];
+    const ST bv = beta[idx];
+    g += prior_deriv(bv, A.prior_kind, A.prior_scale);
+    grad[idx] = g;
+    ST ev = ST(0);
+    if (mode & (UPD_ETA_HALF | UPD_ETA_FULL)) {
+      ev = eta[idx] + ce * g;
+      eta[idx] = ev;
+    }
+    if (mode & UPD_SCALARS) {
+      prior_s += prior_term(bv, A.prior_kind, A.prior_scale);
+      if (mode & UPD_ACCEPT) kin_s += double(ev) * double(ev);
+    }
+    if (mode & UPD_BETA) beta[idx] = bv + eb * ev;
+  }
+  if (!(mode & UPD_SCALARS)) return;
+  block_sum2(prior_s, kin_s);
+  if (threadIdx.x == 0) {
+    double* sl = A.scal + (size_t(c) * A.nblk + blockIdx.x) * 2;
+    sl[0] = prior_s;
+    sl[1] = kin_s;
+  }
+  if (!last_block(A.tickets + c, gridDim.x)) return;
+  if (threadIdx.x != 0) return;
+  Neumaier pr, ki, li;
+  for (int b = 0; b < int(gridDim.x); ++b) {
+    const double* sl = A.scal + (size_t(c) * A.nblk + b) * 2;
+    pr.add(sl[0]);
+    ki.add(sl[1]);
+  }
+  for (int b = 0; b < A.nparts; ++b) li.add(A.lpart[size_t(b) * A.lpart_cstride + c]);
+  const double logk = li.value() + pr.value();
+  A.tickets[c] = 0u;
+  if (!(mode & UPD_ACCEPT)) {
+    A.logk[c] = logk;
+    return;
+  }
+  const int64_t it = *A.iter;
+  const double T = A.temps ? A.temps[*A.local_iter] : 1.0;
+  const double h0 = A.h0[c];
+  const double h1 = -logk + 0.5 * ki.value();
+  const bool finite = isfinite(h1);
+  const double u = accept_uniform(*A.seed, uint64_t(it), uint64_t(c) | (uint64_t(A.chains_word_hi) << 32));
+  const bool acc = finite && (log(u) < (h0 - h1) / T);
+  A.accept[c] = acc ? 1 : 0;
+  hmc_chain_stats* st = static_cast<hmc_chain_stats*>(A.stats) + c;
+  st->iterations += 1;
+  st->accepted += acc ? 1 : 0;
+  st->diverged += finite ? 0 : 1;
+  if (finite) st->sum_abs_dH += fabs(h1 - h0);
+  const double kept = acc ? logk : A.logk0[c];
+  A.logk[c] = kept;
+  st->logpost = kept;
+}
+
+// Start of a trajectory: eta ~ N(0, I), save (beta, grad, log K), H0, then
+// the first momentum half step and the first coefficient step.
+template <typename ST>
+__global__ void __launch_bounds__(kThreads) traj_start_kernel(const UpdateArgs A) {
+  const int c = blockIdx.y;
+  const int64_t per_chain_q = int64_t(A.Km1) * A.p;
+  const int64_t nqb = (per_chain_q + 3) / 4;
+  const size_t base = size_t(c) * A.Km1 * A.p_pad;
+  ST* beta = static_cast<ST*>(A.beta);
+  ST* eta = static_cast<ST*>(A.eta);
+  const ST* grad = static_cast<const ST*>(A.grad);
+  ST* beta0 = static_cast<ST*>(A.beta0);
+  ST* grad0 = static_cast<ST*>(A.grad0);
+  const uint64_t it = uint64_t(*A.iter);
+  const uint64_t seed = *A.seed;
+  const uint64_t chain_word = uint64_t(c) | (uint64_t(A.chains_word_hi) << 32);
+  const ST half = ST(0.5 * A.eps), full = ST(A.eps);
+  double kin = 0.0, unused = 0.0;
+  for (int64_t qb = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; qb < nqb; qb += int64_t(gridDim.x) * blockDim.x) {
+    double z[4];
+    momentum_block(seed, it, chain_word, uint64_t(qb), z);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t q = qb * 4 + r;
+      if (q >= per_chain_q) break;
+      const int64_t k = q / A.p, j = q - k * A.p;
+      const size_t idx = base + size_t(k) * A.p_pad + size_t(j);
+      const ST e = ST(z[r]);
+      kin += double(e) * double(e);
+      const ST b = beta[idx], g = grad[idx];
+      beta0[idx] = b;
+      grad0[idx] = g;
+      const ST eh = e + half * g;
+      eta[idx] = eh;
+      beta[idx] = b + full * eh;
+    }
+  }
+  block_sum2(kin, unused);
+  if (threadIdx.x == 0) A.scal[(size_t(c) * A.nblk + blockIdx.x) * 2 + 1] = kin;
+  if (!last_block(A.tickets + c, gridDim.x)) return;
+  if (threadIdx.x != 0) return;
+  Neumaier ki;
+  for (int b = 0; b < int(gridDim.x); ++b) ki.add(A.scal[(size_t(c) * A.nblk + b) * 2 + 1]);
+  A.tickets[c] = 0u;
+  A.logk0[c] = A.logk[c];
+  A.h0[c] = -A.logk[c] + 0.5 * ki.value();
+}
+
+// Keep the proposal or restore the trajectory start; write the sample; the
+// last block advances the iteration counters.
+template <typename ST>
+__global__ void __launch_bounds__(kThreads) select_kernel(const UpdateArgs A, unsigned int* ticket_all) {
+  const int c = blockIdx.y;
+  const int64_t per_chain = int64_t(A.Km1) * A.p_pad;
+  const size_t base = size_t(c) * per_chain;
+  ST* beta = static_cast<ST*>(A.beta);
+  ST* grad = static_cast<ST*>(A.grad);
+  const ST* beta0 = static_cast<const ST*>(A.beta0);
+  const ST* grad0 = static_cast<const ST*>(A.grad0);
+  const bool acc = A.accept[c] != 0;
+  const int64_t li = *A.local_iter;
+  ST* out = nullptr;
+  if (A.samples && ((li + 1) % A.thin) == 0) {
+    const int64_t slot = (li + 1) / A.thin - 1;
+    out = static_cast<ST*>(A.samples) + size_t(slot) * A.sample_slot_stride + size_t(c) * A.Km1 * A.p;
+  }
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < per_chain;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t k = e / A.p_pad, j = e - k * A.p_pad;
+    if (j >= A.p) continue;
+    const size_t idx = base + size_t(e);
+    ST b = beta[idx];
+    if (!acc) {
+      b = beta0[idx];
+      beta[idx] = b;
+      grad[idx] = grad0[idx];
+    }
+    if (out) out[size_t(k) * A.p + size_t(j)] = b;
+  }
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket_all, 1u) == gridDim.x * gridDim.y - 1u);
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    *ticket_all = 0u;
+    *A.iter += 1;
+    *A.local_iter += 1;
+  }
+}
+
+// hmc_leapfrog start: first half step of the momentum and first coefficient step.
+template <typename ST>
+__global__ void leap_start_kernel(const UpdateArgs A, int64_t total) {
+  ST* beta = static_cast<ST*>(A.beta);
+  ST* eta = static_cast<ST*>(A.eta);
+  const ST* grad = static_cast<const ST*>(A.grad);
+  const ST half = ST(0.5 * A.eps), full = ST(A.eps);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const ST e = eta[i] + half * grad[i];
+    eta[i] = e;
+    beta[i] = beta[i] + full * e;
+  }
+}
+
+template <typename T>
+__global__ void pack_kernel(const T* src, T* dst, int64_t rows, int32_t p, int32_t p_pad) {
+  const int64_t total = rows * p_pad;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / p_pad, j = i - r * p_pad;
+    dst[i] = (j < p) ? src[r * p + j] : T(0);
+  }
+}
+
+template <typename T>
+__global__ void unpack_kernel(const T* src, T* dst, int64_t rows, int32_t p, int32_t p_pad) {
+  const int64_t total = rows * p;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / p, j = i - r * p;
+    dst[i] = src[r * p_pad + j];
+  }
+}
+
+template <typename IT>
+__device__ __forceinline__ float to_f32(IT v) {
+  return float(v);
+}
+
+template <typename IT, typename XT>
+__global__ void convert_x_kernel(const IT* src, XT* dst, const float* scales, int64_t n, int32_t p, int32_t p_pad,
+                                 int* err) {
+  const int64_t total = n * p_pad;
+  int bad = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / p_pad, j = i - r * p_pad;
+    if (j >= p) {
+      dst[i] = XT(0.0f);
+      continue;
+    }
+    const IT v = src[r * p + j];
+    if (!isfinite(double(v))) bad = 1;
+    if constexpr (std::is_same<XT, double>::value) {
+      dst[i] = double(v);
+    } else if constexpr (std::is_same<XT, float>::value) {
+      dst[i] = float(v);
+    } else if constexpr (std::is_same<XT, __nv_bfloat16>::value) {
+      dst[i] = __float2bfloat16_rn(float(v));
+    } else {
+      const float q = float(v) / scales[j];
+      __nv_fp8_e4m3 o;
+      o.__x = __nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+      dst[i] = o;
+    }
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE_X);
+}
+
+template <typename IT>
+__global__ void fp8_scale_kernel(const IT* src, float* scales, int64_t n, int32_t p, int32_t p_pad) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p_pad) return;
+  if (j >= p) {
+    scales[j] = 1.0f;
+    return;
+  }
+  float amax = 0.0f;
+  for (int64_t r = 0; r < n; ++r) amax = fmaxf(amax, fabsf(float(src[r * p + j])));
+  scales[j] = (amax == 0.0f) ? 1.0f : amax / 448.0f;
+}
+
+__global__ void check_labels_kernel(const int32_t* y, int64_t n, int32_t K, int* err) {
+  int bad = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    if (y[i] < 0 || y[i] >= K) bad = 1;
+  if (bad) atomicOr(err, ERR_BAD_LABEL);
+}
+
+__global__ void init_stats_kernel(hmc_chain_stats* s, int chains) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < chains) s[c] = hmc_chain_stats{0, 0, 0, 0.0, 0.0};
+}
+
+int grid_for(int64_t work, int cap = 4096) {
+  int64_t g = (work + kThreads - 1) / kThreads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return int(g);
+}
+
+}  // namespace
+
+int update_blocks_per_chain(int64_t per_chain) {
+  int64_t g = (per_chain + 4 * kThreads - 1) / (4 * kThreads);
+  if (g < 1) g = 1;
+  if (g > 256) g = 256;
+  return int(g);
+}
+
+cudaError_t launch_reduce_update(int st, const UpdateArgs& a, int mode, cudaStream_t s) {
+  dim3 grid(a.nblk, a.chains);
+  if (st == HMC_F64)
+    reduce_update_kernel<double><<<grid, kThreads, 0, s>>>(a, mode);
+  else
+    reduce_update_kernel<float><<<grid, kThreads, 0, s>>>(a, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_traj_start(int st, const UpdateArgs& a, cudaStream_t s) {
+  dim3 grid(a.nblk, a.chains);
+  if (st == HMC_F64)
+    traj_start_kernel<double><<<grid, kThreads, 0, s>>>(a);
+  else
+    traj_start_kernel<float><<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(int st, const UpdateArgs& a, unsigned int* ticket_all, cudaStream_t s) {
+  dim3 grid(a.nblk, a.chains);
+  if (st == HMC_F64)
+    select_kernel<double><<<grid, kThreads, 0, s>>>(a, ticket_all);
+  else
+    select_kernel<float><<<grid, kThreads, 0, s>>>(a, ticket_all);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leap_start(int st, const UpdateArgs& a, cudaStream_t s) {
+  const int64_t total = int64_t(a.chains) * a.Km1 * a.p_pad;
+  if (st == HMC_F64)
+    leap_start_kernel<double><<<grid_for(total), kThreads, 0, s>>>(a, total);
+  else
+    leap_start_kernel<float><<<grid_for(total), kThreads, 0, s>>>(a, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s) {
+  const int g = grid_for(rows * p_pad);
+  if (st == HMC_F64)
+    pack_kernel<double><<<g, kThreads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), rows, p, p_pad);
+  else
+    pack_kernel<float><<<g, kThreads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), rows, p, p_pad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s) {
+  const int g = grid_for(rows * p);
+  if (st == HMC_F64)
+    unpack_kernel<double><<<g, kThreads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), rows, p, p_pad);
+  else
+    unpack_kernel<float><<<g, kThreads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), rows, p, p_pad);
+  return cudaGetLastError();
+}
+
+template <typename IT>
+static cudaError_t convert_from(const IT* src, int xt, void* dst, const float* scales, int64_t n, int32_t p, int32_t p_pad,
+                                int* err, cudaStream_t s) {
+  const int g = grid_for(n * p_pad, 8192);
+  switch (xt) {
+    case HMC_F64:
+      convert_x_kernel<IT, double><<<g, kThreads, 0, s>>>(src, static_cast<double*>(dst), scales, n, p, p_pad, err);
+      break;
+    case HMC_F32:
+      convert_x_kernel<IT, float><<<g, kThreads, 0, s>>>(src, static_cast<float*>(dst), scales, n, p, p_pad, err);
+      break;
+    case HMC_BF16:
+      convert_x_kernel<IT, __nv_bfloat16><<<g, kThreads, 0, s>>>(src, static_cast<__nv_bfloat16*>(dst), scales, n, p,
+                                                                   p_pad, err);
+      break;
+    default:
+      convert_x_kernel<IT, __nv_fp8_e4m3><<<g, kThreads, 0, s>>>(src, static_cast<__nv_fp8_e4m3*>(dst), scales, n, p,
+                                                                   p_pad, err);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_x(int in_dtype, const void* src, int xt, void* dst, const float* scales, int64_t n, int32_t p,
+                             int32_t p_pad, int* err, cudaStream_t s) {
+  if (in_dtype == HMC_F64) return convert_from(static_cast<const double*>(src), xt, dst, scales, n, p, p_pad, err, s);
+  return convert_from(static_cast<const float*>(src), xt, dst, scales, n, p, p_pad, err, s);
+}
+
+cudaError_t launch_fp8_scales(int in_dtype, const void* src, float* scales, int64_t n, int32_t p, int32_t p_pad,
+                              cudaStream_t s) {
+  const int g = (p_pad + kThreads - 1) / kThreads;
+  if (in_dtype == HMC_F64)
+    fp8_scale_kernel<double><<<g, kThreads, 0, s>>>(static_cast<const double*>(src), scales, n, p, p_pad);
+  else
+    fp8_scale_kernel<float><<<g, kThreads, 0, s>>>(static_cast<const float*>(src), scales, n, p, p_pad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_labels(const int32_t* y, int64_t n, int32_t K, int* err, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  check_labels_kernel<<<grid_for(n), kThreads, 0, s>>>(y, n, K, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_stats(void* stats, int chains, cudaStream_t s) {
+  init_stats_kernel<<<(chains + 127) / 128, 128, 0, s>>>(static_cast<hmc_chain_stats*>(stats), chains);
+  return cudaGetLastError();
+}
+
+}  // namespace hmc
