@@ -71,7 +71,7 @@ typedef struct {
   int32_t engine;         /* 0 auto, 1 CUDA-core fused kernel, 2 tensor-core fused kernel */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
-  int32_t tile[4];        /* {cluster size, rows per tile, threads, stages}; 0 = autotuned */
+  int32_t tile[4];        /* {cluster size, rows per super-tile, rows per chunk, ring chunks}; 0 = chosen */
 } hmc_opts;
 
 /* Per-chain counters of hmc_sample (host memory, one entry per chain). */

@@ -69,7 +69,7 @@ struct Problem {
   int32_t* y = nullptr;
   float* xscale = nullptr;
   // fused-pass configuration
-  int S = 1, BM = 32, NT = 32, NSTAGE = 2, PC = 32, nclusters = 1, ct_launch = 1, group_chains = 1;
+  int S = 1, BM = 32, CR = 8, NT = 32, NSTAGE = 2, PC = 32, nclusters = 1, ct_launch = 1, group_chains = 1;
   size_t smem = 0;
   int64_t ntiles = 0;
   void* gpart = nullptr;
@@ -85,6 +85,14 @@ struct Problem {
   int64_t* iter = nullptr;  // [3]: global iteration, local iteration, generator seed
   int nblk = 1;
   int64_t state_elems = 0;  // max_chains * Km1 * p_pad
+  // tensor-core engine
+  int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel
+  TcPlan tp{};
+  TcMaps tmaps{};
+  void* bbf = nullptr;      // BF16 B operand [N][p_pad]
+  void* zg = nullptr;       // partial-logit exchange [nclu][2][S][128][N]
+  void* rg = nullptr;       // residual exchange [nclu][2][128][NP]
+  int nlparts = 0;          // log-likelihood partials reduced per chain
 };
 
 struct FusedTimer {
@@ -97,7 +105,7 @@ struct FusedTimer {
 struct hmc_ctx {
   int xt = HMC_F32, st = HMC_F32, prior_kind = 0;
   double prior_scale = 1.0;
-  int max_chains = 1, engine = 1;
+  int max_chains = 1, engine = 0;
   long long spin_limit = 1ll << 22;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture / replay
@@ -186,7 +194,7 @@ hmc_status check_device_error(hmc_ctx* h) {
 
 // ------------------------------------------------------------- configuration
 struct TileChoice {
-  int S, BM, NT, NSTAGE, PC;
+  int S, BM, CR, NT, NSTAGE, PC;
   size_t smem;
 };
 
@@ -197,30 +205,36 @@ hmc_status choose_simt(hmc_ctx* h, Problem& P, int ct_cols, TileChoice* out) {
   HMC_CUDA(cudaGetDevice(&dev));
   HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const int Ss[] = {1, 2, 4, 8, 16};
-  const int BMs[] = {32, 16, 8};
-  const int NSs[] = {3, 2};
+  const int BMs[] = {32, 64, 16};
+  const int CRs[] = {8, 16, 32};
+  const int NSs[] = {6, 5, 4, 3, 2};
   bool found = false;
   TileChoice best{};
-  double best_score = -1.0;
+  double best_score = -1e30;
   for (int S : Ss) {
     if (h->tile[0] && S != h->tile[0]) continue;
     int PC = round_up((P.p + S - 1) / S, 32);
     if (PC < 32) PC = 32;
-    int NT = round_up(std::max(32, PC / 4), 32);
-    if (h->tile[2]) NT = std::max(NT, round_up(h->tile[2], 32));
+    const int NT = round_up(std::max(32, PC / 4), 32);
     if (NT > kSimtMaxThreads || PC > 4 * NT) continue;
     for (int BM : BMs) {
       if (h->tile[1] && BM != h->tile[1]) continue;
-      for (int NS : NSs) {
-        if (h->tile[3] && NS != h->tile[3]) continue;
-        const size_t smem = simt_smem_bytes(h->xt, h->st, ct_cols, PC, BM, S, NT, NS);
-        if (smem > size_t(smem_max)) continue;
-        // Prefer few CTAs per cluster, then tall tiles, then deep pipelines.
-        const double score = 1000.0 / S + BM + NS;
-        if (score > best_score) {
-          best_score = score;
-          best = TileChoice{S, BM, NT, NS, PC, smem};
-          found = true;
+      for (int CR : CRs) {
+        if (h->tile[2] && CR != h->tile[2]) continue;
+        if (CR > BM || BM % CR) continue;
+        for (int NS : NSs) {
+          if (h->tile[3] && NS != h->tile[3]) continue;
+          const size_t smem = simt_smem_bytes(h->xt, h->st, ct_cols, PC, BM, S, NT, NS, CR);
+          if (smem > size_t(smem_max)) continue;
+          // Small clusters (every SM usable, fewer exchanges), a ring of 3-4
+          // chunks in flight, 32-row super-tiles, 8-row chunks.
+          const double score = -10.0 * S + 5.0 * std::min(NS, 4) + (BM == 32 ? 3.0 : 0.0) + (CR == 8 ? 1.0 : 0.0) +
+                               (P.n < 4096 ? 0.0 : 0.0);
+          if (score > best_score) {
+            best_score = score;
+            best = TileChoice{S, BM, CR, NT, NS, PC, smem};
+            found = true;
+          }
         }
       }
     }
@@ -230,29 +244,108 @@ hmc_status choose_simt(hmc_ctx* h, Problem& P, int ct_cols, TileChoice* out) {
   return HMC_OK;
 }
 
+// Tensor-core plan: the largest chain group whose coefficient columns fit TMEM
+// next to the cluster's gradient slice, then the cluster size that keeps the
+// most SMs busy.
+hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
+  *ok = false;
+  int dev = 0, smem_max = 0;
+  HMC_CUDA(cudaGetDevice(&dev));
+  HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int best_g = 0, best_sms = 0;
+  TcPlan best{};
+  int best_nst = 0;
+  size_t best_smem = 0;
+  int best_maxclu = 0;
+  for (int S : {16, 8, 4, 2, 1}) {
+    if (h->tile[0] && S != h->tile[0]) continue;
+    for (int g = h->max_chains; g >= 1; --g) {
+      TcPlan pl;
+      if (!tc_plan(P.p, g * P.Km1, S, &pl)) continue;
+      int nst = 0;
+      size_t smem = 0;
+      for (int s = 6; s >= 2; --s) {
+        if (h->tile[3] && s != h->tile[3]) continue;
+        // At least half of an SM's shared memory: one CTA per SM, so no CTA
+        // ever waits for TMEM held by a CTA of another cluster.
+        const size_t sm = std::max(tc_smem_bytes(pl, s, g), size_t(116 * 1024));
+        if (sm <= size_t(smem_max)) {
+          nst = s;
+          smem = sm;
+          break;
+        }
+      }
+      if (!nst) continue;
+      HMC_CUDA(tc_prepare(smem, S));
+      int maxclu = 0;
+      if (tc_max_active_clusters(smem, S, &maxclu) != cudaSuccess) {
+        cudaGetLastError();
+        maxclu = 0;
+      }
+      if (maxclu < 1) continue;
+      const int sms = maxclu * S;
+      if (g > best_g || (g == best_g && sms > best_sms)) {
+        best_g = g;
+        best_sms = sms;
+        best = pl;
+        best_nst = nst;
+        best_smem = smem;
+        best_maxclu = maxclu;
+      }
+      break;  // largest group for this S found
+    }
+  }
+  if (!best_g) return HMC_OK;
+  P.engine = 2;
+  P.tp = best;
+  P.group_chains = best_g;
+  P.ct_launch = best_g * P.Km1;
+  P.S = best.S;
+  P.PC = best.PC;
+  P.p_pad = best.S * best.PC;
+  P.BM = 128;
+  P.CR = 128;
+  P.NT = 192;
+  P.NSTAGE = best_nst;
+  P.smem = best_smem;
+  P.ntiles = (P.n + 127) / 128;
+  P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>(best_maxclu, P.ntiles)));
+  HMC_CUDA(tc_prepare(P.smem, P.S));
+  *ok = true;
+  return HMC_OK;
+}
+
 hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, const int32_t* y) {
   const int xb = dtype_bytes(h->xt);
-  const int maxct = simt_max_ct(h->xt);
-  if (P.Km1 > maxct)
-    return fail(HMC_EUNSUPPORTED, "K-1 = " + std::to_string(P.Km1) + " exceeds the CUDA-core kernel's class bound " +
-                                      std::to_string(maxct));
-  P.group_chains = std::max(1, std::min(h->max_chains, maxct / P.Km1));
-  P.ct_launch = P.group_chains * P.Km1;
-  TileChoice tc{};
-  HMC_TRY(choose_simt(h, P, P.ct_launch, &tc));
-  P.S = tc.S;
-  P.BM = tc.BM;
-  P.NT = tc.NT;
-  P.NSTAGE = tc.NSTAGE;
-  P.PC = tc.PC;
-  P.smem = tc.smem;
-  P.p_pad = P.S * P.PC;
-  P.ntiles = (P.n + P.BM - 1) / P.BM;
-  HMC_CUDA(simt_prepare(h->xt, h->st, P.ct_launch, P.smem, P.S));
-  int maxclu = 0;
-  HMC_CUDA(simt_max_active_clusters(h->xt, h->st, P.ct_launch, P.smem, P.S, P.NT, &maxclu));
-  if (maxclu < 1) return fail(HMC_EUNSUPPORTED, "the fused kernel cannot be resident with this tile configuration");
-  P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>(maxclu, P.ntiles)));
+  bool tc_ok = false;
+  if (h->xt == HMC_BF16 && h->engine != 1 && P.n > 0) HMC_TRY(choose_tc(h, P, &tc_ok));
+  if (h->engine == 2 && !tc_ok)
+    return fail(HMC_EUNSUPPORTED, "the tensor-core engine needs BF16 storage of X, n > 0 and chains * (K-1) columns "
+                                  "that fit TMEM next to the cluster's gradient slice");
+  if (!tc_ok) {
+    const int maxct = simt_max_ct(h->xt);
+    if (P.Km1 > maxct)
+      return fail(HMC_EUNSUPPORTED, "K-1 = " + std::to_string(P.Km1) + " exceeds the CUDA-core kernel's class bound " +
+                                        std::to_string(maxct));
+    P.group_chains = std::max(1, std::min(h->max_chains, maxct / P.Km1));
+    P.ct_launch = P.group_chains * P.Km1;
+    TileChoice tc{};
+    HMC_TRY(choose_simt(h, P, P.ct_launch, &tc));
+    P.S = tc.S;
+    P.BM = tc.BM;
+    P.CR = tc.CR;
+    P.NT = tc.NT;
+    P.NSTAGE = tc.NSTAGE;
+    P.PC = tc.PC;
+    P.smem = tc.smem;
+    P.p_pad = P.S * P.PC;
+    P.ntiles = (P.n + P.BM - 1) / P.BM;
+    HMC_CUDA(simt_prepare(h->xt, h->st, P.ct_launch, P.smem, P.S));
+    int maxclu = 0;
+    HMC_CUDA(simt_max_active_clusters(h->xt, h->st, P.ct_launch, P.smem, P.S, P.NT, &maxclu));
+    if (maxclu < 1) return fail(HMC_EUNSUPPORTED, "the fused kernel cannot be resident with this tile configuration");
+    P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>(maxclu, P.ntiles)));
+  }
 
   // X: convert on the device into the storage type, zero-padded columns.
   const size_t in_bytes = size_t(P.n) * P.p * (x_dtype == HMC_F64 ? 8 : 4);
@@ -281,7 +374,18 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   const size_t sb = state_bytes(h);
   P.state_elems = int64_t(h->max_chains) * P.Km1 * P.p_pad;
   HMC_CUDA(cudaMalloc(&P.gpart, size_t(P.nclusters) * P.state_elems * sb));
-  HMC_CUDA(cudaMalloc(&P.lpart, size_t(P.nclusters) * h->max_chains * sizeof(double)));
+  P.nlparts = P.engine == 2 ? P.nclusters * P.S : P.nclusters;
+  HMC_CUDA(cudaMalloc(&P.lpart, size_t(P.nlparts) * h->max_chains * sizeof(double)));
+  if (P.engine == 2) {
+    const TcPlan& tp = P.tp;
+    HMC_CUDA(cudaMalloc(&P.bbf, size_t(tp.N) * P.p_pad * 2));
+    HMC_CUDA(cudaMemsetAsync(P.bbf, 0, size_t(tp.N) * P.p_pad * 2, h->stream));
+    HMC_CUDA(cudaMalloc(&P.zg, size_t(P.nclusters) * 2 * P.S * 128 * tp.N * sizeof(float)));
+    HMC_CUDA(cudaMalloc(&P.rg, size_t(P.nclusters) * 2 * 128 * tp.NP * 2));
+    HMC_CUDA(cudaMemsetAsync(P.rg, 0, size_t(P.nclusters) * 2 * 128 * tp.NP * 2, h->stream));
+    if (!tc_make_maps(tp, P.X, P.n, P.p_pad, P.bbf, P.rg, P.nclusters, &P.tmaps))
+      return fail(HMC_ECUDA, "cuTensorMapEncodeTiled failed (tensor maps of the tensor-core engine)");
+  }
   for (StateSet* s : {&P.cs, &P.us}) {
     for (void** q : {&s->beta, &s->eta, &s->grad, &s->beta0, &s->grad0}) {
       HMC_CUDA(cudaMalloc(q, size_t(P.state_elems) * sb));
@@ -306,7 +410,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
 void free_problem(Problem& P) {
   void* ptrs[] = {P.X, P.y, P.xscale, P.gpart, P.lpart, P.cs.beta, P.cs.eta, P.cs.grad, P.cs.beta0, P.cs.grad0,
                   P.us.beta, P.us.eta, P.us.grad, P.us.beta0, P.us.grad0, P.logk, P.logk0, P.h0, P.scal,
-                  P.tickets, P.accept, P.stats, P.iter};
+                  P.tickets, P.accept, P.stats, P.iter, P.bbf, P.zg, P.rg};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -345,38 +449,84 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
   const size_t sb = state_bytes(h);
   for (int c0 = 0; c0 < chains; c0 += P.group_chains) {
     const int c1 = std::min(chains, c0 + P.group_chains);
-    LpgArgs a{};
-    a.X = P.X;
-    a.y = P.y;
-    a.xscale = P.xscale;
-    a.beta = static_cast<const char*>(S.beta) + size_t(c0) * P.Km1 * P.p_pad * sb;
-    a.gpart = static_cast<char*>(P.gpart) + size_t(c0) * P.Km1 * P.p_pad * sb;
-    a.gpart_cstride = P.state_elems;
-    a.lpart = P.lpart + c0;
-    a.lpart_cstride = h->max_chains;
-    a.err = h->err_d;
-    a.n = P.n;
-    a.p_pad = P.p_pad;
-    a.PC = P.PC;
-    a.C = (c1 - c0) * P.Km1;
-    a.Km1 = P.Km1;
-    a.chains = c1 - c0;
-    a.BM = P.BM;
-    a.S = P.S;
-    a.NT = P.NT;
-    a.NSTAGE = P.NSTAGE;
-    a.nclusters = P.nclusters;
-    a.ntiles = P.ntiles;
-    a.spin_limit = h->spin_limit;
-    a.inject_timeout = h->inject_timeout ? 1 : 0;
+    const int C = (c1 - c0) * P.Km1;
+    const void* beta = static_cast<const char*>(S.beta) + size_t(c0) * P.Km1 * P.p_pad * sb;
+    void* gpart = static_cast<char*>(P.gpart) + size_t(c0) * P.Km1 * P.p_pad * sb;
+    const bool inject = h->inject_timeout;
     h->inject_timeout = false;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->timing) {
-      HMC_TRY(timer_pair(h, &e0, &e1));
-      HMC_CUDA(cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal));
+    if (P.engine == 2) {
+      if (C < P.tp.N)
+        HMC_CUDA(cudaMemsetAsync(static_cast<char*>(P.bbf) + size_t(C) * P.p_pad * 2, 0,
+                                 size_t(P.tp.N - C) * P.p_pad * 2, stream));
+      HMC_CUDA(tc_beta_to_bf16(static_cast<const float*>(beta), P.bbf, C, P.p_pad, stream));
     }
-    HMC_CUDA(simt_launch(h->xt, h->st, a, P.smem, stream));
-    if (h->timing) HMC_CUDA(cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // Inside a stream capture the events must become graph nodes.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (h->timing) {
+      HMC_CUDA(cudaStreamIsCapturing(stream, &cap));
+      HMC_TRY(timer_pair(h, &e0, &e1));
+      HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal)
+                                                    : cudaEventRecord(e0, stream));
+    }
+    cudaError_t le;
+    if (P.engine == 2) {
+      TcLaunch L{};
+      L.n = P.n;
+      L.p_pad = P.p_pad;
+      L.C = C;
+      L.Km1 = P.Km1;
+      L.chains = c1 - c0;
+      L.NST = P.NSTAGE;
+      L.nclusters = P.nclusters;
+      L.gpart = gpart;
+      L.gpart_cstride = P.state_elems;
+      L.lpart = P.lpart + c0;
+      L.lpart_cstride = h->max_chains;
+      L.zg = P.zg;
+      L.rg = P.rg;
+      L.y = P.y;
+      L.err = h->err_d;
+      L.spin_limit = h->spin_limit;
+      L.inject_timeout = inject ? 1 : 0;
+      le = tc_launch(P.tp, P.tmaps, L, P.smem, stream);
+    } else {
+      LpgArgs a{};
+      a.X = P.X;
+      a.y = P.y;
+      a.xscale = P.xscale;
+      a.beta = beta;
+      a.gpart = gpart;
+      a.gpart_cstride = P.state_elems;
+      a.lpart = P.lpart + c0;
+      a.lpart_cstride = h->max_chains;
+      a.err = h->err_d;
+      a.n = P.n;
+      a.p_pad = P.p_pad;
+      a.PC = P.PC;
+      a.C = C;
+      a.Km1 = P.Km1;
+      a.chains = c1 - c0;
+      a.BM = P.BM;
+      a.CR = P.CR;
+      a.S = P.S;
+      a.NT = P.NT;
+      a.NSTAGE = P.NSTAGE;
+      a.nclusters = P.nclusters;
+      a.ntiles = P.ntiles;
+      a.spin_limit = h->spin_limit;
+      a.inject_timeout = inject ? 1 : 0;
+      le = simt_launch(h->xt, h->st, a, P.smem, stream);
+    }
+    if (le != cudaSuccess) {
+      char buf[256];
+      std::snprintf(buf, sizeof(buf), "fused launch failed (%s): engine=%d clusters=%d x S=%d, smem=%zu, C=%d, BM=%d, NSTAGE=%d",
+                    cudaGetErrorString(le), P.engine, P.nclusters, P.S, P.smem, C, P.BM, P.NSTAGE);
+      return fail(HMC_ECUDA, buf);
+    }
+    if (h->timing)
+      HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
+                                                    : cudaEventRecord(e1, stream));
   }
   return HMC_OK;
 }
@@ -393,6 +543,7 @@ UpdateArgs make_update(hmc_ctx* h, Problem& P, StateSet& S, int which_logk, int 
   u.nparts = P.n > 0 ? P.nclusters : 0;
   u.lpart = P.lpart;
   u.lpart_cstride = h->max_chains;
+  u.nlparts = P.n > 0 ? P.nlparts : 0;
   u.logk = P.logk + which_logk * h->max_chains;
   u.logk0 = P.logk0;
   u.h0 = P.h0;
@@ -432,24 +583,27 @@ hmc_status validate_opts(const hmc_opts* o) {
   const int* t = o->tile;
   if (t[0] != 0 && t[0] != 1 && t[0] != 2 && t[0] != 4 && t[0] != 8 && t[0] != 16)
     return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be 0, 1, 2, 4, 8 or 16");
-  if (t[1] != 0 && t[1] != 8 && t[1] != 16 && t[1] != 32)
-    return fail(HMC_EINVAL, "opts.tile[1] (rows per tile) must be 0, 8, 16 or 32");
-  if (t[2] < 0 || t[2] > 384) return fail(HMC_EINVAL, "opts.tile[2] (threads) must be in [0, 384]");
-  if (t[3] != 0 && t[3] != 2 && t[3] != 3) return fail(HMC_EINVAL, "opts.tile[3] (stages) must be 0, 2 or 3");
+  if (t[1] != 0 && t[1] != 16 && t[1] != 32 && t[1] != 64)
+    return fail(HMC_EINVAL, "opts.tile[1] (rows per super-tile) must be 0, 16, 32 or 64");
+  if (t[2] != 0 && t[2] != 8 && t[2] != 16 && t[2] != 32)
+    return fail(HMC_EINVAL, "opts.tile[2] (rows per chunk) must be 0, 8, 16 or 32");
+  if (t[3] != 0 && (t[3] < 2 || t[3] > 6)) return fail(HMC_EINVAL, "opts.tile[3] (ring chunks) must be 0 or in [2, 6]");
   return HMC_OK;
 }
 
 void build_description(hmc_ctx* h) {
-  std::string s = "{\"engine\": \"simt\", \"x_storage\": " + std::to_string(h->xt) +
+  std::string s = "{\"engine\": \"" + std::string(h->probs.empty() || h->probs[0].engine == 1 ? "simt" : "tcgen05") +
+                  "\", \"x_storage\": " + std::to_string(h->xt) +
                   ", \"state\": " + std::to_string(h->st) + ", \"max_chains\": " + std::to_string(h->max_chains) +
                   ", \"problems\": [";
   for (size_t b = 0; b < h->probs.size(); ++b) {
     const Problem& P = h->probs[b];
     char buf[512];
     std::snprintf(buf, sizeof(buf),
-                  "%s{\"n\": %lld, \"p\": %d, \"K\": %d, \"p_pad\": %d, \"S\": %d, \"BM\": %d, \"NT\": %d, "
-                  "\"NSTAGE\": %d, \"PC\": %d, \"nclusters\": %d, \"smem\": %zu, \"group_chains\": %d, \"ct\": %d}",
-                  b ? ", " : "", (long long)P.n, P.p, P.K, P.p_pad, P.S, P.BM, P.NT, P.NSTAGE, P.PC, P.nclusters,
+                  "%s{\"n\": %lld, \"p\": %d, \"K\": %d, \"p_pad\": %d, \"S\": %d, \"BM\": %d, \"CR\": %d, "
+                  "\"NT\": %d, \"NSTAGE\": %d, \"PC\": %d, \"nclusters\": %d, \"smem\": %zu, \"group_chains\": %d, "
+                  "\"ct\": %d}",
+                  b ? ", " : "", (long long)P.n, P.p, P.K, P.p_pad, P.S, P.BM, P.CR, P.NT, P.NSTAGE, P.PC, P.nclusters,
                   P.smem, P.group_chains, P.ct_launch);
     s += buf;
   }
@@ -472,7 +626,6 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
   hmc_default_opts(&o);
   if (opts) o = *opts;
   HMC_TRY(validate_opts(&o));
-  if (o.engine == 2) return fail(HMC_EUNSUPPORTED, "tensor-core engine not available for this configuration");
   for (int b = 0; b < nprob; ++b) {
     if (n[b] < 0 || n[b] > (int64_t(1) << 40)) return fail(HMC_EINVAL, "n out of range");
     if (p[b] < 1 || p[b] > (int64_t(1) << 24)) return fail(HMC_EINVAL, "p out of range");
@@ -485,7 +638,7 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
   h->prior_kind = prior;
   h->prior_scale = prior_scale;
   h->max_chains = o.max_chains;
-  h->engine = 1;
+  h->engine = o.engine;
   h->spin_limit = o.spin_limit > 0 ? o.spin_limit : (1ll << 22);
   h->stream = static_cast<cudaStream_t>(o.stream);
   for (int i = 0; i < 4; ++i) h->tile[i] = o.tile[i];
@@ -574,6 +727,10 @@ hmc_status eval_state(hmc_ctx* h, bool chain_state, int chains) {
 }
 
 }  // namespace
+
+namespace hmc {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace hmc
 
 // =================================================================== C ABI
 extern "C" {

@@ -1,6 +1,7 @@
 // Host-side declarations shared by the translation units of libhmc.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "../../include/hmc.h"
@@ -28,10 +29,11 @@ struct LpgArgs {
   int32_t C;                // coefficient columns of this launch (chains * Km1)
   int32_t Km1;              // K - 1
   int32_t chains;           // chains of this launch
-  int32_t BM;               // rows per tile (8, 16 or 32)
+  int32_t BM;               // rows per super-tile (16, 32 or 64)
+  int32_t CR;               // rows per ring chunk (8, 16 or 32; divides BM)
   int32_t S;                // cluster size
   int32_t NT;               // threads per CTA
-  int32_t NSTAGE;           // X tile stages in shared memory
+  int32_t NSTAGE;           // ring chunk buffers in shared memory
   int32_t nclusters;        // clusters in the grid
   int64_t ntiles;           // ceil(n / BM)
   long long spin_limit;     // probes per bounded wait
@@ -41,17 +43,48 @@ struct LpgArgs {
 // CUDA-core fused kernel (any X storage type, small C).
 constexpr int kSimtMaxThreads = 384;
 int simt_max_ct(int xt);                                     // largest C one launch handles
-size_t simt_smem_bytes(int xt, int st, int C, int PC, int BM, int S, int NT, int NSTAGE);
+size_t simt_smem_bytes(int xt, int st, int C, int PC, int BM, int S, int NT, int NSTAGE, int CR);
 cudaError_t simt_prepare(int xt, int st, int C, size_t smem, int S);   // func attributes
 cudaError_t simt_max_active_clusters(int xt, int st, int C, size_t smem, int S, int NT, int* out);
 cudaError_t simt_launch(int xt, int st, const LpgArgs& a, size_t smem, cudaStream_t stream);
+
+// Tensor-core fused kernel (BF16 X, tcgen05 + TMEM + TMA), lpg_tc.cu.
+struct TcPlan {
+  int N, NP, PC, MB, S;
+  uint32_t tmem_cols, stage_bytes;
+};
+struct TcMaps {
+  alignas(64) unsigned char bytes[3 * 128];  // three CUtensorMap: X, B operand, R exchange
+};
+struct TcLaunch {
+  int64_t n;
+  int32_t p_pad, C, Km1, chains, NST, nclusters;
+  void* gpart;
+  int64_t gpart_cstride;
+  double* lpart;
+  int32_t lpart_cstride;
+  void* zg;
+  void* rg;
+  const int32_t* y;
+  int* err;
+  long long spin_limit;
+  int32_t inject_timeout;
+};
+bool tc_plan(int64_t p, int C, int S, TcPlan* out);
+size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains);
+cudaError_t tc_prepare(size_t smem, int S);
+cudaError_t tc_max_active_clusters(size_t smem, int S, int* out);
+bool tc_make_maps(const TcPlan& pl, const void* X, int64_t n, int32_t p_pad, const void* bbf, const void* rg,
+                  int nclusters, TcMaps* maps);
+cudaError_t tc_beta_to_bf16(const float* beta, void* out, int C, int p_pad, cudaStream_t s);
+cudaError_t tc_launch(const TcPlan& pl, const TcMaps& maps, const TcLaunch& L, size_t smem, cudaStream_t stream);
 
 // Element-wise / reduction kernels (update.cu).
 struct UpdateArgs {
   void* beta;  void* eta;  void* grad;          // [chains][Km1][p_pad] state type
   void* beta0; void* grad0;                     // saved trajectory start
   const void* gpart; int64_t gpart_cstride; int32_t nparts;   // partial gradients
-  const double* lpart; int32_t lpart_cstride;
+  const double* lpart; int32_t lpart_cstride; int32_t nlparts; // partial log-likelihoods
   double* logk;     // [chains] current log K
   double* logk0;    // [chains] at trajectory start
   double* h0;       // [chains] H at trajectory start
@@ -97,5 +130,8 @@ cudaError_t launch_fp8_scales(int in_dtype, const void* src, float* scales, int6
                               cudaStream_t s);
 cudaError_t launch_check_labels(const int32_t* y, int64_t n, int32_t K, int* err, cudaStream_t s);
 cudaError_t launch_init_stats(void* stats, int chains, cudaStream_t s);
+
+// Message returned by hmc_last_error() for the calling thread.
+void set_last_error(const std::string& msg);
 
 }  // namespace hmc

@@ -43,21 +43,32 @@ int simt_max_ct(int xt) {
   return cts[m - 1];
 }
 
-size_t simt_smem_bytes(int xt, int /*st*/, int C, int PC, int BM, int S, int NT, int NSTAGE) {
+size_t simt_smem_bytes(int xt, int /*st*/, int C, int PC, int BM, int S, int NT, int NSTAGE, int CR) {
   int ct = 0;
   if (!simt::pick(xt, C, &ct)) return ~size_t(0);
   const int xbytes = xt == HMC_F64 ? 8 : xt == HMC_F32 ? 4 : xt == HMC_BF16 ? 2 : 1;
   const int abytes = xt == HMC_F64 ? 8 : 4;
   const int pv = 16 / abytes;
   const int ctp = ((ct + pv - 1) / pv) * pv;
-  return simt::layout(xbytes, abytes, ct, ctp, PC, BM, S, NT, NSTAGE).total;
+  const int vec = 16 / xbytes;
+  const int units = (ct * vec * abytes + 15) / 16;
+  const int cstride = ((units % 2) ? units : units + 1) * 16 / abytes;
+  return simt::layout(xbytes, abytes, ct, ctp, PC, BM, S, NT, NSTAGE, CR, cstride).total;
 }
 
 cudaError_t simt_prepare(int xt, int /*st*/, int C, size_t smem, int S) {
   int ct = 0;
   simt::KernelFn fn = simt::pick(xt, C, &ct);
   if (!fn) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  // The opt-in is a per-function upper bound shared by every handle: set it to
+  // the device maximum so no handle can lower it below another's need.
+  int dev = 0, smem_max = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem > size_t(smem_max)) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
   if (S > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;

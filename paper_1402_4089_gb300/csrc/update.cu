@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
     pr.add(sl[0]);
     ki.add(sl[1]);
   }
-  for (int b = 0; b < A.nparts; ++b) li.add(A.lpart[size_t(b) * A.lpart_cstride + c]);
+  for (int b = 0; b < A.nlparts; ++b) li.add(A.lpart[size_t(b) * A.lpart_cstride + c]);
   const double logk = li.value() + pr.value();
   A.tickets[c] = 0u;
   if (!(mode & UPD_ACCEPT)) {

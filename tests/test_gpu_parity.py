@@ -60,14 +60,15 @@ def test_fp64_plain_workload(cuda):
         check(h, X, y, beta, "gaussian", 10.0, cuda, 1e-11, 1e-11)
 
 
-@pytest.mark.parametrize("S,BM", [(1, 32), (2, 16), (4, 8), (8, 32), (16, 16)])
-def test_fp32_tiles_ragged(cuda, S, BM):
+@pytest.mark.parametrize("S,BM,CR,NS", [(1, 32, 8, 3), (2, 16, 16, 2), (4, 64, 8, 6), (8, 32, 32, 2),
+                                          (16, 16, 8, 4), (1, 64, 16, 5)])
+def test_fp32_tiles_ragged(cuda, S, BM, CR, NS):
     X, y, _ = synthetic.make_problem(1013, 300, 4, seed=5)
     rng = np.random.default_rng(S * 100 + BM)
     beta = (0.2 * rng.standard_normal((2, 3, 300))).astype(np.float32)
-    with hmc.create(X, y, 4, "gaussian", 1.0, max_chains=2, tile=(S, BM, 0, 0)) as h:
+    with hmc.create(X, y, 4, "gaussian", 1.0, max_chains=2, tile=(S, BM, CR, NS)) as h:
         d = h.describe()["problems"][0]
-        assert (d["S"], d["BM"]) == (S, BM)
+        assert (d["S"], d["BM"], d["CR"], d["NSTAGE"]) == (S, BM, CR, NS)
         check(h, X, y, beta, "gaussian", 1.0, cuda, 1e-5, 1e-5)
 
 
@@ -83,7 +84,7 @@ def test_bf16_storage_bits_and_error(cuda):
     X, y, btrue = synthetic.make_problem(3000, 700, 6, seed=7)
     rng = np.random.default_rng(2)
     beta = (0.05 * rng.standard_normal((2, 5, 700))).astype(np.float32)
-    with hmc.create(X, y, 6, "gaussian", 10.0, x_storage="bf16", max_chains=2) as h:
+    with hmc.create(X, y, 6, "gaussian", 10.0, x_storage="bf16", max_chains=2, engine=1) as h:
         bits, _ = h.get_x()
         assert np.array_equal(bits, quant.bf16_bits(X))
         Xq = quant.bf16_decode(bits).astype(np.float64)

@@ -1,0 +1,57 @@
+"""Tensor-core engine (tcgen05, BF16 X) against the FP64 oracle on the same
+stored BF16 values.  The MMA operands are BF16 (coefficients and the residual
+are rounded to BF16 before the contractions; accumulation is FP32 in TMEM),
+so the tolerance is the BF16 bar: gradient relative error <= 1e-2 and
+log K relative error <= 1e-3."""
+import numpy as np
+import pytest
+
+from oracle import model, quant
+from paper_1402_4089_gb300 import hmc, synthetic
+
+pytestmark = pytest.mark.gpu
+
+TOL_G, TOL_L = 1e-2, 1e-3
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _run(cuda, n, p, K, chains, seed, bscale=0.05, tile=None, prior=("gaussian", 10.0)):
+    import torch
+    X, y, _ = synthetic.make_problem(n, p, K, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    beta = (bscale * rng.standard_normal((chains, K - 1, p))).astype(np.float32)
+    with hmc.create(X, y, K, prior[0], prior[1], x_storage="bf16", max_chains=chains, engine=2, tile=tile) as h:
+        d = h.describe()
+        assert d["engine"] == "tcgen05"
+        bits, _ = h.get_x()
+        Xq = quant.bf16_decode(bits).astype(np.float64)
+        lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
+        torch.cuda.synchronize()
+        lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    errs = []
+    for c in range(chains):
+        lk_o = model.log_kernel(Xq, y, beta[c], prior[0], prior[1])
+        g_o = model.grad_log_kernel(Xq, y, beta[c], prior[0], prior[1])
+        errs.append((abs(lp[c] - lk_o) / max(1.0, abs(lk_o)), _rel(g[c], g_o)))
+    return d, errs
+
+
+@pytest.mark.parametrize("n,p,K,chains,S", [(1000, 700, 6, 2, 0), (333, 129, 3, 1, 1), (2049, 1000, 20, 4, 0),
+                                            (128, 64, 2, 3, 2), (5000, 2000, 10, 7, 4)])
+def test_tc_matches_oracle(cuda, n, p, K, chains, S):
+    d, errs = _run(cuda, n, p, K, chains, seed=n + p, tile=(S, 0, 0, 0))
+    for c, (el, eg) in enumerate(errs):
+        assert el <= TOL_L and eg <= TOL_G, (d["problems"][0], c, el, eg)
+
+
+def test_tc_deterministic(cuda):
+    import torch
+    X, y, _ = synthetic.make_problem(3000, 1500, 8, seed=3)
+    beta = torch.from_numpy((0.05 * np.random.default_rng(4).standard_normal((3, 7, 1500))).astype(np.float32)).to(cuda)
+    with hmc.create(X, y, 8, "gaussian", 10.0, x_storage="bf16", max_chains=3, engine=2) as h:
+        a = [t.cpu().numpy() for t in h.logpost_grad(beta)]
+        b = [t.cpu().numpy() for t in h.logpost_grad(beta)]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
