@@ -225,7 +225,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     h = hmc.create(X if xdt != "f64" else X.astype(np.float64), y, K, kind, scale, x_storage=xdt, state=state,
                    max_chains=chains, stream=stream, tile=tile)
-    desc = h.describe()["problems"][0]
+    desc_all = h.describe()
+    desc = desc_all["problems"][0]
     tdt = torch.float64 if state == "f64" else torch.float32
     seed = 20140217
     zeros = torch.zeros((chains, K - 1, p), dtype=tdt, device=dev)
@@ -269,7 +270,8 @@ def run_ours(args):
     achieved = alg_bytes / avg_launch_s / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
-            "kernel": f"lpg_kernel<{xdt},{c_launch}>", "avg_launch_us": round(avg_launch_s * 1e6, 2),
+            "kernel": ("lpg_tc_kernel (tcgen05)" if h.describe()["engine"] == "tcgen05" else "lpg_kernel (CUDA cores)")
+            + f" X={xdt} C={c_launch}", "avg_launch_us": round(avg_launch_s * 1e6, 2),
             "launches_timed": fused_n, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback 6.8 TB/s"}
 
@@ -314,7 +316,8 @@ def run_ours(args):
         "high-dimensional multinomial setting)", "config": config_of(args, spec, n * p * xb),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
         "xpass_gbs": round(achieved, 1), "accept_rate": round(acc, 4), "impl": "ours",
-        "clocks": clk.summary(),
+        "clocks": clk.summary(), "engine": desc_all["engine"],
+        "tile": {k: desc[k] for k in ("S", "BM", "CR", "NSTAGE", "PC", "nclusters", "group_chains", "smem") if k in desc},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -88,10 +88,7 @@ struct Problem {
   // tensor-core engine
   int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel
   TcPlan tp{};
-  TcMaps tmaps{};
-  void* bbf = nullptr;      // BF16 B operand [N][p_pad]
-  void* zg = nullptr;       // partial-logit exchange [nclu][2][S][128][N]
-  void* rg = nullptr;       // residual exchange [nclu][2][128][NP]
+  void* bbf = nullptr;      // BF16 coefficient operand boxes [p_pad / 64][N x 128 B]
   int nlparts = 0;          // log-likelihood partials reduced per chain
 };
 
@@ -356,12 +353,18 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(cudaMemcpyAsync(tmp, X, in_bytes, cudaMemcpyHostToDevice, h->stream));
     Xd = tmp;
   }
-  HMC_CUDA(cudaMalloc(&P.X, std::max<size_t>(16, size_t(P.n) * P.p_pad * xb)));
+  const int64_t n_alloc = P.engine == 2 ? (P.n + 127) / 128 * 128 : P.n;
+  HMC_CUDA(cudaMalloc(&P.X, std::max<size_t>(16, size_t(n_alloc) * P.p_pad * xb)));
   if (h->xt == HMC_FP8E4M3) {
     HMC_CUDA(cudaMalloc(&P.xscale, size_t(P.p_pad) * sizeof(float)));
     HMC_CUDA(launch_fp8_scales(x_dtype, Xd, P.xscale, P.n, P.p, P.p_pad, h->stream));
   }
-  if (P.n > 0) HMC_CUDA(launch_convert_x(x_dtype, Xd, h->xt, P.X, P.xscale, P.n, P.p, P.p_pad, h->err_d, h->stream));
+  if (P.n > 0) {
+    if (P.engine == 2)
+      HMC_CUDA(tc_x_to_tiles(x_dtype, Xd, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
+    else
+      HMC_CUDA(launch_convert_x(x_dtype, Xd, h->xt, P.X, P.xscale, P.n, P.p, P.p_pad, h->err_d, h->stream));
+  }
   HMC_CUDA(cudaMalloc(&P.y, std::max<size_t>(16, size_t(P.n) * sizeof(int32_t))));
   if (P.n > 0)
     HMC_CUDA(cudaMemcpyAsync(P.y, y, size_t(P.n) * sizeof(int32_t), cudaMemcpyDefault, h->stream));
@@ -380,11 +383,6 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     const TcPlan& tp = P.tp;
     HMC_CUDA(cudaMalloc(&P.bbf, size_t(tp.N) * P.p_pad * 2));
     HMC_CUDA(cudaMemsetAsync(P.bbf, 0, size_t(tp.N) * P.p_pad * 2, h->stream));
-    HMC_CUDA(cudaMalloc(&P.zg, size_t(P.nclusters) * 2 * P.S * 128 * tp.N * sizeof(float)));
-    HMC_CUDA(cudaMalloc(&P.rg, size_t(P.nclusters) * 2 * 128 * tp.NP * 2));
-    HMC_CUDA(cudaMemsetAsync(P.rg, 0, size_t(P.nclusters) * 2 * 128 * tp.NP * 2, h->stream));
-    if (!tc_make_maps(tp, P.X, P.n, P.p_pad, P.bbf, P.rg, P.nclusters, &P.tmaps))
-      return fail(HMC_ECUDA, "cuTensorMapEncodeTiled failed (tensor maps of the tensor-core engine)");
   }
   for (StateSet* s : {&P.cs, &P.us}) {
     for (void** q : {&s->beta, &s->eta, &s->grad, &s->beta0, &s->grad0}) {
@@ -410,7 +408,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
 void free_problem(Problem& P) {
   void* ptrs[] = {P.X, P.y, P.xscale, P.gpart, P.lpart, P.cs.beta, P.cs.eta, P.cs.grad, P.cs.beta0, P.cs.grad0,
                   P.us.beta, P.us.eta, P.us.grad, P.us.beta0, P.us.grad0, P.logk, P.logk0, P.h0, P.scal,
-                  P.tickets, P.accept, P.stats, P.iter, P.bbf, P.zg, P.rg};
+                  P.tickets, P.accept, P.stats, P.iter, P.bbf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -454,12 +452,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     void* gpart = static_cast<char*>(P.gpart) + size_t(c0) * P.Km1 * P.p_pad * sb;
     const bool inject = h->inject_timeout;
     h->inject_timeout = false;
-    if (P.engine == 2) {
-      if (C < P.tp.N)
-        HMC_CUDA(cudaMemsetAsync(static_cast<char*>(P.bbf) + size_t(C) * P.p_pad * 2, 0,
-                                 size_t(P.tp.N - C) * P.p_pad * 2, stream));
-      HMC_CUDA(tc_beta_to_bf16(static_cast<const float*>(beta), P.bbf, C, P.p_pad, stream));
-    }
+    if (P.engine == 2) HMC_CUDA(tc_beta_to_tiles(static_cast<const float*>(beta), P.bbf, C, P.tp.N, P.p_pad, stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     // Inside a stream capture the events must become graph nodes.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -472,6 +465,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     cudaError_t le;
     if (P.engine == 2) {
       TcLaunch L{};
+      L.xs = P.X;
+      L.bs = P.bbf;
       L.n = P.n;
       L.p_pad = P.p_pad;
       L.C = C;
@@ -483,13 +478,11 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       L.gpart_cstride = P.state_elems;
       L.lpart = P.lpart + c0;
       L.lpart_cstride = h->max_chains;
-      L.zg = P.zg;
-      L.rg = P.rg;
       L.y = P.y;
       L.err = h->err_d;
       L.spin_limit = h->spin_limit;
       L.inject_timeout = inject ? 1 : 0;
-      le = tc_launch(P.tp, P.tmaps, L, P.smem, stream);
+      le = tc_launch(P.tp, L, P.smem, stream);
     } else {
       LpgArgs a{};
       a.X = P.X;
@@ -1034,9 +1027,18 @@ hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales) {
   if (!dst) return fail(HMC_EINVAL, "dst is NULL");
   Problem& P = h->probs[b];
   const size_t xb = dtype_bytes(h->xt);
-  if (P.n > 0)
+  if (P.n > 0 && P.engine == 2) {
+    void* tmp = nullptr;
+    HMC_CUDA(cudaMalloc(&tmp, size_t(P.n) * P.p * xb));
+    cudaError_t e = tc_tiles_to_rows(P.X, tmp, P.n, P.p, P.p_pad, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, size_t(P.n) * P.p * xb, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    HMC_CUDA(e);
+  } else if (P.n > 0) {
     HMC_CUDA(cudaMemcpy2DAsync(dst, size_t(P.p) * xb, P.X, size_t(P.p_pad) * xb, size_t(P.p) * xb, size_t(P.n),
                                cudaMemcpyDefault, h->stream));
+  }
   if (scales && P.xscale)
     HMC_CUDA(cudaMemcpyAsync(scales, P.xscale, size_t(P.p) * sizeof(float), cudaMemcpyDefault, h->stream));
   HMC_CUDA(cudaStreamSynchronize(h->stream));

@@ -53,18 +53,15 @@ struct TcPlan {
   int N, NP, PC, MB, S;
   uint32_t tmem_cols, stage_bytes;
 };
-struct TcMaps {
-  alignas(64) unsigned char bytes[3 * 128];  // three CUtensorMap: X, B operand, R exchange
-};
 struct TcLaunch {
+  const void* xs;           // X boxes (tc_x_to_tiles layout)
+  const void* bs;           // coefficient operand boxes (tc_beta_to_tiles layout)
   int64_t n;
   int32_t p_pad, C, Km1, chains, NST, nclusters;
   void* gpart;
   int64_t gpart_cstride;
   double* lpart;
   int32_t lpart_cstride;
-  void* zg;
-  void* rg;
   const int32_t* y;
   int* err;
   long long spin_limit;
@@ -74,10 +71,11 @@ bool tc_plan(int64_t p, int C, int S, TcPlan* out);
 size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains);
 cudaError_t tc_prepare(size_t smem, int S);
 cudaError_t tc_max_active_clusters(size_t smem, int S, int* out);
-bool tc_make_maps(const TcPlan& pl, const void* X, int64_t n, int32_t p_pad, const void* bbf, const void* rg,
-                  int nclusters, TcMaps* maps);
-cudaError_t tc_beta_to_bf16(const float* beta, void* out, int C, int p_pad, cudaStream_t s);
-cudaError_t tc_launch(const TcPlan& pl, const TcMaps& maps, const TcLaunch& L, size_t smem, cudaStream_t stream);
+cudaError_t tc_x_to_tiles(int in_dtype, const void* X, void* out, int64_t n, int32_t p, int32_t p_pad, int* err,
+                          cudaStream_t s);
+cudaError_t tc_tiles_to_rows(const void* tiles, void* out_bits, int64_t n, int32_t p, int32_t p_pad, cudaStream_t s);
+cudaError_t tc_beta_to_tiles(const float* beta, void* out, int C, int N, int p_pad, cudaStream_t s);
+cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStream_t stream);
 
 // Element-wise / reduction kernels (update.cu).
 struct UpdateArgs {

@@ -7,26 +7,30 @@
 // owns the column slice [rank*PC, (rank+1)*PC) (PC a multiple of 128) of X and
 // of the coefficients, and accumulates the gradient rows of that slice in
 // TMEM across all of the cluster's tiles.  Per tile:
-//   sweep 1  TMA brings 128 x 64 boxes of X (128-byte swizzle) together with
-//            the matching 64-column box of the BF16 coefficients; MMA
+//   sweep 1  bulk-async copies bring 128 x 64 boxes of X together with the
+//            matching 64-column box of the BF16 coefficients; MMA
 //            D_z[128 x N] += X_box . B_box^T (both operands K-major).
-//   exchange the epilogue warps read D_z (one row per thread), publish the
-//            CTA's partial logits to global memory (L2), and signal every
-//            peer (remote mbarrier arrive); each CTA then owns 128/S rows:
-//            it sums the S partials in rank order, forms the softmax with the
-//            zero logit of class K, the residual R = Y - P (BF16) and the row
-//            log-likelihood, publishes its R rows and signals again.
-//   sweep 2  TMA loads the tile's full R (128 x N, MN-major) and re-reads X
-//            in 128-column blocks (an L2 hit: the tile was streamed one
-//            sweep earlier); MMA D_g[mb] (128 columns x N) += X_blk^T . R with
-//            X_blk read MN-major from the same swizzled boxes.
+//            X and the coefficient operand are stored in device memory as
+//            the shared-memory image of these boxes (128-byte swizzle already
+//            applied, each box 16 KB contiguous), so every copy is a long
+//            contiguous read.
+//   exchange (distributed shared memory only) the drain warps read D_z, one
+//            row per thread, and push each row with st.async into the shared
+//            memory of the CTA that owns it (rows are split 128/S per CTA);
+//            the owner sums the S partials in rank order, forms the softmax
+//            with the zero logit of class K, the residual R = Y - P (BF16) and
+//            the row log-likelihood, and pushes its R rows with st.async
+//            straight into every peer's MMA operand buffer (swizzled layout).
+//            Completion is counted in mbarrier transaction bytes.
+//   sweep 2  X is re-read in 128-column blocks (an L2 hit: the tile was
+//            streamed one sweep earlier); MMA D_g[mb] (128 columns x N) +=
+//            X_blk^T . R with X_blk read MN-major from the same swizzled boxes
+//            and R MN-major from the operand buffer.
 // Sweeps are interleaved S1(0), S1(1), S2(0), S1(2), S2(1), ... so the
 // exchange of one tile overlaps the next tile's first sweep.
 // Warp roles: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-5
-// epilogue (TMEM lanes 0-127).  All waits are bounded.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
+// drain group (TMEM lanes 0-127; the gradient slice at the end), warps 6-13
+// softmax group.  All waits are bounded.
 #include <algorithm>
 #include <cstring>
 
@@ -36,12 +40,18 @@
 namespace hmc {
 namespace tc {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 448;
+constexpr int kSoftThreads = 256;   // warps 6-13
+constexpr int kLA = 1;           // tiles of lookahead between the two sweeps of a tile
+constexpr int kSlots = 1;        // partial-logit receive slots (reuse gated by a cluster 'consumed' barrier)
+constexpr int kRbuf = 1;         // R operand buffers (reuse gated by a cluster 'free' barrier)
 constexpr int kRows = 128;
 constexpr int kBox = 64;          // BF16 elements per 128-byte box row
 constexpr int kBoxBytes = kRows * 128;
 
 struct TcArgs {
+  const __nv_bfloat16* xs;  // X in swizzled 128 x 64 boxes: [row tile][p_pad / 64][16 KB]
+  const __nv_bfloat16* bs;  // coefficient operand boxes: [p_pad / 64][N rows x 128 B]
   int64_t n;
   int32_t p_pad, PC, S, N, NP, C, Km1, chains, MB, NST, nclusters;
   int64_t ntiles;
@@ -50,8 +60,6 @@ struct TcArgs {
   int64_t gpart_cstride;
   double* lpart;            // [cluster*S + rank][lpart_cstride] partial log-likelihood per chain
   int32_t lpart_cstride;
-  float* zg;                // [nclu][2][S][128][N]
-  __nv_bfloat16* rg;        // [nclu][2][128][NP]
   const int32_t* y;
   int* err;
   long long spin_limit;
@@ -59,18 +67,24 @@ struct TcArgs {
 };
 
 struct Smem {
-  size_t ring, rbuf, lacc, bars, total;
+  size_t ring, rbuf, zx, rloc, lacc, ylab, bars, total;
 };
 
 __host__ __device__ inline size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int NP, int items) {
+// zx: [kSlots][S][RS][N] fp32 partial logits received for the owned rows;
+// rloc: [RS][NP] bf16 residual rows of the owned rows before they are pushed.
+__host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int NP, int N, int S, int chains) {
   Smem L;
+  const int RS = kRows / S;
   size_t off = 0;
   L.ring = off;  off = al(off + size_t(NST) * stage_bytes, 1024);
-  L.rbuf = off;  off = al(off + size_t(NP / kBox) * kBoxBytes, 1024);
-  L.lacc = off;  off = al(off + size_t(items) * 8, 16);
-  L.bars = off;  off = al(off + size_t(2 * NST + 16) * 8 + 16, 16);
+  L.rbuf = off;  off = al(off + kRbuf * size_t(NP / kBox) * kBoxBytes, 1024);
+  L.zx = off;    off = al(off + size_t(kSlots) * kRows * N * 4, 16);
+  L.rloc = off;  off = al(off + size_t(RS) * NP * 2, 16);
+  L.lacc = off;  off = al(off + size_t(RS) * chains * 8, 16);
+  L.ylab = off;  off = al(off + size_t(RS) * 4, 16);
+  L.bars = off;  off = al(off + size_t(2 * NST + 20) * 8 + 16, 16);
   L.total = off + 1024;  // slack for aligning the dynamic base to 1024
   return L;
 }
@@ -85,37 +99,56 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, lon
   return false;
 }
 
-__device__ __forceinline__ void named_bar_epi() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void named_bar_drain() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void named_bar_soft() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+// Named barrier of the softmax group that also ANDs a flag across its threads.
+__device__ __forceinline__ bool named_bar_soft_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 2, 256, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
-    lpg_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB,
-                  const __grid_constant__ CUtensorMap tmR, const TcArgs A) {
+    lpg_tc_kernel(const TcArgs A) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int S = A.S, N = A.N, NST = A.NST;
+  const int S = A.S, N = A.N, NST = A.NST, NP = A.NP;
   const uint32_t rank = (S > 1) ? cluster_rank() : 0u;
   const int cl = blockIdx.x / S;
   const int RS = kRows / S;                        // rows this CTA owns in the exchange
-  const int items = RS * A.chains;
-  const Smem Lo = smem_layout(NST, A.stage_bytes, A.NP, items);
+  const int chains = A.chains, C = A.C, Km1 = A.Km1;
+  const int C8 = (C + 7) / 8;                      // 16-byte chunks of one R row
+  const Smem Lo = smem_layout(NST, A.stage_bytes, NP, N, S, chains);
   unsigned char* ring = smem + Lo.ring;
   unsigned char* rbuf = smem + Lo.rbuf;
+  float* zx = reinterpret_cast<float*>(smem + Lo.zx);
+  __nv_bfloat16* rloc = reinterpret_cast<__nv_bfloat16*>(smem + Lo.rloc);
   double* lacc = reinterpret_cast<double*>(smem + Lo.lacc);
+  int* ylab = reinterpret_cast<int*>(smem + Lo.ylab);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lo.bars);
   uint64_t* full = bars;
   uint64_t* empty = bars + NST;
   uint64_t* zdone = bars + 2 * NST;
   uint64_t* zfree = zdone + 1;
-  uint64_t* zrdy = zdone + 2;    // [2]
-  uint64_t* rrdy = zdone + 4;    // [2]
-  uint64_t* rfull = zdone + 6;
-  uint64_t* rfree = zdone + 7;
-  uint64_t* gdone = zdone + 8;
-  uint64_t* drain = zdone + 9;
-  uint64_t* never = zdone + 10;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(zdone + 11);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(zdone + 12);
+  uint64_t* zrdy = zdone + 2;    // partial logits of the owned rows received
+  uint64_t* zxfree = zdone + 3;  // every owner has consumed the previous tile's partials
+  uint64_t* rfull = zdone + 4;   // [2] every owner's R rows received (R buffer b)
+  uint64_t* rfree = zdone + 6;   // [2] this CTA's gradient sweep finished reading R buffer b
+  uint64_t* rfreec = zdone + 8;  // [2] every CTA's gradient sweep finished reading R buffer b
+  uint64_t* gdone = zdone + 10;
+  uint64_t* drain = zdone + 11;
+  uint64_t* never = zdone + 12;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(zdone + 13);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(zdone + 14);
+  const size_t rbuf_bytes = size_t(NP / kBox) * kBoxBytes;
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -124,22 +157,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(zdone, 1);
     mbar_init(zfree, 4);
-    mbar_init(&zrdy[0], S);
-    mbar_init(&zrdy[1], S);
-    mbar_init(&rrdy[0], S);
-    mbar_init(&rrdy[1], S);
-    mbar_init(rfull, 1);
-    mbar_init(rfree, 1);
+    mbar_init(zrdy, 1);
+    mbar_init(zxfree, S);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&rfull[b], 1);
+      mbar_init(&rfree[b], 1);
+      mbar_init(&rfreec[b], S);
+    }
     mbar_init(gdone, 1);
     mbar_init(drain, 1);
     mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init_cluster();
-    prefetch_tmap(&tmX);
-    prefetch_tmap(&tmB);
-    prefetch_tmap(&tmR);
   }
-  for (int i = tid; i < items; i += kThreads) lacc[i] = 0.0;
+  // R operand buffer and the local R rows start (and stay, past column C) zero.
+  for (size_t i = tid; i < kRbuf * rbuf_bytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(rbuf)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < RS * NP / 8; i += kThreads) reinterpret_cast<uint4*>(rloc)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < RS * chains; i += kThreads) lacc[i] = 0.0;
   if (warp == 1) tmem_alloc(tmem_slot, A.tmem_cols);
   fence_before_sync();
   __syncthreads();
@@ -160,76 +195,72 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t T = (*abort_flag || cl >= A.ntiles) ? 0 : (A.ntiles - 1 - cl) / nclu + 1;
   const int64_t nphase = 2 * T;
   const int NKB = A.PC / kBox;
+  const int64_t nkb_all = A.p_pad / kBox;
+  // Phase k of the sweep order: S1(0..first-1), then pairs S1(v), S2(v-kLA),
+  // then the remaining S2 phases.  Returns the tile; *s2 marks a gradient sweep.
+  const int64_t first = T < kLA ? T : kLA;
   auto phase = [&](int64_t k, bool* s2) -> int64_t {
-    if (k == 0) { *s2 = false; return 0; }
-    if (k == nphase - 1) { *s2 = true; return T - 1; }
-    const int64_t v = (k + 1) / 2;
-    *s2 = (k % 2) == 0;
-    return *s2 ? v - 1 : v;
+    if (k < first) { *s2 = false; return k; }
+    const int64_t k1 = k - first;
+    if (k1 < 2 * (T - first)) {
+      *s2 = (k1 & 1) != 0;
+      return *s2 ? (k1 >> 1) : first + (k1 >> 1);
+    }
+    *s2 = true;
+    return T - first + (k1 - 2 * (T - first));
   };
   auto fail = [&](int bit) {
     *abort_flag = 1;
     atomicOr(A.err, bit);
   };
 
-  int64_t issued = 0;  // producer: ring uses issued
-  int64_t r_loads = 0;
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      int64_t j = 0;
+      int64_t j = 0, issued = 0;
       for (int64_t k = 0; k < nphase && !*abort_flag; ++k) {
         bool s2;
         const int64_t u = phase(k, &s2);
-        const int row0 = int((cl + u * nclu) * kRows);
-        if (!s2) {
-          for (int kb = 0; kb < NKB; ++kb, ++j) {
-            const int st = int(j % NST);
-            if (!wait_bounded(&empty[st], uint32_t(((j / NST) & 1) ^ 1), A.spin_limit, abort_flag, false)) {
-              fail(ERR_TIMEOUT_STAGE);
-              break;
-            }
-            unsigned char* sp = ring + size_t(st) * A.stage_bytes;
+        const int nb = s2 ? A.MB : NKB;
+        for (int b = 0; b < nb; ++b, ++j) {
+          const int st = int(j % NST);
+          if (!wait_bounded(&empty[st], uint32_t(((j / NST) & 1) ^ 1), A.spin_limit, abort_flag, false)) {
+            fail(ERR_TIMEOUT_STAGE);
+            break;
+          }
+          unsigned char* sp = ring + size_t(st) * A.stage_bytes;
+          const int64_t t = cl + u * nclu;  // row tile
+          const unsigned char* xt = reinterpret_cast<const unsigned char*>(A.xs) + size_t(t) * nkb_all * kBoxBytes;
+          if (!s2) {
+            const int kb = int(rank) * NKB + b;
             mbar_arrive_expect_tx(&full[st], uint32_t(kBoxBytes + N * 128));
-            const int c0 = int(rank) * A.PC + kb * kBox;
-            tma_load_2d(sp, &tmX, c0, row0, &full[st]);
-            tma_load_2d(sp + kBoxBytes, &tmB, c0, 0, &full[st]);
-            issued = j + 1;
-          }
-        } else {
-          if (u >= 1 && !wait_bounded(rfree, uint32_t((u - 1) & 1), A.spin_limit, abort_flag, false)) {
-            fail(ERR_TIMEOUT_MMA);
-            break;
-          }
-          if (!wait_bounded(&rrdy[u & 1], uint32_t((u >> 1) & 1), A.spin_limit, abort_flag, true)) {
-            fail(ERR_TIMEOUT_EXCHANGE);
-            break;
-          }
-          fence_proxy_async_global();
-          const int nrb = A.NP / kBox;
-          mbar_arrive_expect_tx(rfull, uint32_t(nrb * kBoxBytes));
-          for (int h = 0; h < nrb; ++h)
-            tma_load_2d(rbuf + size_t(h) * kBoxBytes, &tmR, h * kBox, int((cl * 2 + (u & 1)) * kRows), rfull);
-          r_loads = u + 1;
-          for (int mb = 0; mb < A.MB; ++mb, ++j) {
-            const int st = int(j % NST);
-            if (!wait_bounded(&empty[st], uint32_t(((j / NST) & 1) ^ 1), A.spin_limit, abort_flag, false)) {
-              fail(ERR_TIMEOUT_STAGE);
-              break;
-            }
-            unsigned char* sp = ring + size_t(st) * A.stage_bytes;
+            bulk_g2s(sp, xt + size_t(kb) * kBoxBytes, uint32_t(kBoxBytes), &full[st]);
+            bulk_g2s(sp + kBoxBytes, reinterpret_cast<const unsigned char*>(A.bs) + size_t(kb) * N * 128,
+                     uint32_t(N * 128), &full[st]);
+          } else {
+            const int kb = int(rank) * NKB + 2 * b;
             mbar_arrive_expect_tx(&full[st], uint32_t(2 * kBoxBytes));
-            const int c0 = int(rank) * A.PC + mb * 128;
-            tma_load_2d(sp, &tmX, c0, row0, &full[st]);
-            tma_load_2d(sp + kBoxBytes, &tmX, c0 + kBox, row0, &full[st]);
-            issued = j + 1;
+            bulk_g2s(sp, xt + size_t(kb) * kBoxBytes, uint32_t(2 * kBoxBytes), &full[st]);
           }
+          issued = j + 1;
         }
       }
       // Every copy issued must land before shared memory is released.
       for (int64_t jj = (issued > NST ? issued - NST : 0); jj < issued; ++jj)
         (void)wait_bounded(&full[jj % NST], uint32_t((jj / NST) & 1), A.spin_limit, abort_flag, false);
-      if (r_loads > 0) (void)wait_bounded(rfull, uint32_t((r_loads - 1) & 1), A.spin_limit, abort_flag, false);
+    } else if (lane == 1) {
+      // As soon as this CTA's gradient sweep of tile u has finished reading R
+      // buffer u % kRbuf, tell every CTA that may push the R rows of tile u + kRbuf.
+      for (int64_t u = 0; u + kRbuf < T && !*abort_flag; ++u) {
+        const int b = int(u % kRbuf);
+        if (!wait_bounded(&rfree[b], uint32_t((u / kRbuf) & 1), A.spin_limit, abort_flag, false)) {
+          fail(ERR_TIMEOUT_MMA);
+          break;
+        }
+        fence_after_sync();
+        for (int r = 0; r < S; ++r)
+          mbar_arrive_remote(S > 1 ? map_peer(smem_u32(&rfreec[b]), uint32_t(r)) : smem_u32(&rfreec[b]));
+      }
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
@@ -237,6 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id_s1 = idesc_bf16(kRows, N, false, false);
       const uint32_t id_s2 = idesc_bf16(kRows, N, true, true);
       const uint32_t rb = smem_u32(rbuf);
+      const uint32_t rbytes = uint32_t(kRows) * C8 * 16;
       int64_t j = 0;
       for (int64_t k = 0; k < nphase && !*abort_flag; ++k) {
         bool s2;
@@ -267,8 +299,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (*abort_flag) break;
           mma_commit(zdone);
         } else {
-          if (!wait_bounded(rfull, uint32_t(u & 1), A.spin_limit, abort_flag, false)) {
-            fail(ERR_TIMEOUT_STAGE);
+          const int rbi = int(u % kRbuf);
+          mbar_arrive_expect_tx(&rfull[rbi], rbytes);
+          if (!wait_bounded(&rfull[rbi], uint32_t((u / kRbuf) & 1), A.spin_limit, abort_flag, true)) {
+            fail(ERR_TIMEOUT_EXCHANGE);
             break;
           }
           fence_after_sync();
@@ -284,65 +318,112 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
               const uint64_t ad = smem_desc(xa + 2048u * s, uint32_t(kBoxBytes), 1024u, 2u);
-              const uint64_t bd = smem_desc(rb + 2048u * s, uint32_t(kBoxBytes), 1024u, 2u);
+              const uint64_t bd = smem_desc(rb + uint32_t(rbi * rbuf_bytes) + 2048u * s, uint32_t(kBoxBytes), 1024u, 2u);
               mma_bf16(dcol, ad, bd, id_s2, (u > 0 || s > 0) ? 1u : 0u);
             }
             mma_commit(&empty[st]);
           }
           if (*abort_flag) break;
-          mma_commit(rfree);
+          mma_commit(&rfree[rbi]);
         }
       }
       mma_commit(gdone);
       mma_commit(drain);
       (void)wait_bounded(drain, 0u, A.spin_limit, abort_flag, false);
     }
-  } else {
-    // ---------------------------------------------------------------- epilogue (warps 2-5)
+  } else if (warp < 6) {
+    // ------------------------------------------------ drain group (warps 2-5)
     const int q = warp & 3;                 // TMEM lane quarter of this warp
     const int row = 32 * q + lane;          // tile row (sweep-1 accumulator lane)
     const uint32_t tq = tmem + (uint32_t(32 * q) << 16);
-    const int ew = warp - 2;
-    const int Km1 = A.Km1, chains = A.chains;
+    const uint32_t owner = uint32_t(row / RS), rl = uint32_t(row % RS);
     for (int64_t u = 0; u < T && !*abort_flag; ++u) {
-      const int slot = int(u & 1);
-      const int64_t row0 = (cl + u * nclu) * kRows;
-      bool ok = wait_bounded(zdone, uint32_t(u & 1), A.spin_limit, abort_flag, false);
-      if (!ok) {
+      const int slot = int(u % kSlots);
+      if (!wait_bounded(zdone, uint32_t(u & 1), A.spin_limit, abort_flag, false)) {
         fail(ERR_TIMEOUT_MMA);
         break;
       }
       fence_after_sync();
-      float* zrow = A.zg + ((size_t(cl) * 2 + slot) * S + rank) * kRows * size_t(N) + size_t(row) * N;
+      if (u >= 1 && !wait_bounded(zxfree, uint32_t((u - 1) & 1), A.spin_limit, abort_flag, true)) {
+        fail(ERR_TIMEOUT_SLOT);
+        break;
+      }
+      // This row's partial logits go to the owner's slot [slot][rank][rl].
+      const uint32_t laddr = smem_u32(zx + ((size_t(slot) * S + rank) * RS + rl) * N);
+      const uint32_t raddr = (S > 1) ? map_peer(laddr, owner) : laddr;
+      const uint32_t rbar = (S > 1) ? map_peer(smem_u32(&zrdy[slot]), owner) : smem_u32(&zrdy[slot]);
       for (int c0 = 0; c0 < N; c0 += 16) {
         float v[16];
         tmem_ld16(tq + uint32_t(c0), v);
 #pragma unroll
-        for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4*>(zrow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        for (int e = 0; e < 16; e += 4) st_async_v4f(raddr + uint32_t(c0 + e) * 4u, v[e], v[e + 1], v[e + 2], v[e + 3], rbar);
       }
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive_local(zfree);
-      __threadfence();
-      named_bar_epi();
-      if (ew == 0 && lane < S) mbar_arrive_remote(map_peer(smem_u32(&zrdy[slot]), uint32_t(lane)));
-      ok = wait_bounded(&zrdy[slot], uint32_t((u >> 1) & 1), A.spin_limit, abort_flag, true);
-      if (!ok) {
-        fail(ERR_TIMEOUT_EXCHANGE);
+    }
+    // Drain the gradient accumulators of this CTA's column slice.
+    bool gok = false;
+    if (T > 0 && !*abort_flag) {
+      gok = wait_bounded(gdone, 0u, A.spin_limit, abort_flag, false);
+      if (!gok) fail(ERR_TIMEOUT_MMA);
+    }
+    float* gp = A.gpart + size_t(cl) * A.gpart_cstride;
+    if (gok && !*abort_flag) {
+      fence_after_sync();
+      for (int mb = 0; mb < A.MB; ++mb) {
+        const int col = int(rank) * A.PC + mb * 128 + row;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tmem_ld16(tq + uint32_t(N + mb * N + c0), v);
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (c0 + e < C) gp[size_t(c0 + e) * A.p_pad + col] = v[e];
+        }
+      }
+    } else {
+      for (int mb = 0; mb < A.MB; ++mb) {
+        const int col = int(rank) * A.PC + mb * 128 + row;
+        for (int c = 0; c < C; ++c) gp[size_t(c) * A.p_pad + col] = 0.f;
+      }
+    }
+    fence_before_sync();
+  } else {
+    // --------------------------------------------- softmax group (warps 6-13)
+    const int st = tid - 192;               // 0..255
+    const int sw = warp - 6;                // 0..7
+    const uint32_t rb_local = smem_u32(rbuf);
+    for (int64_t u = 0; u < T && !*abort_flag; ++u) {
+      const int slot = int(u % kSlots);
+      const uint32_t use_par = uint32_t((u / kSlots) & 1);
+      const int64_t row0 = (cl + u * nclu) * kRows;
+      if (st == 0) mbar_arrive_expect_tx(&zrdy[slot], uint32_t(kRows) * N * 4);
+      if (st < RS) {
+        const int64_t grow = row0 + int(rank) * RS + st;
+        ylab[st] = grow < A.n ? __ldg(A.y + grow) : -1;
+      }
+      const bool zok = wait_bounded(&zrdy[slot], use_par, A.spin_limit, abort_flag, true);
+      if (!named_bar_soft_and(zok)) {
+        if (!zok) fail(ERR_TIMEOUT_EXCHANGE);
         break;
       }
-      // Owned rows: sum the S partials in rank order, softmax, residual, log-lik.
-      const float* zs = A.zg + (size_t(cl) * 2 + slot) * S * kRows * size_t(N);
-      __nv_bfloat16* rs = A.rg + (size_t(cl) * 2 + slot) * kRows * size_t(A.NP);
-      for (int it = ew; it < items; it += 4) {
+      // Softmax with the zero logit of class K, residual and row log-likelihood:
+      // one warp per (owned row, chain), lane <-> class; the S partials are
+      // summed in rank order.
+      const float* zsl = zx + size_t(slot) * S * RS * N;
+      for (int it = sw; it < RS * chains; it += 8) {
         const int il = it / chains, c = it - il * chains;
-        const int r = int(rank) * RS + il;
-        const int64_t grow = row0 + r;
-        const bool valid = grow < A.n;
+        const int yi = ylab[il];
+        const bool valid = yi >= 0;
         const int cb = c * Km1;
+        float part[16];
+#pragma unroll
+        for (int pr = 0; pr < 16; ++pr)
+          part[pr] = (lane < Km1 && pr < S) ? zsl[(size_t(pr) * RS + il) * N + cb + lane] : 0.f;
         float z = 0.f;
-        if (lane < Km1)
-          for (int pr = 0; pr < S; ++pr) z += __ldcg(zs + (size_t(pr) * kRows + r) * N + cb + lane);
+#pragma unroll
+        for (int pr = 0; pr < 16; ++pr)
+          if (pr < S) z += part[pr];
         float mx = (lane < Km1) ? fmaxf(z, 0.f) : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -351,50 +432,44 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
         se += expf(-mx);
-        const int yi = valid ? __ldg(A.y + grow) : 0;
-        const float zy = __shfl_sync(0xffffffffu, z, yi < Km1 ? yi : 0);
+        const float zy = __shfl_sync(0xffffffffu, z, (valid && yi < Km1) ? yi : 0);
         if (lane < Km1)
-          rs[size_t(r) * A.NP + cb + lane] = __float2bfloat16_rn(valid ? ((lane == yi ? 1.f : 0.f) - e / se) : 0.f);
-        if (lane == 0 && valid) lacc[it] += double((yi < Km1 ? zy : 0.f) - mx - logf(se));
+          rloc[il * NP + cb + lane] = __float2bfloat16_rn(valid ? ((lane == yi ? 1.f : 0.f) - e / se) : 0.f);
+        if (lane == 0 && valid) lacc[il * chains + c] += double((yi < Km1 ? zy : 0.f) - mx - logf(se));
       }
-      __threadfence();
-      fence_proxy_async_global();
-      named_bar_epi();
-      if (ew == 0 && lane < S) mbar_arrive_remote(map_peer(smem_u32(&rrdy[slot]), uint32_t(lane)));
-    }
-    // Drain the gradient accumulators of this CTA's column slice.
-    bool gok = false;
-    if (T > 0 && !*abort_flag) {
-      gok = wait_bounded(gdone, 0u, A.spin_limit, abort_flag, false);
-      if (!gok) fail(ERR_TIMEOUT_MMA);
-    }
-    if (gok && !*abort_flag) {
-      fence_after_sync();
-      float* gp = A.gpart + size_t(cl) * A.gpart_cstride;
-      for (int mb = 0; mb < A.MB; ++mb) {
-        const int col = int(rank) * A.PC + mb * 128 + row;
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          float v[16];
-          tmem_ld16(tq + uint32_t(N + mb * N + c0), v);
-#pragma unroll
-          for (int e = 0; e < 16; ++e)
-            if (c0 + e < A.C) gp[size_t(c0 + e) * A.p_pad + col] = v[e];
-        }
+      // The partials of tile u are consumed: peers may push tile u + 1.
+      named_bar_soft();
+      if (sw == 1 && lane < S)
+        mbar_arrive_remote(S > 1 ? map_peer(smem_u32(zxfree), uint32_t(lane)) : smem_u32(zxfree));
+      // R buffer b = u % kRbuf: every CTA's gradient sweep of tile u - kRbuf
+      // must be done reading it.
+      const int rbi = int(u % kRbuf);
+      bool fok = true;
+      if (u >= kRbuf && st == 0) {
+        fok = wait_bounded(&rfreec[rbi], uint32_t(((u - kRbuf) / kRbuf) & 1), A.spin_limit, abort_flag, true);
+        if (!fok) fail(ERR_TIMEOUT_EXCHANGE);
       }
-    } else {
-      float* gp = A.gpart + size_t(cl) * A.gpart_cstride;
-      for (int mb = 0; mb < A.MB; ++mb) {
-        const int col = int(rank) * A.PC + mb * 128 + row;
-        for (int c = 0; c < A.C; ++c) gp[size_t(c) * A.p_pad + col] = 0.f;
+      if (!named_bar_soft_and(fok && !*abort_flag)) break;
+      // Push the owned R rows into every peer's operand buffer (MN-major,
+      // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r % 8)).
+      for (int it = st; it < RS * C8 * S; it += kSoftThreads) {
+        const int peer = it % S, rest = it / S;
+        const int c8 = rest % C8, il = rest / C8;
+        const int r = int(rank) * RS + il;
+        const uint4 v = *reinterpret_cast<const uint4*>(rloc + il * NP + c8 * 8);
+        const uint32_t off = uint32_t((c8 >> 3) * kBoxBytes + r * 128 + (((c8 & 7) ^ (r & 7)) << 4));
+        const uint32_t la = rb_local + uint32_t(rbi * rbuf_bytes) + off;
+        const uint32_t ra = (S > 1) ? map_peer(la, uint32_t(peer)) : la;
+        const uint32_t rbar = (S > 1) ? map_peer(smem_u32(&rfull[rbi]), uint32_t(peer)) : smem_u32(&rfull[rbi]);
+        st_async_v4f(ra, __uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w), rbar);
       }
     }
-    fence_before_sync();
-    named_bar_epi();
-    if (ew == 0)
+    named_bar_soft();
+    if (sw == 0)
       for (int c = lane; c < chains; c += 32) {
-        double s = 0.0;
-        for (int il = 0; il < RS; ++il) s += lacc[il * chains + c];
-        A.lpart[(size_t(cl) * S + rank) * A.lpart_cstride + c] = s;
+        double sum = 0.0;
+        for (int il = 0; il < RS; ++il) sum += lacc[il * chains + c];
+        A.lpart[(size_t(cl) * S + rank) * A.lpart_cstride + c] = sum;
       }
   }
   __syncthreads();
@@ -405,37 +480,60 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (S > 1) cluster_sync_all();
 }
 
-// FP32 coefficients [C][p_pad] -> BF16 B operand [N][p_pad] (rows >= C stay zero).
-__global__ void beta_to_bf16_kernel(const float* beta, __nv_bfloat16* out, int C, int p_pad) {
-  const int64_t total = int64_t(C) * p_pad;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x)
-    out[i] = __float2bfloat16_rn(beta[i]);
+// Byte offset of element (row r, column c) of a 128-byte-swizzled box whose
+// rows hold 64 BF16 values: 16-byte chunk (c / 8) is stored at chunk
+// (c / 8) ^ (r % 8).
+__host__ __device__ inline uint32_t sw128_offset(int r, int c) {
+  return uint32_t(r) * 128u + uint32_t(((c >> 3) ^ (r & 7)) << 4) + uint32_t((c & 7) * 2);
 }
 
-// ------------------------------------------------------------------ host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    cudaDriverEntryPointQueryResult q;
-    void* p = nullptr;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+// X (row-major n x p, float or double) -> BF16 boxes of 128 rows x 64 columns
+// in their shared-memory image, [n_pad / 128][p_pad / 64][16 KB]; padding zero.
+template <typename IT>
+__global__ void x_to_tiles_kernel(const IT* X, __nv_bfloat16* out, int64_t n, int32_t p, int32_t p_pad, int64_t n_pad,
+                                  int* err) {
+  const int64_t total = n_pad * p_pad;
+  const int64_t nkb = p_pad / kBox;
+  int bad = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = i / p_pad, col = i - row * p_pad;
+    float v = 0.f;
+    if (row < n && col < p) {
+      const IT x = X[row * p + col];
+      if (!isfinite(double(x))) bad = 1;
+      v = float(x);
+    }
+    const int64_t t = row / kRows, kb = col / kBox;
+    const size_t off = size_t(t * nkb + kb) * kBoxBytes + sw128_offset(int(row % kRows), int(col % kBox));
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(out) + off) = __float2bfloat16_rn(v);
   }
-  return fn;
+  if (bad) atomicOr(err, ERR_NONFINITE_X);
 }
 
-bool make_map_bf16(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                   uint32_t box_outer) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {inner * 2};
-  cuuint32_t box[2] = {box_inner, box_outer};
-  cuuint32_t es[2] = {1, 1};
-  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+// Inverse of x_to_tiles for the stored values (BF16 bits, row-major n x p).
+__global__ void tiles_to_rows_kernel(const __nv_bfloat16* tiles, uint16_t* out, int64_t n, int32_t p, int32_t p_pad) {
+  const int64_t total = n * p;
+  const int64_t nkb = p_pad / kBox;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = i / p, col = i - row * p;
+    const int64_t t = row / kRows, kb = col / kBox;
+    const size_t off = size_t(t * nkb + kb) * kBoxBytes + sw128_offset(int(row % kRows), int(col % kBox));
+    out[i] = *reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(tiles) + off);
+  }
+}
+
+// FP32 coefficients [C][p_pad] -> BF16 operand boxes [p_pad / 64][N rows x 128 B]
+// (rows C..N-1 zero), K-major with the 128-byte swizzle.
+__global__ void beta_to_tiles_kernel(const float* beta, __nv_bfloat16* out, int C, int N, int p_pad) {
+  const int64_t total = int64_t(N) * p_pad;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int k = int(i / p_pad);
+    const int64_t col = i - int64_t(k) * p_pad;
+    const float v = (k < C) ? beta[size_t(k) * p_pad + col] : 0.f;
+    const int64_t kb = col / kBox;
+    const size_t off = size_t(kb) * N * 128 + sw128_offset(k, int(col % kBox));
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(out) + off) = __float2bfloat16_rn(v);
+  }
 }
 
 }  // namespace tc
@@ -461,7 +559,7 @@ bool tc_plan(int64_t p, int C, int S, TcPlan* out) {
 }
 
 size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains) {
-  return tc::smem_layout(NST, pl.stage_bytes, pl.NP, (128 / pl.S) * chains).total;
+  return tc::smem_layout(NST, pl.stage_bytes, pl.NP, pl.N, pl.S, chains).total;
 }
 
 cudaError_t tc_prepare(size_t smem, int S) {
@@ -486,28 +584,37 @@ cudaError_t tc_max_active_clusters(size_t smem, int S, int* out) {
   return cudaOccupancyMaxActiveClusters(out, tc::lpg_tc_kernel, &cfg);
 }
 
-bool tc_make_maps(const TcPlan& pl, const void* X, int64_t n, int32_t p_pad, const void* bbf, const void* rg,
-                  int nclusters, TcMaps* maps) {
-  static_assert(sizeof(TcMaps) >= 3 * sizeof(CUtensorMap), "map storage");
-  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(maps->bytes);
-  if (!tc::make_map_bf16(&m[0], X, uint64_t(p_pad), uint64_t(std::max<int64_t>(n, 1)), tc::kBox, tc::kRows)) return false;
-  if (!tc::make_map_bf16(&m[1], bbf, uint64_t(p_pad), uint64_t(pl.N), tc::kBox, uint32_t(pl.N))) return false;
-  if (!tc::make_map_bf16(&m[2], rg, uint64_t(pl.NP), uint64_t(nclusters) * 2 * tc::kRows, tc::kBox, tc::kRows))
-    return false;
-  return true;
-}
-
-cudaError_t tc_beta_to_bf16(const float* beta, void* out, int C, int p_pad, cudaStream_t s) {
-  const int64_t total = int64_t(C) * p_pad;
-  int g = int(std::min<int64_t>(4096, (total + 255) / 256));
-  if (g < 1) g = 1;
-  tc::beta_to_bf16_kernel<<<g, 256, 0, s>>>(beta, static_cast<__nv_bfloat16*>(out), C, p_pad);
+cudaError_t tc_x_to_tiles(int in_dtype, const void* X, void* out, int64_t n, int32_t p, int32_t p_pad, int* err,
+                          cudaStream_t s) {
+  const int64_t n_pad = (n + tc::kRows - 1) / tc::kRows * tc::kRows;
+  const int g = std::max(1, int(std::min<int64_t>(8192, (n_pad * p_pad + 255) / 256)));
+  if (in_dtype == HMC_F64)
+    tc::x_to_tiles_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(X), static_cast<__nv_bfloat16*>(out), n,
+                                                    p, p_pad, n_pad, err);
+  else
+    tc::x_to_tiles_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(X), static_cast<__nv_bfloat16*>(out), n,
+                                                   p, p_pad, n_pad, err);
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch(const TcPlan& pl, const TcMaps& maps, const TcLaunch& L, size_t smem, cudaStream_t stream) {
-  const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps.bytes);
+cudaError_t tc_tiles_to_rows(const void* tiles, void* out_bits, int64_t n, int32_t p, int32_t p_pad, cudaStream_t s) {
+  const int g = std::max(1, int(std::min<int64_t>(8192, (n * p + 255) / 256)));
+  tc::tiles_to_rows_kernel<<<g, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(tiles), static_cast<uint16_t*>(out_bits),
+                                            n, p, p_pad);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_beta_to_tiles(const float* beta, void* out, int C, int N, int p_pad, cudaStream_t s) {
+  const int64_t total = int64_t(N) * p_pad;
+  const int g = std::max(1, int(std::min<int64_t>(4096, (total + 255) / 256)));
+  tc::beta_to_tiles_kernel<<<g, 256, 0, s>>>(beta, static_cast<__nv_bfloat16*>(out), C, N, p_pad);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStream_t stream) {
   tc::TcArgs a{};
+  a.xs = static_cast<const __nv_bfloat16*>(L.xs);
+  a.bs = static_cast<const __nv_bfloat16*>(L.bs);
   a.n = L.n;
   a.p_pad = L.p_pad;
   a.PC = pl.PC;
@@ -527,8 +634,6 @@ cudaError_t tc_launch(const TcPlan& pl, const TcMaps& maps, const TcLaunch& L, s
   a.gpart_cstride = L.gpart_cstride;
   a.lpart = L.lpart;
   a.lpart_cstride = L.lpart_cstride;
-  a.zg = static_cast<float*>(L.zg);
-  a.rg = static_cast<__nv_bfloat16*>(L.rg);
   a.y = L.y;
   a.err = L.err;
   a.spin_limit = L.spin_limit;
@@ -545,7 +650,7 @@ cudaError_t tc_launch(const TcPlan& pl, const TcMaps& maps, const TcLaunch& L, s
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, tc::lpg_tc_kernel, m[0], m[1], m[2], a);
+  return cudaLaunchKernelEx(&cfg, tc::lpg_tc_kernel, a);
 }
 
 }  // namespace hmc
