@@ -210,6 +210,38 @@ const char* hmc_describe(hmc_handle h);
 hmc_status hmc_set_timing(hmc_handle h, int32_t enable);
 hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launches);
 
+/*
+ * hmc_logpost_grad_noalloc -- log K and its gradient (the quantities of
+ * hmc_logpost_grad) for `chains` coefficient states of one FP32 problem,
+ * computed without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc at call time -- programs that give (nearly) all device memory
+ * to their own pool allocator at start-up, and latency-critical loops that
+ * must not pay cudaMalloc's implicit device synchronisation.  No handle is
+ * used; the caller owns every buffer below (all device memory):
+ *   X        FP32, row-major n x ldx; columns [p, ldx) must be zero.
+ *            ldx >= p and a multiple of 32; a multiple of 512 (up to
+ *            24576) always finds a tile.
+ *   y        int32[n], labels in [0, K) (not validated).
+ *   beta     FP32 [chains][K-1][p]; chains * (K-1) <= 20.
+ *   logpost  double[chains]; grad FP32 [chains][K-1][p].
+ *   stream   cudaStream_t (NULL: legacy default stream).
+ * The library's intermediates live in a 16 MiB static device array that
+ * every GPU loading the library holds until the process exits.  Problems
+ * whose intermediates do not fit are rejected with HMC_EINVAL and a message.
+ * The first call on a device takes that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose GPU
+ * work overlaps (other streams or threads) race on it.  The call does not
+ * allocate (no cudaMalloc, cudaFree or allocating library routine) and is
+ * synchronous: it waits for its stream and returns HMC_ETIMEOUT if a
+ * bounded device wait ran out.
+ */
+hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, const int32_t* y, int64_t n, int64_t p,
+                                    int32_t K, hmc_prior_kind prior, double prior_scale,
+                                    const float* beta, int32_t chains, double* logpost, float* grad,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif
