@@ -58,13 +58,14 @@ def annealing_temperatures(burn_in, t0=1.0e3, r=0.9):
 
 
 def sample(X, y, K, kind, scale, chains, L, eps, iters, seed,
-           beta0=None, iter0=0, temps=None):
+           beta0=None, iter0=0, temps=None, chain0=0):
     """Run `chains` independent HMC chains for `iters` iterations.
 
     eps   : scalar or per-iteration array of step sizes.
     beta0 : (chains, K-1, p) start, zeros if None.
     iter0 : RNG iteration index of the first iteration (counter word 1).
     temps : per-iteration acceptance temperatures (None -> all 1).
+    chain0: RNG chain word of chain 0 (counter word 2 is chain0 + c).
 
     Returns a dict with samples (iters, chains, K-1, p), accept (iters, chains),
     dH = H1 - H0, logk (log K of the state kept), diverged, and the final
@@ -90,11 +91,11 @@ def sample(X, y, K, kind, scale, chains, L, eps, iters, seed,
     for t in range(iters):
         it = iter0 + t
         for c in range(chains):
-            eta0 = philox.momentum_normals(seed, it, c, km1 * p).reshape(km1, p)
+            eta0 = philox.momentum_normals(seed, it, chain0 + c, km1 * p).reshape(km1, p)
             h0 = hamiltonian(logk[c], eta0)
             b1, e1, lk1, g1 = leapfrog(X, y, beta[c], eta0, eps_t[t], L, kind, scale, grad0=grad[c])
             h1 = hamiltonian(lk1, e1)
-            u = philox.accept_uniform(seed, it, c)
+            u = philox.accept_uniform(seed, it, chain0 + c)
             finite = np.isfinite(h1)
             acc = bool(finite and np.log(u) < (h0 - h1) / temp_t[t])
             out_div[t, c] = not finite

@@ -121,6 +121,12 @@ struct hmc_ctx {
   int64_t chain_size = 0;
   int tile[4] = {0, 0, 0, 0};
   bool inject_timeout = false;  // HMC_FAULT=timeout at creation: first fused launch times out
+  // One fused launch for every problem of a batch handle (CUDA-core engine).
+  bool batched = false;
+  int b_S = 1, b_NT = 32, b_CT = 1, b_total_clusters = 0;
+  size_t b_smem = 0;
+  LpgArgs* b_table = nullptr;   // device [2][nprob]: chain state, user scratch
+  int* b_first = nullptr;       // device [nprob + 1] first cluster of each problem
   // Cached graph of one HMC iteration and the parameters baked into it.
   cudaGraphExec_t gexec = nullptr;
   int g_chains = 0, g_L = 0, g_thin = 0;
@@ -509,7 +515,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       a.ntiles = P.ntiles;
       a.spin_limit = h->spin_limit;
       a.inject_timeout = inject ? 1 : 0;
-      le = simt_launch(h->xt, h->st, a, P.smem, stream);
+      le = simt_launch(h->xt, h->st, a, P.smem, stream, P.ct_launch);
     }
     if (le != cudaSuccess) {
       char buf[256];
@@ -521,6 +527,112 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
                                                     : cudaEventRecord(e1, stream));
   }
+  return HMC_OK;
+}
+
+LpgArgs batched_args(hmc_ctx* h, Problem& P, StateSet& S) {
+  LpgArgs a{};
+  a.X = P.X;
+  a.y = P.y;
+  a.xscale = P.xscale;
+  a.beta = S.beta;
+  a.gpart = P.gpart;
+  a.gpart_cstride = P.state_elems;
+  a.lpart = P.lpart;
+  a.lpart_cstride = h->max_chains;
+  a.err = h->err_d;
+  a.n = P.n;
+  a.p_pad = P.p_pad;
+  a.PC = P.PC;
+  a.C = h->max_chains * P.Km1;
+  a.Km1 = P.Km1;
+  a.chains = h->max_chains;
+  a.BM = P.BM;
+  a.CR = P.CR;
+  a.S = h->b_S;
+  a.NT = h->b_NT;
+  a.NSTAGE = P.NSTAGE;
+  a.nclusters = P.nclusters;
+  a.ntiles = P.ntiles;
+  a.spin_limit = h->spin_limit;
+  a.inject_timeout = 0;
+  return a;
+}
+
+// Decide whether every problem of a batch handle can share one fused launch,
+// and if so build the device tables and the cluster split (by work).
+hmc_status setup_batched(hmc_ctx* h) {
+  const int m = int(h->probs.size());
+  if (m < 2) return HMC_OK;
+  int NT = 32, C = 1, S = h->probs[0].S;
+  for (Problem& P : h->probs) {
+    if (P.engine != 1 || P.n == 0 || P.group_chains < h->max_chains || P.S != S) return HMC_OK;
+    NT = std::max(NT, P.NT);
+    C = std::max(C, P.ct_launch);
+  }
+  int dev = 0, smem_max = 0;
+  HMC_CUDA(cudaGetDevice(&dev));
+  HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  size_t smem = 0;
+  for (Problem& P : h->probs)
+    smem = std::max(smem, simt_smem_bytes(h->xt, h->st, C, P.PC, P.BM, S, NT, P.NSTAGE, P.CR));
+  if (smem + 1024 > size_t(smem_max)) return HMC_OK;
+  HMC_CUDA(simt_prepare_batched(h->xt, C, S));
+  int cap = 0;
+  HMC_CUDA(simt_max_active_clusters_batched(h->xt, C, smem, S, NT, &cap));
+  if (cap < 1) return HMC_OK;
+  double total = 0.0;
+  for (Problem& P : h->probs) total += double(P.ntiles) * P.BM * P.PC;
+  std::vector<int> first(m + 1, 0);
+  for (int b = 0; b < m; ++b) {
+    Problem& P = h->probs[b];
+    const double share = double(P.ntiles) * P.BM * P.PC / total;
+    int nc = int(std::lround(share * cap));
+    nc = std::max(1, std::min(nc, P.nclusters));
+    P.nclusters = nc;
+    P.nlparts = nc;
+    first[b + 1] = first[b] + nc;
+  }
+  h->b_S = S;
+  h->b_NT = NT;
+  h->b_CT = C;
+  h->b_smem = smem;
+  h->b_total_clusters = first[m];
+  std::vector<LpgArgs> table(2 * m);
+  for (int b = 0; b < m; ++b) {
+    table[b] = batched_args(h, h->probs[b], h->probs[b].cs);
+    table[m + b] = batched_args(h, h->probs[b], h->probs[b].us);
+  }
+  HMC_CUDA(cudaMalloc(&h->b_table, table.size() * sizeof(LpgArgs)));
+  HMC_CUDA(cudaMalloc(&h->b_first, first.size() * sizeof(int)));
+  HMC_CUDA(cudaMemcpy(h->b_table, table.data(), table.size() * sizeof(LpgArgs), cudaMemcpyHostToDevice));
+  HMC_CUDA(cudaMemcpy(h->b_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice));
+  h->batched = true;
+  return HMC_OK;
+}
+
+// The fused pass for every problem: one launch for a batched handle, else one
+// launch per problem (and per chain group).
+hmc_status run_lpg_all(hmc_ctx* h, bool chain_state, int chains, cudaStream_t stream) {
+  if (!h->batched) {
+    for (Problem& P : h->probs) HMC_TRY(run_lpg(h, P, chain_state ? P.cs : P.us, chains, stream));
+    return HMC_OK;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (h->timing) {
+    HMC_CUDA(cudaStreamIsCapturing(stream, &cap));
+    HMC_TRY(timer_pair(h, &e0, &e1));
+    HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal)
+                                                  : cudaEventRecord(e0, stream));
+  }
+  const int m = int(h->probs.size());
+  const cudaError_t le = simt_launch_batched(h->xt, h->b_CT, h->b_table + (chain_state ? 0 : m), h->b_first, m, chains,
+                                             h->b_total_clusters, h->b_S, h->b_NT, h->b_smem, stream);
+  if (le != cudaSuccess) return fail(HMC_ECUDA, std::string("batched fused launch failed: ") + cudaGetErrorString(le));
+  if (h->timing)
+    HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
+                                                  : cudaEventRecord(e1, stream));
   return HMC_OK;
 }
 
@@ -586,7 +698,8 @@ hmc_status validate_opts(const hmc_opts* o) {
 
 void build_description(hmc_ctx* h) {
   std::string s = "{\"engine\": \"" + std::string(h->probs.empty() || h->probs[0].engine == 1 ? "simt" : "tcgen05") +
-                  "\", \"x_storage\": " + std::to_string(h->xt) +
+                  "\", \"batched_launch\": " + std::string(h->batched ? "true" : "false") +
+                  ", \"x_storage\": " + std::to_string(h->xt) +
                   ", \"state\": " + std::to_string(h->st) + ", \"max_chains\": " + std::to_string(h->max_chains) +
                   ", \"problems\": [";
   for (size_t b = 0; b < h->probs.size(); ++b) {
@@ -655,9 +768,32 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
     P.p = int32_t(p[b]);
     P.K = K[b];
     P.Km1 = K[b] - 1;
+  }
+  // A batch on the CUDA-core engine shares one cluster size (the largest any
+  // problem needs) so that one fused launch can serve every problem.
+  const bool want_batch = nprob > 1 && !(h->xt == HMC_BF16 && h->engine != 1) && !h->tile[0];
+  if (want_batch) {
+    int S = 1;
+    for (Problem& P : h->probs) {
+      const int maxct = simt_max_ct(h->xt);
+      if (P.Km1 > maxct) continue;
+      const int g = std::max(1, std::min(h->max_chains, maxct / P.Km1));
+      TileChoice tc{};
+      Problem probe = P;
+      if (choose_simt(h, probe, g * P.Km1, &tc) == HMC_OK) S = std::max(S, tc.S);
+    }
+    h->tile[0] = S;
+  }
+  for (int b = 0; b < nprob; ++b) {
+    Problem& P = h->probs[b];
     hmc_status s = setup_problem(h, P, X[b], x_dtype, y[b]);
     if (s != HMC_OK) return cleanup(s);
     h->chain_size += int64_t(P.Km1) * P.p;
+  }
+  if (want_batch) {
+    h->tile[0] = 0;
+    hmc_status s = setup_batched(h);
+    if (s != HMC_OK) return cleanup(s);
   }
   build_description(h);
   *out = h;
@@ -709,10 +845,10 @@ hmc_status check_chains(hmc_ctx* h, int chains) {
 
 // log K and gradient at the state in `S` for every problem.
 hmc_status eval_state(hmc_ctx* h, bool chain_state, int chains) {
+  HMC_TRY(run_lpg_all(h, chain_state, chains, h->stream));
   for (size_t b = 0; b < h->probs.size(); ++b) {
     Problem& P = h->probs[b];
     StateSet& S = chain_state ? P.cs : P.us;
-    HMC_TRY(run_lpg(h, P, S, chains, h->stream));
     UpdateArgs u = make_update(h, P, S, chain_state ? 0 : 1, chains, 0.0, int(b));
     HMC_CUDA(launch_reduce_update(h->st, u, UPD_SCALARS, h->stream));
   }
@@ -767,6 +903,8 @@ hmc_status hmc_destroy(hmc_handle h) {
     if (s) cudaFree(s);
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->b_table) cudaFree(h->b_table);
+  if (h->b_first) cudaFree(h->b_first);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return HMC_OK;
@@ -823,14 +961,18 @@ hmc_status hmc_leapfrog(hmc_handle h, void* beta, void* eta, void* grad, double*
     HMC_TRY(pack_all(h, gd, chains, false, &StateSet::grad));
   }
   if (!gd || L == 0) HMC_TRY(eval_state(h, false, chains));
-  for (size_t b = 0; b < h->probs.size() && L > 0; ++b) {
-    Problem& P = h->probs[b];
-    UpdateArgs u = make_update(h, P, P.us, 1, chains, eps, int(b));
-    HMC_CUDA(launch_leap_start(h->st, u, h->stream));
+  if (L > 0) {
+    for (size_t b = 0; b < h->probs.size(); ++b) {
+      UpdateArgs u = make_update(h, h->probs[b], h->probs[b].us, 1, chains, eps, int(b));
+      HMC_CUDA(launch_leap_start(h->st, u, h->stream));
+    }
     for (int l = 1; l <= L; ++l) {
-      HMC_TRY(run_lpg(h, P, P.us, chains, h->stream));
+      HMC_TRY(run_lpg_all(h, false, chains, h->stream));
       const int mode = (l < L) ? (UPD_ETA_FULL | UPD_BETA) : (UPD_ETA_HALF | UPD_SCALARS);
-      HMC_CUDA(launch_reduce_update(h->st, u, mode, h->stream));
+      for (size_t b = 0; b < h->probs.size(); ++b) {
+        UpdateArgs u = make_update(h, h->probs[b], h->probs[b].us, 1, chains, eps, int(b));
+        HMC_CUDA(launch_reduce_update(h->st, u, mode, h->stream));
+      }
     }
   }
   HMC_TRY(unpack_all(h, bd, chains, false, &StateSet::beta));
@@ -918,7 +1060,8 @@ hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double e
       h->timer.used = 0;
       HMC_CUDA(cudaStreamBeginCapture(cst, cudaStreamCaptureModeThreadLocal));
       hmc_status cs = HMC_OK;
-      for (int b = 0; b < nprob && cs == HMC_OK; ++b) {
+      std::vector<UpdateArgs> us(nprob);
+      for (int b = 0; b < nprob; ++b) {
         Problem& P = h->probs[b];
         UpdateArgs u = make_update(h, P, P.cs, 0, chains, eps, b);
         u.temps = use_temps ? h->temps_d : nullptr;
@@ -927,19 +1070,19 @@ hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double e
           u.samples = static_cast<char*>(sd) + size_t(block_offset(h, b, chains)) * sb;
           u.sample_slot_stride = int64_t(chains) * h->chain_size;
         }
-        if (launch_traj_start(h->st, u, cst) != cudaSuccess) {
-          cs = fail(HMC_ECUDA, "traj_start launch failed");
-          break;
-        }
-        for (int l = 1; l <= L && cs == HMC_OK; ++l) {
-          cs = run_lpg(h, P, P.cs, chains, cst);
-          if (cs != HMC_OK) break;
-          const int mode = (l < L) ? (UPD_ETA_FULL | UPD_BETA) : (UPD_ETA_HALF | UPD_SCALARS | UPD_ACCEPT);
-          if (launch_reduce_update(h->st, u, mode, cst) != cudaSuccess) cs = fail(HMC_ECUDA, "reduce launch failed");
-        }
-        if (cs == HMC_OK && launch_select(h->st, u, P.tickets + h->max_chains, cst) != cudaSuccess)
-          cs = fail(HMC_ECUDA, "select launch failed");
+        us[b] = u;
+        if (launch_traj_start(h->st, u, cst) != cudaSuccess) cs = fail(HMC_ECUDA, "traj_start launch failed");
       }
+      for (int l = 1; l <= L && cs == HMC_OK; ++l) {
+        cs = run_lpg_all(h, true, chains, cst);
+        if (cs != HMC_OK) break;
+        const int mode = (l < L) ? (UPD_ETA_FULL | UPD_BETA) : (UPD_ETA_HALF | UPD_SCALARS | UPD_ACCEPT);
+        for (int b = 0; b < nprob && cs == HMC_OK; ++b)
+          if (launch_reduce_update(h->st, us[b], mode, cst) != cudaSuccess) cs = fail(HMC_ECUDA, "reduce launch failed");
+      }
+      for (int b = 0; b < nprob && cs == HMC_OK; ++b)
+        if (launch_select(h->st, us[b], h->probs[b].tickets + h->max_chains, cst) != cudaSuccess)
+          cs = fail(HMC_ECUDA, "select launch failed");
       cudaError_t ce = cudaStreamEndCapture(cst, &graph);
       if (cs != HMC_OK) {
         if (graph) cudaGraphDestroy(graph);

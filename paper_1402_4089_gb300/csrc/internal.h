@@ -46,7 +46,15 @@ int simt_max_ct(int xt);                                     // largest C one la
 size_t simt_smem_bytes(int xt, int st, int C, int PC, int BM, int S, int NT, int NSTAGE, int CR);
 cudaError_t simt_prepare(int xt, int st, int C, size_t smem, int S);   // func attributes
 cudaError_t simt_max_active_clusters(int xt, int st, int C, size_t smem, int S, int NT, int* out);
-cudaError_t simt_launch(int xt, int st, const LpgArgs& a, size_t smem, cudaStream_t stream);
+// C_kernel: the column bound the handle was prepared for (a smaller last chain group
+// still runs that instantiation).
+cudaError_t simt_launch(int xt, int st, const LpgArgs& a, size_t smem, cudaStream_t stream, int C_kernel);
+int simt_ct_of(int xt, int C);                               // class bound of the kernel serving C columns
+// One launch for several problems (table and first on the device; first has nprob + 1 entries).
+cudaError_t simt_prepare_batched(int xt, int C, int S);
+cudaError_t simt_max_active_clusters_batched(int xt, int C, size_t smem, int S, int NT, int* out);
+cudaError_t simt_launch_batched(int xt, int C, const LpgArgs* table, const int* first, int nprob, int chains,
+                                int total_clusters, int S, int NT, size_t smem, cudaStream_t stream);
 
 // Tensor-core fused kernel (BF16 X, tcgen05 + TMEM + TMA), lpg_tc.cu.
 struct TcPlan {

@@ -210,7 +210,7 @@ __host__ __device__ inline Layout layout(int xbytes, int abytes, int CT, int CTP
 }
 
 template <typename XT, typename AT, int CT>
-__global__ void __launch_bounds__(kMaxThreads, 1) lpg_kernel(const LpgArgs A) {
+__device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
   constexpr int VEC = Vec<XT>::N;
   constexpr int PV = Ex<AT, CT>::PV;
   constexpr int CTP = Ex<AT, CT>::CTP;
@@ -220,7 +220,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) lpg_kernel(const LpgArgs A) {
   const int NT = A.NT, NW = NT >> 5;
   const int S = A.S, BM = A.BM, PC = A.PC, NSTAGE = A.NSTAGE, CR = A.CR;
   const uint32_t rank = (S > 1) ? cluster_rank() : 0u;
-  const int cl = blockIdx.x / S;
   const size_t xpitch = size_t(PC) * sizeof(XT) + 16;
   constexpr int CSTR = Coef<AT, CT, VEC>::STRIDE;
   const Layout Lo = layout(sizeof(XT), sizeof(AT), CT, CTP, PC, BM, S, NT, NSTAGE, CR, CSTR);
@@ -532,6 +531,36 @@ __global__ void __launch_bounds__(kMaxThreads, 1) lpg_kernel(const LpgArgs A) {
   }
   if (rank == 0 && tid < A.chains) A.lpart[size_t(cl) * A.lpart_cstride + tid] = lacc;
   if (S > 1) cluster_sync_all();
+}
+
+template <typename XT, typename AT, int CT>
+__global__ void __launch_bounds__(kMaxThreads, 1) lpg_kernel(const LpgArgs A) {
+  lpg_body<XT, AT, CT>(A, int(blockIdx.x) / A.S);
+}
+
+// Several independent problems in one launch: clusters [first[b], first[b+1])
+// of the grid work on problem b (its own X, labels, coefficients, tiles and
+// partial slots); every problem shares the cluster size and block size.
+template <typename XT, typename AT, int CT>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    lpg_kernel_batched(const LpgArgs* __restrict__ table, const int* __restrict__ first, int nprob, int chains) {
+  __shared__ LpgArgs args;
+  __shared__ int cl_local;
+  if (threadIdx.x == 0) {
+    const int S = table[0].S;
+    const int gcl = int(blockIdx.x) / S;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {  // last b with first[b] <= gcl
+      const int mid = (lo + hi + 1) / 2;
+      if (first[mid] <= gcl) lo = mid; else hi = mid - 1;
+    }
+    args = table[lo];
+    args.chains = chains;
+    args.C = chains * args.Km1;
+    cl_local = gcl - first[lo];
+  }
+  __syncthreads();
+  lpg_body<XT, AT, CT>(args, cl_local);
 }
 
 }  // namespace simt

@@ -6,6 +6,30 @@ namespace hmc {
 namespace simt {
 
 using KernelFn = void (*)(const LpgArgs);
+using BatchedFn = void (*)(const LpgArgs*, const int*, int, int);
+int table_batched_f64(const int** cts, const BatchedFn** fns);
+int table_batched_f32(const int** cts, const BatchedFn** fns);
+int table_batched_bf16(const int** cts, const BatchedFn** fns);
+int table_batched_fp8(const int** cts, const BatchedFn** fns);
+
+static BatchedFn pick_batched(int xt, int C, int* ct) {
+  const int* cts;
+  const BatchedFn* fns;
+  int m = 0;
+  switch (xt) {
+    case HMC_F64: m = table_batched_f64(&cts, &fns); break;
+    case HMC_F32: m = table_batched_f32(&cts, &fns); break;
+    case HMC_BF16: m = table_batched_bf16(&cts, &fns); break;
+    default: m = table_batched_fp8(&cts, &fns);
+  }
+  for (int i = 0; i < m; ++i)
+    if (cts[i] >= C) {
+      *ct = cts[i];
+      return fns[i];
+    }
+  *ct = 0;
+  return nullptr;
+}
 int table_f64(const int** cts, const KernelFn** fns);
 int table_f32(const int** cts, const KernelFn** fns);
 int table_bf16(const int** cts, const KernelFn** fns);
@@ -35,6 +59,12 @@ static KernelFn pick(int xt, int C, int* ct) {
 }
 
 }  // namespace simt
+
+int simt_ct_of(int xt, int C) {
+  int ct = 0;
+  simt::pick(xt, C, &ct);
+  return ct;
+}
 
 int simt_max_ct(int xt) {
   const int* cts;
@@ -111,9 +141,51 @@ cudaError_t simt_max_active_clusters(int xt, int /*st*/, int C, size_t smem, int
   return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
 }
 
-cudaError_t simt_launch(int xt, int /*st*/, const LpgArgs& a, size_t smem, cudaStream_t stream) {
+cudaError_t simt_prepare_batched(int xt, int C, int S) {
   int ct = 0;
-  simt::KernelFn fn = simt::pick(xt, a.C, &ct);
+  simt::BatchedFn fn = simt::pick_batched(xt, C, &ct);
+  if (!fn) return cudaErrorInvalidValue;
+  int dev = 0, smem_max = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max - 1024);
+  if (e == cudaSuccess && S > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t simt_max_active_clusters_batched(int xt, int C, size_t smem, int S, int NT, int* out) {
+  int ct = 0;
+  simt::BatchedFn fn = simt::pick_batched(xt, C, &ct);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config(cfg, attr, S, S, NT, smem, nullptr);
+  if (S == 1) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *out = per_sm * sms;
+    return cudaSuccess;
+  }
+  return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
+}
+
+cudaError_t simt_launch_batched(int xt, int C, const LpgArgs* table, const int* first, int nprob, int chains,
+                                int total_clusters, int S, int NT, size_t smem, cudaStream_t stream) {
+  int ct = 0;
+  simt::BatchedFn fn = simt::pick_batched(xt, C, &ct);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config(cfg, attr, total_clusters * S, S, NT, smem, stream);
+  return cudaLaunchKernelEx(&cfg, fn, table, first, nprob, chains);
+}
+
+cudaError_t simt_launch(int xt, int /*st*/, const LpgArgs& a, size_t smem, cudaStream_t stream, int C_kernel) {
+  int ct = 0;
+  simt::KernelFn fn = simt::pick(xt, C_kernel > a.C ? C_kernel : a.C, &ct);
   if (!fn) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];

@@ -183,7 +183,7 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
     a.ntiles = ntiles;
     a.spin_limit = 1ll << 22;
     a.inject_timeout = 0;
-    NA_CUDA(simt_launch(HMC_F32, HMC_F32, a, smem, stream));
+    NA_CUDA(simt_launch(HMC_F32, HMC_F32, a, smem, stream, 0));
   }
   UpdateArgs u{};
   u.beta = bpad;

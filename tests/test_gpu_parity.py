@@ -154,6 +154,7 @@ def test_batch_of_uneven_problems(cuda):
     with hmc.create_batch([pr[0] for pr in probs], [pr[1] for pr in probs], [s[2] for s in shapes],
                           "gaussian", 5.0, max_chains=chains) as h:
         assert h.chain_size == sum((K - 1) * p for (n, p, K) in shapes)
+        assert h.describe()["batched_launch"] is True
         lp, g = h.logpost_grad(flat, chains=chains)
         off = 0
         for b, ((X, y, _), (n, p, K)) in enumerate(zip(probs, shapes)):
@@ -259,3 +260,27 @@ def test_timeout_is_reported_and_handle_recovers(cuda):
         lp, g = h.logpost_grad(beta)          # the handle and the context stay usable
         lk_o, g_o = oracle_lpg(X, y, beta, "gaussian", 1.0)
         assert lk_err(lp[0], lk_o[0]) <= 1e-5 and rel(g[0], g_o[0]) <= 1e-5
+
+
+def test_batch_sampling_matches_oracle(cuda):
+    """Two problems in one handle, one fused launch per leapfrog step; the
+    chains of problem b draw with chain word (b << 32) + c."""
+    import torch
+    shapes = [(400, 30, 3), (250, 45, 4)]
+    probs = [synthetic.make_problem(n, p, K, seed=31, sub=i, dtype=np.float64) for i, (n, p, K) in enumerate(shapes)]
+    chains, iters, L, eps, seed = 2, 6, 8, 0.02, 99
+    with hmc.create_batch([pr[0] for pr in probs], [pr[1] for pr in probs], [s[2] for s in shapes], "cauchy", 1.0,
+                          x_storage="f64", state="f64", max_chains=chains) as h:
+        assert h.describe()["batched_launch"] is True
+        size = chains * h.chain_size
+        samples = torch.empty((iters, size), dtype=torch.float64, device=cuda)
+        b0 = torch.zeros(size, dtype=torch.float64, device=cuda)
+        h.sample(chains, L, eps, iters, seed, beta0=b0, samples=samples)
+        s = samples.cpu().numpy()
+        off = 0
+        for b, ((X, y, _), (n, p, K)) in enumerate(zip(probs, shapes)):
+            blk = chains * (K - 1) * p
+            ref = ohmc.sample(X, y, K, "cauchy", 1.0, chains, L, eps, iters, seed, chain0=b << 32)
+            got = s[:, off:off + blk].reshape(iters, chains, K - 1, p)
+            assert np.max(np.abs(got - ref["samples"])) <= 1e-9
+            off += blk
