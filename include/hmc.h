@@ -71,7 +71,8 @@ typedef struct {
   int32_t engine;         /* 0 auto, 1 CUDA-core fused kernel, 2 tensor-core fused kernel */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
-  int32_t tile[4];        /* {cluster size, rows per super-tile, rows per chunk, ring chunks}; 0 = chosen */
+  int32_t tile[4];        /* {cluster size, 0, 0, ring slots}; 0 = chosen (entries 1, 2 reserved, must be 0
+                             on the CUDA-core engine) */
 } hmc_opts;
 
 /* Per-chain counters of hmc_sample (host memory, one entry per chain). */
@@ -220,8 +221,8 @@ hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launch
  * must not pay cudaMalloc's implicit device synchronisation.  No handle is
  * used; the caller owns every buffer below (all device memory):
  *   X        FP32, row-major n x ldx; columns [p, ldx) must be zero.
- *            ldx >= p and a multiple of 32; a multiple of 512 (up to
- *            24576) always finds a tile.
+ *            ldx >= p and a multiple of 16; a multiple of 256 (up to
+ *            20480) always finds a tile.
  *   y        int32[n], labels in [0, K) (not validated).
  *   beta     FP32 [chains][K-1][p]; chains * (K-1) <= 20.
  *   logpost  double[chains]; grad FP32 [chains][K-1][p].

@@ -69,7 +69,7 @@ struct Problem {
   int32_t* y = nullptr;
   float* xscale = nullptr;
   // fused-pass configuration
-  int S = 1, BM = 32, CR = 8, NT = 32, NSTAGE = 2, PC = 32, nclusters = 1, ct_launch = 1, group_chains = 1;
+  int S = 1, BM = 32, CR = 8, NT = 32, NWL = 1, NSTAGE = 2, PC = 32, nclusters = 1, ct_launch = 1, group_chains = 1;
   size_t smem = 0;
   int64_t ntiles = 0;
   void* gpart = nullptr;
@@ -123,7 +123,7 @@ struct hmc_ctx {
   bool inject_timeout = false;  // HMC_FAULT=timeout at creation: first fused launch times out
   // One fused launch for every problem of a batch handle (CUDA-core engine).
   bool batched = false;
-  int b_S = 1, b_NT = 32, b_CT = 1, b_total_clusters = 0;
+  int b_S = 1, b_NT = 32, b_NWL = 1, b_CT = 1, b_total_clusters = 0;
   size_t b_smem = 0;
   LpgArgs* b_table = nullptr;   // device [2][nprob]: chain state, user scratch
   int* b_first = nullptr;       // device [nprob + 1] first cluster of each problem
@@ -196,56 +196,7 @@ hmc_status check_device_error(hmc_ctx* h) {
 }
 
 // ------------------------------------------------------------- configuration
-struct TileChoice {
-  int S, BM, CR, NT, NSTAGE, PC;
-  size_t smem;
-};
-
 int round_up(int64_t v, int64_t m) { return int((v + m - 1) / m * m); }
-
-hmc_status choose_simt(hmc_ctx* h, Problem& P, int ct_cols, TileChoice* out) {
-  int dev = 0, smem_max = 0;
-  HMC_CUDA(cudaGetDevice(&dev));
-  HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int Ss[] = {1, 2, 4, 8, 16};
-  const int BMs[] = {32, 64, 16};
-  const int CRs[] = {8, 16, 32};
-  const int NSs[] = {6, 5, 4, 3, 2};
-  bool found = false;
-  TileChoice best{};
-  double best_score = -1e30;
-  for (int S : Ss) {
-    if (h->tile[0] && S != h->tile[0]) continue;
-    int PC = round_up((P.p + S - 1) / S, 32);
-    if (PC < 32) PC = 32;
-    const int NT = round_up(std::max(32, PC / 4), 32);
-    if (NT > kSimtMaxThreads || PC > 4 * NT) continue;
-    for (int BM : BMs) {
-      if (h->tile[1] && BM != h->tile[1]) continue;
-      for (int CR : CRs) {
-        if (h->tile[2] && CR != h->tile[2]) continue;
-        if (CR > BM || BM % CR) continue;
-        for (int NS : NSs) {
-          if (h->tile[3] && NS != h->tile[3]) continue;
-          const size_t smem = simt_smem_bytes(h->xt, h->st, ct_cols, PC, BM, S, NT, NS, CR);
-          if (smem > size_t(smem_max)) continue;
-          // Small clusters (every SM usable, fewer exchanges), a ring of 3-4
-          // chunks in flight, 32-row super-tiles, 8-row chunks.
-          const double score = -10.0 * S + 5.0 * std::min(NS, 4) + (BM == 32 ? 3.0 : 0.0) + (CR == 8 ? 1.0 : 0.0) +
-                               (P.n < 4096 ? 0.0 : 0.0);
-          if (score > best_score) {
-            best_score = score;
-            best = TileChoice{S, BM, CR, NT, NS, PC, smem};
-            found = true;
-          }
-        }
-      }
-    }
-  }
-  if (!found) return fail(HMC_EUNSUPPORTED, "no CUDA-core tile configuration fits this problem (p too large for the cluster sizes available)");
-  *out = best;
-  return HMC_OK;
-}
 
 // Tensor-core plan: the largest chain group whose coefficient columns fit TMEM
 // next to the cluster's gradient slice, then the cluster size that keeps the
@@ -332,21 +283,24 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
                                         std::to_string(maxct));
     P.group_chains = std::max(1, std::min(h->max_chains, maxct / P.Km1));
     P.ct_launch = P.group_chains * P.Km1;
-    TileChoice tc{};
-    HMC_TRY(choose_simt(h, P, P.ct_launch, &tc));
+    if (h->tile[1] || h->tile[2])
+      return fail(HMC_EINVAL, "tile[1] and tile[2] must be 0 on the CUDA-core engine (8-row super-tiles)");
+    P.ntiles = (P.n + 7) / 8;
+    SimtTile tc{};
+    HMC_CUDA(simt_choose(h->xt, P.ct_launch, P.p, P.ntiles, h->tile[0], h->tile[3], 0, &tc));
+    if (!tc.S)
+      return fail(HMC_EUNSUPPORTED, "no CUDA-core tile configuration fits this problem (p too large for the cluster sizes "
+                                    "available, or the requested tile does not fit)");
     P.S = tc.S;
-    P.BM = tc.BM;
-    P.CR = tc.CR;
+    P.BM = 8;
+    P.CR = 8;
     P.NT = tc.NT;
+    P.NWL = tc.NWL;
     P.NSTAGE = tc.NSTAGE;
     P.PC = tc.PC;
     P.smem = tc.smem;
     P.p_pad = P.S * P.PC;
-    P.ntiles = (P.n + P.BM - 1) / P.BM;
-    HMC_CUDA(simt_prepare(h->xt, h->st, P.ct_launch, P.smem, P.S));
-    int maxclu = 0;
-    HMC_CUDA(simt_max_active_clusters(h->xt, h->st, P.ct_launch, P.smem, P.S, P.NT, &maxclu));
-    if (maxclu < 1) return fail(HMC_EUNSUPPORTED, "the fused kernel cannot be resident with this tile configuration");
+    const int maxclu = tc.maxclu;
     P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>(maxclu, P.ntiles)));
   }
 
@@ -510,6 +464,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       a.CR = P.CR;
       a.S = P.S;
       a.NT = P.NT;
+      a.NWL = P.NWL;
       a.NSTAGE = P.NSTAGE;
       a.nclusters = P.nclusters;
       a.ntiles = P.ntiles;
@@ -551,6 +506,7 @@ LpgArgs batched_args(hmc_ctx* h, Problem& P, StateSet& S) {
   a.CR = P.CR;
   a.S = h->b_S;
   a.NT = h->b_NT;
+  a.NWL = h->b_NWL;
   a.NSTAGE = P.NSTAGE;
   a.nclusters = P.nclusters;
   a.ntiles = P.ntiles;
@@ -564,18 +520,21 @@ LpgArgs batched_args(hmc_ctx* h, Problem& P, StateSet& S) {
 hmc_status setup_batched(hmc_ctx* h) {
   const int m = int(h->probs.size());
   if (m < 2) return HMC_OK;
-  int NT = 32, C = 1, S = h->probs[0].S;
+  int NWC = 1, C = 1, S = h->probs[0].S;
   for (Problem& P : h->probs) {
     if (P.engine != 1 || P.n == 0 || P.group_chains < h->max_chains || P.S != S) return HMC_OK;
-    NT = std::max(NT, P.NT);
+    NWC = std::max(NWC, (P.PC + 127) / 128);
     C = std::max(C, P.ct_launch);
   }
+  if (NWC > simt_max_grad_warps(h->xt, C)) return HMC_OK;
+  const int NWL = simt_logit_warps(NWC);
+  const int NT = 32 * (NWC + NWL + 1);
   int dev = 0, smem_max = 0;
   HMC_CUDA(cudaGetDevice(&dev));
   HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   size_t smem = 0;
   for (Problem& P : h->probs)
-    smem = std::max(smem, simt_smem_bytes(h->xt, h->st, C, P.PC, P.BM, S, NT, P.NSTAGE, P.CR));
+    smem = std::max(smem, simt_smem_bytes(h->xt, h->st, C, P.PC, S, NWL, P.NSTAGE));
   if (smem + 1024 > size_t(smem_max)) return HMC_OK;
   HMC_CUDA(simt_prepare_batched(h->xt, C, S));
   int cap = 0;
@@ -595,6 +554,7 @@ hmc_status setup_batched(hmc_ctx* h) {
   }
   h->b_S = S;
   h->b_NT = NT;
+  h->b_NWL = NWL;
   h->b_CT = C;
   h->b_smem = smem;
   h->b_total_clusters = first[m];
@@ -773,14 +733,13 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
   // problem needs) so that one fused launch can serve every problem.
   const bool want_batch = nprob > 1 && !(h->xt == HMC_BF16 && h->engine != 1) && !h->tile[0];
   if (want_batch) {
+    // Smallest cluster whose column slices fit the block for every problem.
     int S = 1;
     for (Problem& P : h->probs) {
       const int maxct = simt_max_ct(h->xt);
-      if (P.Km1 > maxct) continue;
-      const int g = std::max(1, std::min(h->max_chains, maxct / P.Km1));
-      TileChoice tc{};
-      Problem probe = P;
-      if (choose_simt(h, probe, g * P.Km1, &tc) == HMC_OK) S = std::max(S, tc.S);
+      const int g = std::max(1, std::min(h->max_chains, maxct / std::max(1, P.Km1)));
+      const int64_t cols = int64_t(128) * simt_max_grad_warps(h->xt, std::min(maxct, g * P.Km1));
+      while (S < 16 && (int64_t(P.p) + S - 1) / S > cols) S *= 2;
     }
     h->tile[0] = S;
   }

@@ -29,27 +29,43 @@ struct LpgArgs {
   int32_t C;                // coefficient columns of this launch (chains * Km1)
   int32_t Km1;              // K - 1
   int32_t chains;           // chains of this launch
-  int32_t BM;               // rows per super-tile (16, 32 or 64)
-  int32_t CR;               // rows per ring chunk (8, 16 or 32; divides BM)
+  int32_t BM;               // rows per super-tile (8 on the CUDA-core engine)
+  int32_t CR;               // unused by the CUDA-core engine (kept equal to BM)
   int32_t S;                // cluster size
-  int32_t NT;               // threads per CTA
-  int32_t NSTAGE;           // ring chunk buffers in shared memory
+  int32_t NT;               // threads per CTA (consumer warps + 1 producer warp)
+  int32_t NSTAGE;           // ring slots (super-tiles) in shared memory
   int32_t nclusters;        // clusters in the grid
   int64_t ntiles;           // ceil(n / BM)
   long long spin_limit;     // probes per bounded wait
   int32_t inject_timeout;   // 1: wait on a barrier nothing arrives at (host-side fault injection)
+  int32_t NWL;              // CUDA-core engine: logit warps (the rest but one are gradient warps)
 };
 
 // CUDA-core fused kernel (any X storage type, small C).
-constexpr int kSimtMaxThreads = 384;
+constexpr int kSimtMaxThreads = 512;   // up to 10 gradient + 5 logit + 1 producer warps
 int simt_max_ct(int xt);                                     // largest C one launch handles
-size_t simt_smem_bytes(int xt, int st, int C, int PC, int BM, int S, int NT, int NSTAGE, int CR);
+// Shared memory of one CTA: PC columns, cluster size S, NWL logit warps, NSTAGE ring slots.
+size_t simt_smem_bytes(int xt, int st, int C, int PC, int S, int NWL, int NSTAGE);
 cudaError_t simt_prepare(int xt, int st, int C, size_t smem, int S);   // func attributes
+// Tile of the CUDA-core pass: cluster size S (CTA column slice PC, a multiple
+// of 16), NWC gradient warps (one per 32 column quads), NWL logit warps,
+// NSTAGE ring slots; NT = 32 * (NWC + NWL + 1) threads.
+struct SimtTile {
+  int S, PC, NWC, NWL, NT, NSTAGE;
+  size_t smem;
+  int maxclu;   // clusters resident at once
+};
+// Picks the tile keeping the most SMs streaming X (S = 0 in *out: none fits).
+// force_S / force_NS: 0 = free.  exact_ld > 0: S * PC must equal it.
+cudaError_t simt_choose(int xt, int C, int64_t p, int64_t ntiles, int force_S, int force_NS, int64_t exact_ld,
+                        SimtTile* out);
 cudaError_t simt_max_active_clusters(int xt, int st, int C, size_t smem, int S, int NT, int* out);
 // C_kernel: the column bound the handle was prepared for (a smaller last chain group
 // still runs that instantiation).
 cudaError_t simt_launch(int xt, int st, const LpgArgs& a, size_t smem, cudaStream_t stream, int C_kernel);
 int simt_ct_of(int xt, int C);                               // class bound of the kernel serving C columns
+int simt_max_grad_warps(int xt, int C);                      // gradient warps the kernel allows
+int simt_logit_warps(int nwc);                               // logit warps paired with nwc gradient warps
 // One launch for several problems (table and first on the device; first has nprob + 1 entries).
 cudaError_t simt_prepare_batched(int xt, int C, int S);
 cudaError_t simt_max_active_clusters_batched(int xt, int C, size_t smem, int S, int NT, int* out);

@@ -6,23 +6,32 @@
 // reading every element of X from HBM once.
 //
 // Work decomposition (GB300): a thread-block cluster of S CTAs walks
-// super-tiles of BM rows; CTA `rank` owns the column slice
-// [rank*PC, (rank+1)*PC) of X and of the coefficients.  X reaches shared
-// memory through a ring of NSTAGE chunk buffers (CR rows x PC columns each,
-// bulk-async copies completing on mbarriers).  Each super-tile is swept twice:
-//   sweep 1 (logits): lane <-> row of the chunk, warps split the slice's
-//      columns, coefficients broadcast from shared memory; after the last
-//      chunk a fixed-order cross-warp sum gives the CTA's partial logits,
-//      which are pushed into every peer's exchange slot (st.async completing
-//      on the peer's mbarrier);
-//   sweep 2 (gradient): every CTA sums the S partials in rank order (so all
-//      CTAs hold identical logits), forms the softmax with the fixed zero
-//      logit of class K, the residual R = Y - P and the row log-likelihood,
-//      then re-reads the super-tile's chunks (an L2 hit: they were streamed a
-//      moment earlier) and accumulates X^T R in registers (thread <-> 4
-//      columns), across all super-tiles of the cluster, without atomics.
-// Sweeps are interleaved S1(0), S1(1), S2(0), S1(2), S2(1), ... so the
-// exchange of one super-tile completes while the next one's logits are formed.
+// super-tiles of BM = 8 rows; CTA `rank` owns the column slice
+// [rank*PC, (rank+1)*PC) of X and of the coefficients.  Inside a CTA three
+// warp roles run their own loops over the cluster's tiles, handing tiles
+// over through mbarriers:
+//   producer (1 warp): bulk-async copies of each tile's slice into a ring
+//      of NSTAGE shared-memory slots, with bulk L2 prefetches further ahead;
+//   logit group (NWL warps): sweep 1 -- lane = (row group a, phase c) holds
+//      R rows and visits the quads (4 columns) c, c+P, ... of the 32-quad
+//      spans of its warp, so each coefficient vector loaded from shared memory
+//      feeds R rows; a shuffle reduce-scatter over the P phases and a
+//      fixed-order sum over warps give the CTA's partial logits, pushed into
+//      every peer's exchange slot (st.async completing on the peer's
+//      mbarrier);
+//   gradient group (NWC warps, one per span): once every CTA's partials of a tile have
+//      arrived, sums the S partials in rank order (so all CTAs hold identical
+//      logits), forms the softmax with the fixed zero logit of class K, the
+//      residual R = Y - P and the row log-likelihood, then thread <-> quad
+//      accumulates X^T R in registers across all tiles of the cluster,
+//      without atomics, and returns the slot to the producer.
+// The logit group runs ahead (up to the ring depth) while the gradient group
+// finishes earlier tiles, so the exchange, softmax and both sweeps of
+// different tiles overlap.
+//
+// Every wait is bounded.  A wait that runs out records an error bit and the
+// role carries on (later waits are skipped), so all barriers stay matched,
+// every copy in flight lands, and the kernel returns.
 #pragma once
 #include "device_common.cuh"
 #include "internal.h"
@@ -30,26 +39,8 @@
 namespace hmc {
 namespace simt {
 
-constexpr int kMaxThreads = kSimtMaxThreads;
-
-template <typename XT>
-struct Vec;
-template <>
-struct Vec<double> {
-  static constexpr int N = 2;
-};
-template <>
-struct Vec<float> {
-  static constexpr int N = 4;
-};
-template <>
-struct Vec<__nv_bfloat16> {
-  static constexpr int N = 8;
-};
-template <>
-struct Vec<__nv_fp8_e4m3> {
-  static constexpr int N = 16;
-};
+constexpr int kMaxThreads = kSimtMaxThreads;   // 2 x 7 consumer warps + producer
+constexpr int kBM = 8;   // rows per super-tile
 
 __device__ __forceinline__ float bf16lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
@@ -61,73 +52,36 @@ __device__ __forceinline__ void fp8x2(uint32_t two, float& a, float& b) {
   b = f.y;
 }
 
-// 16 bytes of X (shared memory, 16-byte aligned) -> Vec<XT>::N values.
+// 4 consecutive elements of X in shared memory (aligned to 4 elements).
 template <typename XT, typename AT>
-__device__ __forceinline__ void load16(const unsigned char* p, AT* o);
+__device__ __forceinline__ void load_quad(const unsigned char* p, AT* o);
 
 template <>
-__device__ __forceinline__ void load16<double, double>(const unsigned char* p, double* o) {
-  const double2 v = *reinterpret_cast<const double2*>(p);
-  o[0] = v.x;
-  o[1] = v.y;
-}
-template <>
-__device__ __forceinline__ void load16<float, float>(const unsigned char* p, float* o) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  o[0] = v.x;
-  o[1] = v.y;
-  o[2] = v.z;
-  o[3] = v.w;
-}
-template <>
-__device__ __forceinline__ void load16<__nv_bfloat16, float>(const unsigned char* p, float* o) {
-  const uint4 v = *reinterpret_cast<const uint4*>(p);
-  o[0] = bf16lo(v.x); o[1] = bf16hi(v.x);
-  o[2] = bf16lo(v.y); o[3] = bf16hi(v.y);
-  o[4] = bf16lo(v.z); o[5] = bf16hi(v.z);
-  o[6] = bf16lo(v.w); o[7] = bf16hi(v.w);
-}
-template <>
-__device__ __forceinline__ void load16<__nv_fp8_e4m3, float>(const unsigned char* p, float* o) {
-  const uint4 v = *reinterpret_cast<const uint4*>(p);
-  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    fp8x2(w[q], o[4 * q + 0], o[4 * q + 1]);
-    fp8x2(w[q] >> 16, o[4 * q + 2], o[4 * q + 3]);
-  }
-}
-
-// 4 consecutive elements of X (aligned to 4 elements).
-template <typename XT, typename AT>
-__device__ __forceinline__ void load4(const unsigned char* p, AT* o);
-
-template <>
-__device__ __forceinline__ void load4<double, double>(const unsigned char* p, double* o) {
+__device__ __forceinline__ void load_quad<double, double>(const unsigned char* p, double* o) {
   const double2 a = *reinterpret_cast<const double2*>(p);
   const double2 b = *reinterpret_cast<const double2*>(p + 16);
   o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 template <>
-__device__ __forceinline__ void load4<float, float>(const unsigned char* p, float* o) {
+__device__ __forceinline__ void load_quad<float, float>(const unsigned char* p, float* o) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
 }
 template <>
-__device__ __forceinline__ void load4<__nv_bfloat16, float>(const unsigned char* p, float* o) {
+__device__ __forceinline__ void load_quad<__nv_bfloat16, float>(const unsigned char* p, float* o) {
   const uint2 v = *reinterpret_cast<const uint2*>(p);
   o[0] = bf16lo(v.x); o[1] = bf16hi(v.x); o[2] = bf16lo(v.y); o[3] = bf16hi(v.y);
 }
 template <>
-__device__ __forceinline__ void load4<__nv_fp8_e4m3, float>(const unsigned char* p, float* o) {
+__device__ __forceinline__ void load_quad<__nv_fp8_e4m3, float>(const unsigned char* p, float* o) {
   const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
   fp8x2(v, o[0], o[1]);
   fp8x2(v >> 16, o[2], o[3]);
 }
 
-// N consecutive coefficient values from shared memory (16-byte aligned).
+// N consecutive values of the state type from shared memory (16-byte aligned).
 template <typename AT, int N>
-__device__ __forceinline__ void load_coef(const AT* p, AT* o) {
+__device__ __forceinline__ void load_vec(const AT* p, AT* o) {
   if constexpr (sizeof(AT) == 4) {
 #pragma unroll
     for (int q = 0; q < N; q += 4) {
@@ -143,17 +97,6 @@ __device__ __forceinline__ void load_coef(const AT* p, AT* o) {
   }
 }
 
-// (a0, a1) += x * (r0, r1) with one packed FP32x2 FMA (each lane rounded once,
-// exactly as two scalar FMAs).
-__device__ __forceinline__ void fma2(float& a0, float& a1, float x, float r0, float r1) {
-  unsigned long long acc, xx, rr;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(acc) : "f"(a0), "f"(a1));
-  asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(x));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(rr) : "f"(r0), "f"(r1));
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(xx), "l"(rr));
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(acc));
-}
-
 template <typename AT>
 __device__ __forceinline__ AT ex(AT x);
 template <>
@@ -167,97 +110,155 @@ __device__ __forceinline__ float lg<float>(float x) { return logf(x); }
 template <>
 __device__ __forceinline__ double lg<double>(double x) { return log(x); }
 
-// Coefficients in shared memory, group-major: for column group g (VEC
-// columns) the CT x VEC values are contiguous, padded to an odd number of
-// 16-byte units so that the groups read together by one warp fall in
-// different banks.
-template <typename AT, int CT, int VEC>
-struct Coef {
-  static constexpr int RAW = CT * VEC;                         // values per group
-  static constexpr int UNITS = (RAW * int(sizeof(AT)) + 15) / 16;
-  static constexpr int STRIDE = ((UNITS % 2) ? UNITS : UNITS + 1) * 16 / int(sizeof(AT));
+// Named barrier of one consumer group (ids 1 and 2; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Shape of one instantiation (class bound CT, state type of `abytes` bytes).
+struct ShapeRT {
+  int R;     // rows per lane in sweep 1
+  int A;     // row groups per warp
+  int P;     // phases per row group
+  int QPL;   // quads per lane per 32-quad span
+  int PV;    // values per 16-byte vector
+  int CTP;   // exchanged / residual row width (whole 16-byte vectors)
+  int CTQ;   // classes padded so that R*CTQ splits evenly over the P phases
+  int V;     // values per lane entering the reduce-scatter
+  int VP;    // values per lane leaving it
 };
 
-// Width of one exchanged logit row: a whole number of 16-byte vectors.
+__host__ __device__ constexpr ShapeRT shape_rt(int abytes, int CT) {
+  ShapeRT s{};
+  s.R = 2;
+  s.A = kBM / s.R;
+  s.P = 32 / s.A;
+  s.QPL = 32 / s.P;
+  s.PV = 16 / abytes;
+  s.CTP = ((CT + s.PV - 1) / s.PV) * s.PV;
+  int c = CT;
+  while ((s.R * c) % s.P) ++c;
+  s.CTQ = c;
+  s.V = s.R * s.CTQ;
+  s.VP = s.V / s.P;
+  return s;
+}
+
+// Warps an instantiation supports (register budget of its launch bound):
+// gradient warps (one per 32 column quads) and logit warps (half as many,
+// each sweeping several spans).
+__host__ __device__ constexpr int max_grad_warps(int abytes, int CT) { return (abytes == 4 && CT <= 12) ? 10 : 5; }
+__host__ __device__ constexpr int logit_warps(int nwc) { return (nwc + 1) / 2; }
+__host__ __device__ constexpr int max_threads(int abytes, int CT) {
+  return 32 * (max_grad_warps(abytes, CT) + logit_warps(max_grad_warps(abytes, CT)) + 1);
+}
+
 template <typename AT, int CT>
-struct Ex {
-  static constexpr int PV = 16 / sizeof(AT);
-  static constexpr int CTP = ((CT + PV - 1) / PV) * PV;
+struct Shape {
+  static constexpr ShapeRT s = shape_rt(int(sizeof(AT)), CT);
+  static constexpr int R = s.R, A = s.A, P = s.P, QPL = s.QPL, PV = s.PV, CTP = s.CTP, CTQ = s.CTQ, V = s.V,
+                       VP = s.VP;
+  static_assert(CTQ >= CTP, "reduce-scatter rows cover the exchanged width");
+  static_assert(V % P == 0, "whole values per lane after the reduce-scatter");
 };
 
-// Shared-memory layout; the host computes the same size with smem_bytes().
+// Shared-memory layout; the host computes the same size with simt_smem_bytes().
 struct Layout {
   size_t xs, bs, red, zx, rs, lrow, ylab, bars, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__host__ __device__ inline Layout layout(int xbytes, int abytes, int CT, int CTP, int PC, int BM, int S, int NT,
-                                         int NSTAGE, int CR, int coef_stride) {
+// NWL: logit warps.
+__host__ __device__ inline Layout layout(int xbytes, int abytes, int CT, int CTP, int V, int A, int PC, int S, int NWL,
+                                         int NSTAGE) {
   Layout L;
   const size_t xpitch = size_t(PC) * xbytes + 16;
   size_t off = 0;
-  L.xs = off;   off = align16(off + size_t(NSTAGE) * CR * xpitch);
-  L.bs = off;   off = align16(off + size_t(PC / (16 / xbytes)) * coef_stride * abytes);
-  L.red = off;  off = align16(off + size_t(NT / 32) * BM * CT * abytes);
-  L.zx = off;   off = align16(off + size_t(2) * S * BM * CTP * abytes);
-  L.rs = off;   off = align16(off + size_t(BM) * CTP * abytes);
-  L.lrow = off; off = align16(off + size_t(BM) * CT * 8);
-  L.ylab = off; off = align16(off + size_t(BM) * 4);
-  L.bars = off; off = align16(off + size_t(NSTAGE + 5) * 8);
+  L.xs = off;   off = align16(off + size_t(NSTAGE) * kBM * xpitch);
+  L.bs = off;   off = align16(off + size_t(CT) * PC * abytes);
+  L.red = off;  off = align16(off + size_t(2) * NWL * A * V * abytes);
+  L.zx = off;   off = align16(off + size_t(2) * S * kBM * CTP * abytes);
+  L.rs = off;   off = align16(off + size_t(2) * kBM * CTP * abytes);
+  L.lrow = off; off = align16(off + size_t(2) * kBM * CT * 8);
+  L.ylab = off; off = align16(off + size_t(2) * kBM * 4);
+  L.bars = off; off = align16(off + size_t(2 * NSTAGE + 6) * 8);
   L.total = off;
   return L;
 }
 
 template <typename XT, typename AT, int CT>
 __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
-  constexpr int VEC = Vec<XT>::N;
-  constexpr int PV = Ex<AT, CT>::PV;
-  constexpr int CTP = Ex<AT, CT>::CTP;
+  using Sh = Shape<AT, CT>;
+  constexpr int R = Sh::R, NA = Sh::A, P = Sh::P, QPL = Sh::QPL, PV = Sh::PV, CTP = Sh::CTP, CTQ = Sh::CTQ,
+                V = Sh::V, VP = Sh::VP;
+  constexpr int BM = kBM;
+  constexpr int MAXW = logit_warps(max_grad_warps(int(sizeof(AT)), CT));
   extern __shared__ __align__(128) unsigned char smem[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int NT = A.NT, NW = NT >> 5;
-  const int S = A.S, BM = A.BM, PC = A.PC, NSTAGE = A.NSTAGE, CR = A.CR;
+  const int NTB = int(blockDim.x);
+  const int NWL = A.NWL, NTL = NWL * 32;                 // logit warps / threads
+  const int NWC = NTB / 32 - 1 - NWL, NTG = NWC * 32;    // gradient warps / threads
+  const bool logit = warp < NWL, producer = warp == NWL + NWC;
+  const int S = A.S, PC = A.PC, NSTAGE = A.NSTAGE;
+  const int nq = PC >> 2;                                  // column quads of the slice
   const uint32_t rank = (S > 1) ? cluster_rank() : 0u;
   const size_t xpitch = size_t(PC) * sizeof(XT) + 16;
-  constexpr int CSTR = Coef<AT, CT, VEC>::STRIDE;
-  const Layout Lo = layout(sizeof(XT), sizeof(AT), CT, CTP, PC, BM, S, NT, NSTAGE, CR, CSTR);
+  int err0 = 0;
+
+  const Layout Lo = layout(sizeof(XT), sizeof(AT), CT, CTP, V, NA, PC, S, NWL, NSTAGE);
   unsigned char* xs = smem + Lo.xs;
   AT* bs = reinterpret_cast<AT*>(smem + Lo.bs);
   AT* red = reinterpret_cast<AT*>(smem + Lo.red);
   AT* zx = reinterpret_cast<AT*>(smem + Lo.zx);
-  AT* rs = reinterpret_cast<AT*>(smem + Lo.rs);
-  double* lrow = reinterpret_cast<double*>(smem + Lo.lrow);
-  int* ylab = reinterpret_cast<int*>(smem + Lo.ylab);
+  AT* rs = reinterpret_cast<AT*>(smem + Lo.rs);            // [2][BM][CTP] residual rows
+  double* lrow = reinterpret_cast<double*>(smem + Lo.lrow);  // [2][BM][CT] row log-likelihoods
+  int* ylab = reinterpret_cast<int*>(smem + Lo.ylab);       // [2][BM] labels
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lo.bars);
-  uint64_t* zfull = full + NSTAGE;
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* zfull = empty + NSTAGE;
   uint64_t* zempty = zfull + 2;
   uint64_t* never = zempty + 2;  // fault injection: a barrier no thread arrives at
+  uint64_t* bbar = never + 1;    // coefficient slice landed
 
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(&full[s], 1);
-    mbar_init(&zfull[0], 1);
-    mbar_init(&zfull[1], 1);
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NWC);
+    }
+    // Exchange slot b of tile t is full once every logit thread of this CTA
+    // has arrived (labels and, for S = 1, the logits written) and, for S > 1,
+    // the partials of all S CTAs have landed; it is empty once the gradient
+    // group of every CTA has read it.
+    mbar_init(&zfull[0], NTL);
+    mbar_init(&zfull[1], NTL);
     mbar_init(&zempty[0], S);
     mbar_init(&zempty[1], S);
     mbar_init(never, 1);
+    mbar_init(bbar, 1);
     fence_mbar_init_cluster();
   }
-  // Coefficient slice, FP8 column scales folded in: X B = X_q diag(s) B.
+  __syncthreads();
+  // Coefficient slice, class-major (one bulk copy per class row), FP8
+  // column scales folded in: X B = X_q diag(s) B.  Rows past C start at zero.
   {
-    const AT* beta = static_cast<const AT*>(A.beta);
-    for (int idx = tid; idx < CT * PC; idx += NT) {
-      const int k = idx / PC, j = idx - k * PC;
-      const int col = int(rank) * PC + j;
-      AT v = AT(0);
-      if (k < A.C) {
-        v = beta[size_t(k) * A.p_pad + col];
-        if (A.xscale) v *= AT(A.xscale[col]);
-      }
-      bs[size_t(j / VEC) * CSTR + k * VEC + (j % VEC)] = v;
+    if (producer) {
+      const uint32_t rb = uint32_t(PC) * sizeof(AT);
+      if (lane == 0) mbar_arrive_expect_tx(bbar, rb * uint32_t(A.C));
+      __syncwarp();
+      const AT* beta = static_cast<const AT*>(A.beta) + size_t(rank) * PC;
+      for (int k = lane; k < A.C; k += 32) bulk_g2s(bs + size_t(k) * PC, beta + size_t(k) * A.p_pad, rb, bbar);
     }
-    for (int idx = tid; idx < BM * CTP; idx += NT) rs[idx] = AT(0);
+    for (int idx = A.C * PC + tid; idx < CT * PC; idx += NTB) bs[idx] = AT(0);
+    for (int idx = tid; idx < 2 * BM * CTP; idx += NTB) rs[idx] = AT(0);
+    if (!mbar_wait_cta(bbar, 0u, A.spin_limit)) err0 |= ERR_TIMEOUT_STAGE;
+    if (A.xscale) {
+      for (int idx = tid; idx < A.C * PC; idx += NTB) {
+        const int j = idx % PC;
+        bs[idx] *= AT(A.xscale[int(rank) * PC + j]);
+      }
+    }
   }
   if (S > 1)
     cluster_sync_all();
@@ -265,276 +266,295 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
     __syncthreads();
 
   const int64_t nclu = A.nclusters;
-  const int64_t my_tiles = (cl < A.ntiles) ? (A.ntiles - 1 - cl) / nclu + 1 : 0;
+  const int64_t T = (cl < A.ntiles) ? (A.ntiles - 1 - cl) / nclu + 1 : 0;   // super-tiles of this cluster
+  auto row0_of = [&](int64_t t) { return (cl + t * nclu) * BM; };
+  auto rows_of = [&](int64_t t) { return int(min(int64_t(BM), A.n - row0_of(t))); };
   const uint32_t row_bytes = uint32_t(PC) * sizeof(XT);
-  auto row0_of = [&](int64_t u) { return (cl + u * nclu) * BM; };
-  auto rows_of = [&](int64_t u) { return int(min(int64_t(BM), A.n - row0_of(u))); };
-  auto nch_of = [&](int64_t u) { return (rows_of(u) + CR - 1) / CR; };
-
-  AT G[4][CT];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int k = 0; k < CT; ++k) G[q][k] = AT(0);
-  double lacc = 0.0;
-  int err = 0;
-
-  if (A.inject_timeout) {
-    const bool ok = mbar_wait_cta(never, 0u, A.spin_limit);
-    if (__syncthreads_or(!ok)) err |= ERR_TIMEOUT_STAGE;
+  int err = err0;
+  long long lim = err0 ? 0 : A.spin_limit;
+  if (A.inject_timeout && !producer) {
+    if (!mbar_wait_cta(never, 0u, lim)) {
+      err |= ERR_TIMEOUT_STAGE;
+      lim = 0;
+    }
   }
-  const int64_t T = err ? 0 : my_tiles;
-  const int64_t nphase = 2 * T;
-  // Phase k of the sweep order S1(0), S1(1), S2(0), S1(2), S2(1), ..., S2(T-1):
-  // returns the super-tile, sets *s2 for a gradient sweep.
-  auto phase = [&](int64_t k, bool* s2) -> int64_t {
-    if (k == 0) { *s2 = false; return 0; }
-    if (k == nphase - 1) { *s2 = true; return T - 1; }
-    const int64_t v = (k + 1) / 2;
-    *s2 = (k % 2) == 0;
-    return *s2 ? v - 1 : v;
-  };
 
-  // Producer cursor (identical in every thread; warp 0 issues).
-  int64_t pk = 0, issued = 0, xwaited = 0;
-  int pc = 0;
-  auto issue_next = [&]() {
-    if (pk >= nphase) return;
-    bool s2;
-    const int64_t u = phase(pk, &s2);
-    const int64_t row0 = row0_of(u) + int64_t(pc) * CR;
-    const int rv = min(CR, rows_of(u) - pc * CR);
-    const int slot = int(issued % NSTAGE);
-    if (warp == 0) {
+  if (producer) {
+    // ---------------------------------------------------------------- producer
+    const XT* Xs = static_cast<const XT*>(A.X) + size_t(rank) * PC;
+    // The ring holds few tiles; HBM latency under full load is several
+    // microseconds, so tiles further ahead are pulled into L2 with bulk
+    // prefetches (about 256 KB per CTA in flight) and the ring's copies hit L2.
+    const int64_t tile_bytes = int64_t(BM) * row_bytes;
+    const int64_t PF = max(int64_t(NSTAGE), min(int64_t(24), (int64_t(256) * 1024 + tile_bytes - 1) / tile_bytes));
+    auto prefetch = [&](int64_t t) {
+      const int rv = rows_of(t);
+      const XT* src = Xs + size_t(row0_of(t)) * A.p_pad;
+      if (lane < rv) bulk_prefetch_l2(src + size_t(lane) * A.p_pad, row_bytes);
+    };
+    for (int64_t t = NSTAGE; t < min(PF, T); ++t) prefetch(t);
+    for (int64_t t = 0; t < T; ++t) {
+      if (t + PF < T) prefetch(t + PF);
+      const int slot = int(t % NSTAGE);
+      if (t >= NSTAGE) {
+        if (!mbar_wait_cta(&empty[slot], uint32_t(((t / NSTAGE) - 1) & 1), lim)) {
+          err |= ERR_TIMEOUT_SLOT;
+          lim = 0;
+        }
+      }
+      const int rv = rows_of(t);
       if (lane == 0) mbar_arrive_expect_tx(&full[slot], row_bytes * uint32_t(rv));
       __syncwarp();
-      const XT* src = static_cast<const XT*>(A.X) + size_t(row0) * A.p_pad + size_t(rank) * PC;
-      for (int i = lane; i < rv; i += 32)
-        bulk_g2s(xs + (size_t(slot) * CR + i) * xpitch, src + size_t(i) * A.p_pad, row_bytes, &full[slot]);
+      const XT* src = Xs + size_t(row0_of(t)) * A.p_pad;
+      if (lane < rv) bulk_g2s(xs + (size_t(slot) * BM + lane) * xpitch, src + size_t(lane) * A.p_pad, row_bytes, &full[slot]);
     }
-    issued += 1;
-    if (++pc == nch_of(u)) {
-      pc = 0;
-      ++pk;
-    }
-  };
-  for (int i = 0; i < NSTAGE; ++i) issue_next();
-
-  int64_t m = 0;        // chunks consumed
-  int lab0 = 0, lab1 = 0;  // labels of rows tid and tid + NT of super-tile lab_tile
-  int64_t lab_tile = -1;
-  auto load_labels = [&](int64_t u) {
-    const int r = rows_of(u);
-    const int32_t* yp = A.y + row0_of(u);
-    lab0 = (tid < r) ? __ldg(yp + tid) : 0;
-    lab1 = (tid + NT < r) ? __ldg(yp + tid + NT) : 0;
-    lab_tile = u;
-  };
-  for (int64_t k = 0; k < nphase && !err; ++k) {
-    bool s2;
-    const int64_t u = phase(k, &s2);
-    const int rv = rows_of(u);
-    const int nch = (rv + CR - 1) / CR;
-    const int xsl = int(u & 1);
-    const uint32_t use = uint32_t(u >> 1);
-    if (!s2) {
-      if (u >= 1) load_labels(u - 1);  // the super-tile whose gradient sweep comes next
-    } else {
-      if (lab_tile != u) load_labels(u);
-      if (tid < BM) ylab[tid] = lab0;
-      if (tid + NT < BM) ylab[tid + NT] = lab1;
-      const AT* zslot = zx + size_t(xsl) * S * BM * CTP;
-      if (S > 1) {
-        const bool ok = mbar_wait_cluster(&zfull[xsl], use & 1u, A.spin_limit);
-        if (__syncthreads_or(!ok)) {
-          err |= ERR_TIMEOUT_EXCHANGE;
-          break;
+    // Every copy must land before shared memory is released.
+    for (int64_t t = max(int64_t(0), T - NSTAGE); t < T; ++t)
+      (void)mbar_wait_cta(&full[t % NSTAGE], uint32_t((t / NSTAGE) & 1), A.spin_limit);
+  } else if (logit) {
+    // ---------------------------------------------------------------- logit group
+    const int ga = lane / P, gc = lane % P;        // row group, phase
+    for (int64_t t = 0; t < T; ++t) {
+      const int slot = int(t % NSTAGE);
+      const int buf = int(t & 1);
+      const int rv = rows_of(t);
+      // Labels of this tile: loaded now, stored with the exchange (the load's
+      // latency overlaps the sweep).
+      int ylv = 0;
+      if (tid < BM && tid < rv) ylv = __ldg(A.y + row0_of(t) + tid);
+      if (!mbar_wait_cta(&full[slot], uint32_t((t / NSTAGE) & 1), lim)) {
+        err |= ERR_TIMEOUT_STAGE;
+        lim = 0;
+      }
+      const unsigned char* xst = xs + size_t(slot) * BM * xpitch;
+      AT acc[R][CT];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[r][c] = AT(0);
+      for (int q0 = warp * 32; q0 < nq; q0 += NWL * 32) {
+#pragma unroll
+      for (int m = 0; m < QPL; ++m) {
+        const int q = q0 + gc + m * P;
+        if (q < nq) {
+          AT xv[R][4];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            load_quad<XT, AT>(xst + size_t(ga * R + r) * xpitch + size_t(q) * 4 * sizeof(XT), xv[r]);
+#pragma unroll
+          for (int c = 0; c < CT; ++c) {
+            AT b[4];
+            load_vec<AT, 4>(bs + size_t(c) * PC + 4 * q, b);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[r][c] = fma(xv[r][j], b[j], acc[r][c]);
+          }
         }
-      } else {
-        __syncthreads();
       }
-      // Softmax with the zero logit of class K, residual and row
-      // log-likelihood: one warp per (row, chain), lane <-> class.
-      const int Km1 = A.Km1, chains = A.chains;
-      for (int it = warp; it < BM * chains; it += NW) {
-        const int i = it / chains, c = it - i * chains;
-        const int cb = c * Km1;
-        AT z = AT(0);
-        if (lane < Km1)
-          for (int r = 0; r < S; ++r) z += zslot[(size_t(r) * BM + i) * CTP + cb + lane];
-        AT mx = (lane < Km1) ? max(z, AT(0)) : AT(0);
+      }
+      AT val[V];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const AT e = (lane < Km1) ? ex<AT>(z - mx) : AT(0);
-        AT se = e;
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
-        se += ex<AT>(-mx);
-        const int yi = ylab[i];
-        const AT zy = __shfl_sync(0xffffffffu, z, yi < Km1 ? yi : 0);
-        const bool valid = i < rv;
-        if (lane < Km1) rs[size_t(i) * CTP + cb + lane] = valid ? (lane == yi ? AT(1) : AT(0)) - e / se : AT(0);
-        if (lane == 0) lrow[size_t(i) * CT + c] = valid ? double((yi < Km1 ? zy : AT(0)) - mx - lg<AT>(se)) : 0.0;
+        for (int c = 0; c < CTQ; ++c) val[r * CTQ + c] = (c < CT) ? acc[r][c] : AT(0);
+      // Reduce-scatter over the P phases of the row group: after the step
+      // with mask m a lane keeps the half of its values selected by bit m,
+      // so phase gc ends with the sums of values [gc*VP, (gc+1)*VP).
+#pragma unroll
+      for (int m = P / 2, h = V / 2; m >= 1; m >>= 1, h >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+          const AT send = up ? val[i] : val[i + h];
+          const AT keep = up ? val[i + h] : val[i];
+          val[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
       }
-      __syncthreads();
-      if (S > 1 && tid < S) mbar_arrive_remote(map_peer(smem_u32(&zempty[xsl]), uint32_t(tid)));
-      if (rank == 0 && tid < A.chains) {
-        double sl = 0.0;
-        for (int i = 0; i < rv; ++i) sl += lrow[size_t(i) * CT + tid];
-        lacc += sl;
-      }
-    }
-
-    for (int c = 0; c < nch; ++c, ++m) {
-      const int slot = int(m % NSTAGE);
       {
-        const bool ok = mbar_wait_cta(&full[slot], uint32_t((m / NSTAGE) & 1), A.spin_limit);
-        if (__syncthreads_or(!ok)) {
-          err |= ERR_TIMEOUT_STAGE;
-          break;
-        }
+        AT* rw = red + ((size_t(buf) * NWL + warp) * NA + ga) * V + gc * VP;
+#pragma unroll
+        for (int i = 0; i < VP; ++i) rw[i] = val[i];
       }
-      xwaited = m + 1;
-      const unsigned char* xst = xs + size_t(slot) * CR * xpitch;
-      const int crv = min(CR, rv - c * CR);
-      if (!s2) {
-        // Sweep 1: partial logits of this chunk's rows.
-        const int LPR = 32 / CR;
-        const int i = lane % CR, sub = lane / CR;
-        const int G16 = PC / VEC;
-        const int gpw = (G16 + NW - 1) / NW;
-        const int gbeg = warp * gpw, gend = min(G16, gbeg + gpw);
-        AT z[CT];
-#pragma unroll
-        for (int kk = 0; kk < CT; ++kk) z[kk] = AT(0);
-        const unsigned char* xrow = xst + size_t(i) * xpitch;
-        for (int g = gbeg + sub; g < gend; g += LPR) {
-          AT xv[VEC];
-          load16<XT, AT>(xrow + size_t(g) * 16, xv);
-          const AT* bg = bs + size_t(g) * CSTR;
-#pragma unroll
-          for (int kk = 0; kk < CT; ++kk) {
-            AT bv[VEC];
-            load_coef<AT, VEC>(bg + kk * VEC, bv);
-            AT acc = z[kk];
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) acc = fma(xv[q], bv[q], acc);
-            z[kk] = acc;
-          }
-        }
-        for (int o = CR; o < 32; o <<= 1)
-#pragma unroll
-          for (int kk = 0; kk < CT; ++kk) z[kk] += __shfl_xor_sync(0xffffffffu, z[kk], o);
-        if (sub == 0)
-#pragma unroll
-          for (int kk = 0; kk < CT; ++kk) red[(size_t(warp) * BM + c * CR + i) * CT + kk] = z[kk];
-      } else if (4 * tid < PC) {
-        // Sweep 2: partial X^T R for this thread's 4 columns.
-        const unsigned char* xcol = xst + size_t(4) * tid * sizeof(XT);
-        const AT* rrow = rs + size_t(c) * CR * CTP;
-        for (int i = 0; i < crv; ++i) {
-          AT r[CTP];
-          load_coef<AT, CTP>(rrow + size_t(i) * CTP, r);
-          AT xv[4];
-          load4<XT, AT>(xcol + size_t(i) * xpitch, xv);
-          if constexpr (sizeof(AT) == 4) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-#pragma unroll
-              for (int kk = 0; kk + 1 < CT; kk += 2) fma2(G[q][kk], G[q][kk + 1], xv[q], r[kk], r[kk + 1]);
-              if (CT % 2) G[q][CT - 1] = fma(xv[q], r[CT - 1], G[q][CT - 1]);
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-              for (int kk = 0; kk < CT; ++kk) G[q][kk] = fma(xv[q], r[kk], G[q][kk]);
-          }
-        }
-      }
-      __syncthreads();   // ring slot free
-      issue_next();
-    }
-    if (err) break;
+      group_sync(1, NTL);
 
-    if (!s2) {
-      // Partial logits of super-tile u: fixed-order sum over warps, pushed to
-      // every peer's slot u&1.
-      if (S > 1) {
-        if (tid == 0) mbar_arrive_expect_tx(&zfull[xsl], uint32_t(S * BM * CTP * sizeof(AT)));
-        const bool ok = mbar_wait_cluster(&zempty[xsl], (use & 1u) ^ 1u, A.spin_limit);
-        if (__syncthreads_or(!ok)) {
-          err |= ERR_TIMEOUT_SLOT;
-          break;
-        }
+      // Exchange slot `buf` must have been read by every CTA (tile t - 2).
+      if (!(S > 1 ? mbar_wait_cluster(&zempty[buf], uint32_t(((t >> 1) & 1) ^ 1), lim)
+                  : mbar_wait_cta(&zempty[buf], uint32_t(((t >> 1) & 1) ^ 1), lim))) {
+        err |= ERR_TIMEOUT_SLOT;
+        lim = 0;
       }
-      AT* zslot = zx + size_t(xsl) * S * BM * CTP;
-      const int nv = CTP / PV;
-      for (int it = tid; it < BM * nv; it += NT) {
-        const int i = it / nv, kv = (it - i * nv) * PV;
+      if (tid < BM) ylab[buf * BM + tid] = ylv;
+      if (S > 1 && tid == 0) mbar_arrive_expect_tx(&zfull[buf], uint32_t(S * BM * CTP * sizeof(AT)));
+      // One (row, class) value per thread: the NWL warp partials are loaded
+      // together and added in warp order; PV neighbouring classes are then
+      // gathered into one lane, which pushes them as a 16-byte vector.
+      constexpr int NV = BM * CTP;
+      for (int base = 0; base < NV; base += NTL) {
+        const int idx = base + tid;
+        const bool act = idx < NV;
+        const int i = act ? idx / CTP : 0, kc = act ? idx - (idx / CTP) * CTP : 0;
+        const int a = i / R, r = i % R;
+        AT sum = AT(0);
+        if (act && kc < CT) {
+          AT wv[MAXW];
+#pragma unroll
+          for (int w = 0; w < MAXW; ++w)
+            wv[w] = (w < NWL) ? red[((size_t(buf) * NWL + w) * NA + a) * V + r * CTQ + kc] : AT(0);
+#pragma unroll
+          for (int w = 0; w < MAXW; ++w)
+            if (w < NWL) sum += wv[w];
+        }
         AT v[PV];
 #pragma unroll
-        for (int q = 0; q < PV; ++q) {
-          const int kk = kv + q;
-          AT sum = AT(0);
-          if (kk < CT && i < rv)
-            for (int w = 0; w < NW; ++w) sum += red[(size_t(w) * BM + i) * CT + kk];
-          v[q] = sum;
-        }
-        AT* dst = zslot + (size_t(rank) * BM + i) * CTP + kv;
-        if (S == 1) {
+        for (int q = 0; q < PV; ++q) v[q] = __shfl_sync(0xffffffffu, sum, (lane + q) & 31);
+        if (act && kc % PV == 0) {
+          AT* dst = zx + (size_t(buf) * S + rank) * BM * CTP + size_t(i) * CTP + kc;
+          if (S == 1) {
 #pragma unroll
-          for (int q = 0; q < PV; ++q) dst[q] = v[q];
-        } else {
-          const uint32_t laddr = smem_u32(dst), lbar = smem_u32(&zfull[xsl]);
-          for (int r = 0; r < S; ++r) {
-            const uint32_t ra = map_peer(laddr, uint32_t(r)), rb = map_peer(lbar, uint32_t(r));
-            if constexpr (sizeof(AT) == 4)
-              st_async_v4f(ra, float(v[0]), float(v[1]), float(v[2]), float(v[3]), rb);
-            else
-              st_async_v2d(ra, double(v[0]), double(v[1]), rb);
+            for (int q = 0; q < PV; ++q) dst[q] = v[q];
+          } else {
+            const uint32_t laddr = smem_u32(dst), lbar = smem_u32(&zfull[buf]);
+            for (int r2 = 0; r2 < S; ++r2) {
+              const uint32_t ra = map_peer(laddr, uint32_t(r2)), rb = map_peer(lbar, uint32_t(r2));
+              if constexpr (sizeof(AT) == 4)
+                st_async_v4f(ra, float(v[0]), float(v[1]), float(v[2]), float(v[3]), rb);
+              else
+                st_async_v2d(ra, double(v[0]), double(v[1]), rb);
+            }
           }
         }
       }
-      if (S == 1) __syncthreads();
+      // Release: labels (and the local logits when S = 1) are visible to the
+      // gradient group once its wait on zfull completes.
+      if (!(S > 1 && tid == 0)) mbar_arrive_local(&zfull[buf]);
     }
-  }
+  } else {
+    // ---------------------------------------------------------------- gradient group
+    const int gw = warp - NWL, gt = tid - NTL;     // warp / thread within the group
+    const int qq = gw * 32 + lane;                 // this thread's quad
+    AT G[4][CT];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < CT; ++k) G[q][k] = AT(0);
+    double lacc = 0.0;
+    const int Km1 = A.Km1, chains = A.chains;
+    int W = 1;
+    while (W < Km1) W <<= 1;
+    const int RPW = 32 / W, sl = lane % W;
+    const int ntask = BM * chains;
 
-  if (err) {
-    // Let every copy this CTA issued land before its shared memory goes away.
-    if (tid == 0) {
-      for (int64_t tt = xwaited; tt < issued; ++tt)
-        (void)mbar_wait_cta(&full[tt % NSTAGE], uint32_t((tt / NSTAGE) & 1), A.spin_limit);
-      atomicOr(A.err, err);
+    for (int64_t t = 0; t < T; ++t) {
+      const int slot = int(t % NSTAGE);
+      const int buf = int(t & 1);
+      const int rv = rows_of(t);
+      if (!(S > 1 ? mbar_wait_cluster(&zfull[buf], uint32_t((t >> 1) & 1), lim)
+                  : mbar_wait_cta(&zfull[buf], uint32_t((t >> 1) & 1), lim))) {
+        err |= ERR_TIMEOUT_EXCHANGE;
+        lim = 0;
+      }
+      // Softmax with the zero logit of class K, residual and row
+      // log-likelihood: a warp takes 32/W (row, chain) tasks at once, W
+      // lanes per task (W = K-1 rounded up to a power of two), lane <-> class.
+      const AT* zs = zx + size_t(buf) * S * BM * CTP;
+      AT* rsb = rs + size_t(buf) * BM * CTP;
+      double* lrb = lrow + size_t(buf) * BM * CT;
+      for (int base = gw * RPW; base < ntask; base += NWC * RPW) {
+        const int it = base + lane / W;
+        const bool task = it < ntask;
+        const int i = task ? it / chains : 0, c = task ? it - (it / chains) * chains : 0;
+        const int cb = c * Km1;
+        const bool valid = task && i < rv;
+        const bool cls = task && sl < Km1;
+        AT z = AT(0);
+        if (cls) {
+          AT zr[16];
+#pragma unroll
+          for (int r = 0; r < 16; ++r) zr[r] = (r < S) ? zs[(size_t(r) * BM + i) * CTP + cb + sl] : AT(0);
+#pragma unroll
+          for (int r = 0; r < 16; ++r)
+            if (r < S) z += zr[r];
+        }
+        AT mx = cls ? max(z, AT(0)) : AT(0);
+        for (int o = W / 2; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o, W));
+        const AT e = cls ? ex<AT>(z - mx) : AT(0);
+        AT se = e;
+        for (int o = W / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o, W);
+        se += ex<AT>(-mx);
+        const int yi = valid ? ylab[buf * BM + i] : 0;
+        const AT zy = __shfl_sync(0xffffffffu, z, yi < Km1 ? yi : 0, W);
+        if (cls) rsb[size_t(i) * CTP + cb + sl] = valid ? (sl == yi ? AT(1) : AT(0)) - e / se : AT(0);
+        if (task && sl == 0) lrb[size_t(i) * CT + c] = valid ? double((yi < Km1 ? zy : AT(0)) - mx - lg<AT>(se)) : 0.0;
+      }
+      group_sync(2, NTG);
+      // Exchange slot `buf` read: release it in every CTA of the cluster.
+      if (gt < S) {
+        if (S > 1)
+          mbar_arrive_remote(map_peer(smem_u32(&zempty[buf]), uint32_t(gt)));
+        else
+          mbar_arrive_local(&zempty[buf]);
+      }
+      // Sweep 2: G += X_tile^T R over the tile's rows (fixed row order;
+      // rows past the end of X contribute zero).
+      if (qq < nq) {
+        const unsigned char* xst = xs + size_t(slot) * BM * xpitch + size_t(qq) * 4 * sizeof(XT);
+#pragma unroll
+        for (int i = 0; i < BM; ++i) {
+          AT xv[4];
+          load_quad<XT, AT>(xst + size_t(i) * xpitch, xv);
+          if (i >= rv)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[q] = AT(0);
+          AT r[CTP];
+          load_vec<AT, CTP>(rsb + size_t(i) * CTP, r);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) G[q][c] = fma(xv[q], r[c], G[q][c]);
+        }
+      }
+      if (rank == 0 && gt < chains) {
+        double sl2 = 0.0;
+        for (int i = 0; i < rv; ++i) sl2 += lrb[size_t(i) * CT + gt];
+        lacc += sl2;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&empty[slot]);
     }
-  }
-  if (4 * tid < PC) {
-    AT* gp = static_cast<AT*>(A.gpart) + size_t(cl) * A.gpart_cstride;
-    const int col = int(rank) * PC + 4 * tid;
-    AT sc[4] = {AT(1), AT(1), AT(1), AT(1)};
-    if (A.xscale)
+
+    if (qq < nq) {
+      AT* gp = static_cast<AT*>(A.gpart) + size_t(cl) * A.gpart_cstride;
+      const int col = int(rank) * PC + 4 * qq;
+      AT sc[4] = {AT(1), AT(1), AT(1), AT(1)};
+      if (A.xscale)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sc[q] = AT(A.xscale[col + q]);
+        for (int q = 0; q < 4; ++q) sc[q] = AT(A.xscale[col + q]);
 #pragma unroll
-    for (int kk = 0; kk < CT; ++kk) {
-      if (kk < A.C) {
-        AT* d = gp + size_t(kk) * A.p_pad + col;
-        if constexpr (sizeof(AT) == 4) {
-          *reinterpret_cast<float4*>(d) = make_float4(float(G[0][kk] * sc[0]), float(G[1][kk] * sc[1]),
-                                                      float(G[2][kk] * sc[2]), float(G[3][kk] * sc[3]));
-        } else {
-          reinterpret_cast<double2*>(d)[0] = make_double2(double(G[0][kk] * sc[0]), double(G[1][kk] * sc[1]));
-          reinterpret_cast<double2*>(d)[1] = make_double2(double(G[2][kk] * sc[2]), double(G[3][kk] * sc[3]));
+      for (int kk = 0; kk < CT; ++kk) {
+        if (kk < A.C) {
+          AT* d = gp + size_t(kk) * A.p_pad + col;
+          if constexpr (sizeof(AT) == 4) {
+            *reinterpret_cast<float4*>(d) = make_float4(float(G[0][kk] * sc[0]), float(G[1][kk] * sc[1]),
+                                                        float(G[2][kk] * sc[2]), float(G[3][kk] * sc[3]));
+          } else {
+            reinterpret_cast<double2*>(d)[0] = make_double2(double(G[0][kk] * sc[0]), double(G[1][kk] * sc[1]));
+            reinterpret_cast<double2*>(d)[1] = make_double2(double(G[2][kk] * sc[2]), double(G[3][kk] * sc[3]));
+          }
         }
       }
     }
+    if (rank == 0 && gt < A.chains) A.lpart[size_t(cl) * A.lpart_cstride + gt] = lacc;
   }
-  if (rank == 0 && tid < A.chains) A.lpart[size_t(cl) * A.lpart_cstride + tid] = lacc;
-  if (S > 1) cluster_sync_all();
+  if (err) atomicOr(A.err, err);
+  if (S > 1)
+    cluster_sync_all();   // no peer may still write into this CTA's shared memory
+  else
+    __syncthreads();
 }
 
 template <typename XT, typename AT, int CT>
-__global__ void __launch_bounds__(kMaxThreads, 1) lpg_kernel(const LpgArgs A) {
+__global__ void __launch_bounds__(max_threads(int(sizeof(AT)), CT), 1) lpg_kernel(const LpgArgs A) {
   lpg_body<XT, AT, CT>(A, int(blockIdx.x) / A.S);
 }
 
@@ -542,7 +562,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) lpg_kernel(const LpgArgs A) {
 // of the grid work on problem b (its own X, labels, coefficients, tiles and
 // partial slots); every problem shares the cluster size and block size.
 template <typename XT, typename AT, int CT>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(max_threads(int(sizeof(AT)), CT), 1)
     lpg_kernel_batched(const LpgArgs* __restrict__ table, const int* __restrict__ first, int nprob, int chains) {
   __shared__ LpgArgs args;
   __shared__ int cl_local;

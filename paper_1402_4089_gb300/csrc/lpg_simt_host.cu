@@ -2,6 +2,8 @@
 // sizing, function attributes, occupancy query and the cluster launch.
 #include "lpg_simt.cuh"
 
+#include <algorithm>
+
 namespace hmc {
 namespace simt {
 
@@ -66,6 +68,13 @@ int simt_ct_of(int xt, int C) {
   return ct;
 }
 
+int simt_max_grad_warps(int xt, int C) {
+  const int ct = simt_ct_of(xt, C);
+  return simt::max_grad_warps(xt == HMC_F64 ? 8 : 4, ct);
+}
+
+int simt_logit_warps(int nwc) { return simt::logit_warps(nwc); }
+
 int simt_max_ct(int xt) {
   const int* cts;
   const simt::KernelFn* fns;
@@ -73,17 +82,13 @@ int simt_max_ct(int xt) {
   return cts[m - 1];
 }
 
-size_t simt_smem_bytes(int xt, int /*st*/, int C, int PC, int BM, int S, int NT, int NSTAGE, int CR) {
+size_t simt_smem_bytes(int xt, int /*st*/, int C, int PC, int S, int NWL, int NSTAGE) {
   int ct = 0;
   if (!simt::pick(xt, C, &ct)) return ~size_t(0);
   const int xbytes = xt == HMC_F64 ? 8 : xt == HMC_F32 ? 4 : xt == HMC_BF16 ? 2 : 1;
   const int abytes = xt == HMC_F64 ? 8 : 4;
-  const int pv = 16 / abytes;
-  const int ctp = ((ct + pv - 1) / pv) * pv;
-  const int vec = 16 / xbytes;
-  const int units = (ct * vec * abytes + 15) / 16;
-  const int cstride = ((units % 2) ? units : units + 1) * 16 / abytes;
-  return simt::layout(xbytes, abytes, ct, ctp, PC, BM, S, NT, NSTAGE, CR, cstride).total;
+  const simt::ShapeRT sh = simt::shape_rt(abytes, ct);
+  return simt::layout(xbytes, abytes, ct, sh.CTP, sh.V, sh.A, PC, S, NWL, NSTAGE).total;
 }
 
 cudaError_t simt_prepare(int xt, int /*st*/, int C, size_t smem, int S) {
@@ -139,6 +144,59 @@ cudaError_t simt_max_active_clusters(int xt, int /*st*/, int C, size_t smem, int
   cudaLaunchAttribute attr[1];
   fill_config(cfg, attr, S, S, NT, smem, nullptr);
   return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
+}
+
+static int xbytes_of(int xt) { return xt == HMC_F64 ? 8 : xt == HMC_F32 ? 4 : xt == HMC_BF16 ? 2 : 1; }
+
+cudaError_t simt_choose(int xt, int C, int64_t p, int64_t ntiles, int force_S, int force_NS, int64_t exact_ld,
+                        SimtTile* out) {
+  *out = SimtTile{};
+  int dev = 0, smem_max = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t want = std::max<int64_t>(1, ntiles);
+  int64_t best_active = -1;
+  for (int S : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16}) {
+    if (force_S && S != force_S) continue;
+    int64_t PC;
+    if (exact_ld > 0) {
+      if (exact_ld % (16 * S)) continue;
+      PC = exact_ld / S;
+    } else {
+      // Slices start on 128-byte boundaries: bulk copies from unaligned
+      // slices stream far slower.
+      const int64_t al = std::max(16, 128 / xbytes_of(xt));
+      PC = ((p + S - 1) / S + al - 1) / al * al;
+    }
+    if (PC < 16) PC = 16;
+    const int NWC = int((PC + 127) / 128);
+    if (NWC > simt_max_grad_warps(xt, C)) continue;
+    const int NWL = simt_logit_warps(NWC);
+    const int NT = 32 * (NWC + NWL + 1);
+    for (int NS = 6; NS >= 2; --NS) {
+      if (force_NS && NS != force_NS) continue;
+      const size_t smem = simt_smem_bytes(xt, 0, C, int(PC), S, NWL, NS);
+      if (smem > size_t(smem_max)) continue;
+      e = simt_prepare(xt, 0, C, smem, S);
+      if (e != cudaSuccess) return e;
+      int maxclu = 0;
+      e = simt_max_active_clusters(xt, 0, C, smem, S, NT, &maxclu);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      if (maxclu < 1) break;
+      // Most SMs streaming X, then the smaller cluster (fewer logit exchanges).
+      const int64_t active = std::min<int64_t>(maxclu, want) * S;
+      if (active > best_active) {
+        best_active = active;
+        *out = SimtTile{S, int(PC), NWC, NWL, NT, NS, smem, maxclu};
+      }
+      break;  // deepest ring that fits for this cluster size
+    }
+  }
+  return cudaSuccess;
 }
 
 cudaError_t simt_prepare_batched(int xt, int C, int S) {

@@ -81,7 +81,7 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
   using namespace hmc;
   hmc::set_last_error(std::string());
   if (n < 0 || p < 1 || K < 2 || K > 1024 || chains < 1) return nfail(HMC_EINVAL, "need n >= 0, p >= 1, 2 <= K <= 1024, chains >= 1");
-  if (ldx < p || ldx % 32 != 0) return nfail(HMC_EINVAL, "ldx must be a multiple of 32 and >= p");
+  if (ldx < p || ldx % 16 != 0) return nfail(HMC_EINVAL, "ldx must be a multiple of 16 and >= p");
   if ((n > 0 && (!X || !y)) || !beta || !logpost || !grad) return nfail(HMC_EINVAL, "NULL pointer argument");
   if (prior != HMC_PRIOR_GAUSSIAN && prior != HMC_PRIOR_CAUCHY) return nfail(HMC_EINVAL, "unknown prior kind");
   if (!(prior_scale > 0.0) || !std::isfinite(prior_scale)) return nfail(HMC_EINVAL, "prior_scale must be finite and > 0");
@@ -91,33 +91,14 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
     return nfail(HMC_EINVAL, "chains * (K-1) = " + std::to_string(C) + " exceeds " + std::to_string(simt_max_ct(HMC_F32)));
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
 
-  // Tile: cluster size S with PC = ldx / S a multiple of 32 the CTA covers.
-  int dev = 0, smem_max = 0;
-  NA_CUDA(cudaGetDevice(&dev));
-  NA_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  int S = 0, BM = 0, CR = 8, NT = 0, NS = 0, PC = 0;
-  size_t smem = 0;
-  for (int s : {1, 2, 4, 8, 16}) {
-    if (ldx % (32 * s) != 0) continue;
-    const int pc = int(ldx / s);
-    const int nt = ((std::max(32, pc / 4) + 31) / 32) * 32;
-    if (nt > kSimtMaxThreads || pc > 4 * nt) continue;
-    for (int bm : {32, 16}) {
-      for (int ns : {4, 3, 2}) {
-        const size_t sm = simt_smem_bytes(HMC_F32, HMC_F32, C, pc, bm, s, nt, ns, CR);
-        if (sm <= size_t(smem_max) && !S) {
-          S = s; BM = bm; NT = nt; NS = ns; PC = pc; smem = sm;
-        }
-      }
-    }
-    if (S) break;
-  }
-  if (!S) return nfail(HMC_EINVAL, "no tile fits ldx = " + std::to_string(ldx) + " (use a multiple of 512 up to 24576)");
-  NA_CUDA(simt_prepare(HMC_F32, HMC_F32, C, smem, S));
-  int maxclu = 0;
-  NA_CUDA(simt_max_active_clusters(HMC_F32, HMC_F32, C, smem, S, NT, &maxclu));
-  if (maxclu < 1) return nfail(HMC_EUNSUPPORTED, "the fused kernel cannot be resident with this tile");
-  const int64_t ntiles = (n + BM - 1) / BM;
+  // Tile: cluster size S with column slice PC = ldx / S (no repacking of X).
+  const int64_t ntiles = (n + 7) / 8;
+  SimtTile tile{};
+  NA_CUDA(simt_choose(HMC_F32, C, p, ntiles, 0, 0, ldx, &tile));
+  if (!tile.S)
+    return nfail(HMC_EINVAL, "no tile fits ldx = " + std::to_string(ldx) + " (use a multiple of 256 up to 20480)");
+  const int S = tile.S, PC = tile.PC, NT = tile.NT, NS = tile.NSTAGE, maxclu = tile.maxclu;
+  const size_t smem = tile.smem;
 
   // Scratch layout (bytes, 256-aligned pieces).
   const size_t elems = size_t(C) * size_t(ldx);
@@ -174,10 +155,11 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
     a.C = C;
     a.Km1 = Km1;
     a.chains = chains;
-    a.BM = BM;
-    a.CR = CR;
+    a.BM = 8;
+    a.CR = 8;
     a.S = S;
     a.NT = NT;
+    a.NWL = tile.NWL;
     a.NSTAGE = NS;
     a.nclusters = int32_t(nclu);
     a.ntiles = ntiles;

@@ -63,7 +63,7 @@ def test_noalloc_rejects_oversize_and_bad_stride(cuda):
     L = hmc.lib()
     f = L.hmc_logpost_grad_noalloc
     dummy = torch.zeros(16, device=cuda)
-    # ldx not a multiple of 32
+    # ldx not a multiple of 16
     assert f(dummy.data_ptr(), 100, dummy.data_ptr(), 1, 90, 3, 0, 1.0, dummy.data_ptr(), 1, dummy.data_ptr(),
              dummy.data_ptr(), None) == hmc.EINVAL
     # intermediates beyond the static maximum: 20 columns x 24576 x 4 B x (beta, grad, one partial) > 16 MiB? no:
