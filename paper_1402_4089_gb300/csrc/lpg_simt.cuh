@@ -15,19 +15,21 @@
 //   logit group (NWL warps): sweep 1 -- lane = (row group a, phase c) holds
 //      R rows and visits the quads (4 columns) c, c+P, ... of the 32-quad
 //      spans of its warp, so each coefficient vector loaded from shared memory
-//      feeds R rows; a shuffle reduce-scatter over the P phases and a
-//      fixed-order sum over warps give the CTA's partial logits, pushed into
-//      every peer's exchange slot (st.async completing on the peer's
-//      mbarrier);
-//   gradient group (NWC warps, one per span): once every CTA's partials of a tile have
-//      arrived, sums the S partials in rank order (so all CTAs hold identical
-//      logits), forms the softmax with the fixed zero logit of class K, the
-//      residual R = Y - P and the row log-likelihood, then thread <-> quad
-//      accumulates X^T R in registers across all tiles of the cluster,
-//      without atomics, and returns the slot to the producer.
-// The logit group runs ahead (up to the ring depth) while the gradient group
-// finishes earlier tiles, so the exchange, softmax and both sweeps of
-// different tiles overlap.
+//      feeds R rows; the ring slot is released as soon as these loads are
+//      done; a shuffle reduce-scatter over the P phases and a fixed-order sum
+//      over warps give the CTA's partial logits, pushed into every peer's
+//      exchange slot (st.async completing on the peer's mbarrier);
+//   gradient group (NWC warps, one per span): once every CTA's partials of a
+//      tile have arrived, sums the S partials in rank order (so all CTAs hold
+//      identical logits), forms the softmax with the fixed zero logit of
+//      class K, the residual R = Y - P and the row log-likelihood, then
+//      thread <-> quad accumulates X^T R in registers across all tiles of the
+//      cluster, without atomics.  Its X quads are read again from global
+//      memory: the tile was streamed through L2 at most a few tiles earlier,
+//      so this is an L2 hit and HBM still sees X once.
+// The ring therefore only covers the HBM latency and sweep 1; the exchange,
+// softmax and sweep 2 of up to kNZ earlier tiles run behind it, so the
+// latency of the cluster exchange no longer holds ring slots.
 //
 // Every wait is bounded.  A wait that runs out records an error bit and the
 // role carries on (later waits are skipped), so all barriers stay matched,
@@ -41,6 +43,7 @@ namespace simt {
 
 constexpr int kMaxThreads = kSimtMaxThreads;   // 2 x 7 consumer warps + producer
 constexpr int kBM = 8;   // rows per super-tile
+constexpr int kNZ = 4;   // exchange slots: tiles the logit group may run ahead of the gradient group
 
 __device__ __forceinline__ float bf16lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
@@ -77,6 +80,53 @@ __device__ __forceinline__ void load_quad<__nv_fp8_e4m3, float>(const unsigned c
   const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
   fp8x2(v, o[0], o[1]);
   fp8x2(v >> 16, o[2], o[3]);
+}
+
+// 4 consecutive elements of X from global memory as raw 32-bit words
+// (read-only path, no L1 allocation: each word is used by one thread once).
+template <typename XT>
+__device__ __forceinline__ void ldg_quad(const XT* p, uint32_t* w);
+template <>
+__device__ __forceinline__ void ldg_quad<float>(const float* p, uint32_t* w) {
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+}
+template <>
+__device__ __forceinline__ void ldg_quad<double>(const double* p, uint32_t* w) {
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]) : "l"(p + 2));
+}
+template <>
+__device__ __forceinline__ void ldg_quad<__nv_bfloat16>(const __nv_bfloat16* p, uint32_t* w) {
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "l"(p));
+}
+template <>
+__device__ __forceinline__ void ldg_quad<__nv_fp8_e4m3>(const __nv_fp8_e4m3* p, uint32_t* w) {
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(w[0]) : "l"(p));
+}
+
+template <typename XT, typename AT>
+__device__ __forceinline__ void quad_of_words(const uint32_t* w, AT* o);
+template <>
+__device__ __forceinline__ void quad_of_words<float, float>(const uint32_t* w, float* o) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) o[j] = __uint_as_float(w[j]);
+}
+template <>
+__device__ __forceinline__ void quad_of_words<double, double>(const uint32_t* w, double* o) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) o[j] = __hiloint2double(int(w[2 * j + 1]), int(w[2 * j]));
+}
+template <>
+__device__ __forceinline__ void quad_of_words<__nv_bfloat16, float>(const uint32_t* w, float* o) {
+  o[0] = bf16lo(w[0]); o[1] = bf16hi(w[0]); o[2] = bf16lo(w[1]); o[3] = bf16hi(w[1]);
+}
+template <>
+__device__ __forceinline__ void quad_of_words<__nv_fp8_e4m3, float>(const uint32_t* w, float* o) {
+  fp8x2(w[0], o[0], o[1]);
+  fp8x2(w[0] >> 16, o[2], o[3]);
 }
 
 // N consecutive values of the state type from shared memory (16-byte aligned).
@@ -178,11 +228,11 @@ __host__ __device__ inline Layout layout(int xbytes, int abytes, int CT, int CTP
   L.xs = off;   off = align16(off + size_t(NSTAGE) * kBM * xpitch);
   L.bs = off;   off = align16(off + size_t(CT) * PC * abytes);
   L.red = off;  off = align16(off + size_t(2) * NWL * A * V * abytes);
-  L.zx = off;   off = align16(off + size_t(2) * S * kBM * CTP * abytes);
-  L.rs = off;   off = align16(off + size_t(2) * kBM * CTP * abytes);
-  L.lrow = off; off = align16(off + size_t(2) * kBM * CT * 8);
-  L.ylab = off; off = align16(off + size_t(2) * kBM * 4);
-  L.bars = off; off = align16(off + size_t(2 * NSTAGE + 6) * 8);
+  L.zx = off;   off = align16(off + size_t(kNZ) * S * kBM * CTP * abytes);
+  L.rs = off;   off = align16(off + size_t(kNZ) * kBM * CTP * abytes);
+  L.lrow = off; off = align16(off + size_t(kNZ) * kBM * CT * 8);
+  L.ylab = off; off = align16(off + size_t(kNZ) * kBM * 4);
+  L.bars = off; off = align16(off + size_t(2 * NSTAGE + 2 * kNZ + 2) * 8);
   L.total = off;
   return L;
 }
@@ -193,6 +243,7 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
   constexpr int R = Sh::R, NA = Sh::A, P = Sh::P, QPL = Sh::QPL, PV = Sh::PV, CTP = Sh::CTP, CTQ = Sh::CTQ,
                 V = Sh::V, VP = Sh::VP;
   constexpr int BM = kBM;
+  constexpr int QW = int(sizeof(XT));     // 32-bit words of one quad of X
   constexpr int MAXW = logit_warps(max_grad_warps(int(sizeof(AT)), CT));
   extern __shared__ __align__(128) unsigned char smem[];
 
@@ -212,29 +263,31 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
   AT* bs = reinterpret_cast<AT*>(smem + Lo.bs);
   AT* red = reinterpret_cast<AT*>(smem + Lo.red);
   AT* zx = reinterpret_cast<AT*>(smem + Lo.zx);
-  AT* rs = reinterpret_cast<AT*>(smem + Lo.rs);            // [2][BM][CTP] residual rows
-  double* lrow = reinterpret_cast<double*>(smem + Lo.lrow);  // [2][BM][CT] row log-likelihoods
-  int* ylab = reinterpret_cast<int*>(smem + Lo.ylab);       // [2][BM] labels
+  AT* rs = reinterpret_cast<AT*>(smem + Lo.rs);            // [kNZ][BM][CTP] residual rows
+  double* lrow = reinterpret_cast<double*>(smem + Lo.lrow);  // [kNZ][BM][CT] row log-likelihoods
+  int* ylab = reinterpret_cast<int*>(smem + Lo.ylab);       // [kNZ][BM] labels
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lo.bars);
   uint64_t* empty = full + NSTAGE;
   uint64_t* zfull = empty + NSTAGE;
-  uint64_t* zempty = zfull + 2;
-  uint64_t* never = zempty + 2;  // fault injection: a barrier no thread arrives at
+  uint64_t* zempty = zfull + kNZ;
+  uint64_t* never = zempty + kNZ;  // fault injection: a barrier no thread arrives at
   uint64_t* bbar = never + 1;    // coefficient slice landed
 
   if (tid == 0) {
+    // A ring slot is empty once every logit warp has finished sweep 1 on it
+    // (the gradient sweep reads the tile again from L2, not from the ring).
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], NWC);
+      mbar_init(&empty[s], NWL);
     }
     // Exchange slot b of tile t is full once every logit thread of this CTA
     // has arrived (labels and, for S = 1, the logits written) and, for S > 1,
     // the partials of all S CTAs have landed; it is empty once the gradient
     // group of every CTA has read it.
-    mbar_init(&zfull[0], NTL);
-    mbar_init(&zfull[1], NTL);
-    mbar_init(&zempty[0], S);
-    mbar_init(&zempty[1], S);
+    for (int b = 0; b < kNZ; ++b) {
+      mbar_init(&zfull[b], NTL);
+      mbar_init(&zempty[b], S);
+    }
     mbar_init(never, 1);
     mbar_init(bbar, 1);
     fence_mbar_init_cluster();
@@ -251,7 +304,7 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
       for (int k = lane; k < A.C; k += 32) bulk_g2s(bs + size_t(k) * PC, beta + size_t(k) * A.p_pad, rb, bbar);
     }
     for (int idx = A.C * PC + tid; idx < CT * PC; idx += NTB) bs[idx] = AT(0);
-    for (int idx = tid; idx < 2 * BM * CTP; idx += NTB) rs[idx] = AT(0);
+    for (int idx = tid; idx < kNZ * BM * CTP; idx += NTB) rs[idx] = AT(0);
     if (!mbar_wait_cta(bbar, 0u, A.spin_limit)) err0 |= ERR_TIMEOUT_STAGE;
     if (A.xscale) {
       for (int idx = tid; idx < A.C * PC; idx += NTB) {
@@ -316,7 +369,8 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
     const int ga = lane / P, gc = lane % P;        // row group, phase
     for (int64_t t = 0; t < T; ++t) {
       const int slot = int(t % NSTAGE);
-      const int buf = int(t & 1);
+      const int buf = int(t % kNZ);
+      const int rb2 = int(t & 1);          // reduction buffer
       const int rv = rows_of(t);
       // Labels of this tile: loaded now, stored with the exchange (the load's
       // latency overlaps the sweep).
@@ -353,6 +407,9 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
         }
       }
       }
+      // Sweep 1 is done with this ring slot.
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&empty[slot]);
       AT val[V];
 #pragma unroll
       for (int r = 0; r < R; ++r)
@@ -372,15 +429,16 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
         }
       }
       {
-        AT* rw = red + ((size_t(buf) * NWL + warp) * NA + ga) * V + gc * VP;
+        AT* rw = red + ((size_t(rb2) * NWL + warp) * NA + ga) * V + gc * VP;
 #pragma unroll
         for (int i = 0; i < VP; ++i) rw[i] = val[i];
       }
       group_sync(1, NTL);
 
-      // Exchange slot `buf` must have been read by every CTA (tile t - 2).
-      if (!(S > 1 ? mbar_wait_cluster(&zempty[buf], uint32_t(((t >> 1) & 1) ^ 1), lim)
-                  : mbar_wait_cta(&zempty[buf], uint32_t(((t >> 1) & 1) ^ 1), lim))) {
+      // Exchange slot `buf` must have been read by every CTA (tile t - kNZ).
+      const uint32_t zpar = uint32_t((t / kNZ) & 1);
+      if (!(S > 1 ? mbar_wait_cluster(&zempty[buf], zpar ^ 1u, lim)
+                  : mbar_wait_cta(&zempty[buf], zpar ^ 1u, lim))) {
         err |= ERR_TIMEOUT_SLOT;
         lim = 0;
       }
@@ -400,7 +458,7 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
           AT wv[MAXW];
 #pragma unroll
           for (int w = 0; w < MAXW; ++w)
-            wv[w] = (w < NWL) ? red[((size_t(buf) * NWL + w) * NA + a) * V + r * CTQ + kc] : AT(0);
+            wv[w] = (w < NWL) ? red[((size_t(rb2) * NWL + w) * NA + a) * V + r * CTQ + kc] : AT(0);
 #pragma unroll
           for (int w = 0; w < MAXW; ++w)
             if (w < NWL) sum += wv[w];
@@ -445,12 +503,22 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
     const int RPW = 32 / W, sl = lane % W;
     const int ntask = BM * chains;
 
+    const XT* Xq = static_cast<const XT*>(A.X) + size_t(rank) * PC + size_t(qq) * 4;
     for (int64_t t = 0; t < T; ++t) {
-      const int slot = int(t % NSTAGE);
-      const int buf = int(t & 1);
+      const int buf = int(t % kNZ);
       const int rv = rows_of(t);
-      if (!(S > 1 ? mbar_wait_cluster(&zfull[buf], uint32_t((t >> 1) & 1), lim)
-                  : mbar_wait_cta(&zfull[buf], uint32_t((t >> 1) & 1), lim))) {
+      // This thread's column quad of the tile's rows, read again from L2
+      // (the producer streamed the tile at most a few tiles earlier); the
+      // loads are issued before the exchange wait so their latency overlaps it.
+      uint32_t xw[BM][QW];
+      if (qq < nq) {
+        const XT* src = Xq + size_t(row0_of(t)) * A.p_pad;
+#pragma unroll
+        for (int i = 0; i < BM; ++i)
+          if (i < rv) ldg_quad<XT>(src + size_t(i) * A.p_pad, xw[i]);
+      }
+      if (!(S > 1 ? mbar_wait_cluster(&zfull[buf], uint32_t((t / kNZ) & 1), lim)
+                  : mbar_wait_cta(&zfull[buf], uint32_t((t / kNZ) & 1), lim))) {
         err |= ERR_TIMEOUT_EXCHANGE;
         lim = 0;
       }
@@ -498,11 +566,10 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
       // Sweep 2: G += X_tile^T R over the tile's rows (fixed row order;
       // rows past the end of X contribute zero).
       if (qq < nq) {
-        const unsigned char* xst = xs + size_t(slot) * BM * xpitch + size_t(qq) * 4 * sizeof(XT);
 #pragma unroll
         for (int i = 0; i < BM; ++i) {
           AT xv[4];
-          load_quad<XT, AT>(xst + size_t(i) * xpitch, xv);
+          quad_of_words<XT, AT>(xw[i], xv);
           if (i >= rv)
 #pragma unroll
             for (int q = 0; q < 4; ++q) xv[q] = AT(0);
@@ -519,8 +586,6 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
         for (int i = 0; i < rv; ++i) sl2 += lrb[size_t(i) * CT + gt];
         lacc += sl2;
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive_local(&empty[slot]);
     }
 
     if (qq < nq) {

@@ -156,6 +156,9 @@ cudaError_t simt_choose(int xt, int C, int64_t p, int64_t ntiles, int force_S, i
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   const int64_t want = std::max<int64_t>(1, ntiles);
+  int nsm = 0;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   int64_t best_active = -1;
   for (int S : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16}) {
     if (force_S && S != force_S) continue;
@@ -187,8 +190,19 @@ cudaError_t simt_choose(int xt, int C, int64_t p, int64_t ntiles, int force_S, i
         break;
       }
       if (maxclu < 1) break;
-      // Most SMs streaming X, then the smaller cluster (fewer logit exchanges).
-      const int64_t active = std::min<int64_t>(maxclu, want) * S;
+      // Most SMs streaming X (CTAs that share an SM share its issue slots and
+      // bandwidth, so they count once), then the smaller cluster (fewer logit
+      // exchanges).
+      int per_sm = 1;
+      {
+        int ct = 0;
+        simt::KernelFn fn = simt::pick(xt, C, &ct);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem) != cudaSuccess || per_sm < 1) {
+          cudaGetLastError();
+          per_sm = 1;
+        }
+      }
+      const int64_t active = std::min<int64_t>(nsm, (std::min<int64_t>(maxclu, want) * S + per_sm - 1) / per_sm);
       if (active > best_active) {
         best_active = active;
         *out = SimtTile{S, int(PC), NWC, NWL, NT, NS, smem, maxclu};
