@@ -71,8 +71,8 @@ typedef struct {
   int32_t engine;         /* 0 auto, 1 CUDA-core fused kernel, 2 tensor-core fused kernel */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
-  int32_t tile[4];        /* {cluster size, 0, 0, ring slots}; 0 = chosen (entries 1, 2 reserved, must be 0
-                             on the CUDA-core engine) */
+  int32_t tile[4];        /* {cluster size 1..16, 0, 0, ring slots}; 0 = chosen (entries 1, 2 reserved,
+                             must be 0 on the CUDA-core engine) */
 } hmc_opts;
 
 /* Per-chain counters of hmc_sample (host memory, one entry per chain). */

@@ -285,15 +285,15 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     P.ct_launch = P.group_chains * P.Km1;
     if (h->tile[1] || h->tile[2])
       return fail(HMC_EINVAL, "tile[1] and tile[2] must be 0 on the CUDA-core engine (8-row super-tiles)");
-    P.ntiles = (P.n + 7) / 8;
+    P.ntiles = (P.n + kSimtRows - 1) / kSimtRows;
     SimtTile tc{};
     HMC_CUDA(simt_choose(h->xt, P.ct_launch, P.p, P.ntiles, h->tile[0], h->tile[3], 0, &tc));
     if (!tc.S)
       return fail(HMC_EUNSUPPORTED, "no CUDA-core tile configuration fits this problem (p too large for the cluster sizes "
                                     "available, or the requested tile does not fit)");
     P.S = tc.S;
-    P.BM = 8;
-    P.CR = 8;
+    P.BM = kSimtRows;
+    P.CR = kSimtRows;
     P.NT = tc.NT;
     P.NWL = tc.NWL;
     P.NSTAGE = tc.NSTAGE;
@@ -646,8 +646,7 @@ hmc_status validate_opts(const hmc_opts* o) {
   if (o->engine < 0 || o->engine > 2) return fail(HMC_EINVAL, "opts.engine must be 0, 1 or 2");
   if (o->spin_limit < 0) return fail(HMC_EINVAL, "opts.spin_limit must be >= 0");
   const int* t = o->tile;
-  if (t[0] != 0 && t[0] != 1 && t[0] != 2 && t[0] != 4 && t[0] != 8 && t[0] != 16)
-    return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be 0, 1, 2, 4, 8 or 16");
+  if (t[0] < 0 || t[0] > 16) return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be in [0, 16]");
   if (t[1] != 0 && t[1] != 16 && t[1] != 32 && t[1] != 64)
     return fail(HMC_EINVAL, "opts.tile[1] (rows per super-tile) must be 0, 16, 32 or 64");
   if (t[2] != 0 && t[2] != 8 && t[2] != 16 && t[2] != 32)

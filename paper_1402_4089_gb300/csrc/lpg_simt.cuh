@@ -42,7 +42,7 @@ namespace hmc {
 namespace simt {
 
 constexpr int kMaxThreads = kSimtMaxThreads;   // 2 x 7 consumer warps + producer
-constexpr int kBM = 8;   // rows per super-tile
+constexpr int kBM = kSimtRows;   // rows per super-tile
 constexpr int kNZ = 4;   // exchange slots: tiles the logit group may run ahead of the gradient group
 
 __device__ __forceinline__ float bf16lo(uint32_t u) { return __uint_as_float(u << 16); }
@@ -129,6 +129,40 @@ __device__ __forceinline__ void quad_of_words<__nv_fp8_e4m3, float>(const uint32
   fp8x2(w[0] >> 16, o[2], o[3]);
 }
 
+// Packed FP32 pairs (f32x2): one instruction issues two IEEE fused
+// multiply-adds, so the FP32 sweeps need half the FMA issue slots.  The low
+// half of the 64-bit register is the first element.
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+  return f;
+}
+
+// 4 consecutive elements of X in shared memory as two FP32 pairs (x0,x1), (x2,x3).
+template <typename XT>
+__device__ __forceinline__ void load_quad2(const unsigned char* p, uint64_t* o) {
+  if constexpr (sizeof(XT) == 4) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+  } else {
+    float f[4];
+    load_quad<XT, float>(p, f);
+    o[0] = pack2(f[0], f[1]);
+    o[1] = pack2(f[2], f[3]);
+  }
+}
+
 // N consecutive values of the state type from shared memory (16-byte aligned).
 template <typename AT, int N>
 __device__ __forceinline__ void load_vec(const AT* p, AT* o) {
@@ -186,7 +220,7 @@ __host__ __device__ constexpr ShapeRT shape_rt(int abytes, int CT) {
   s.QPL = 32 / s.P;
   s.PV = 16 / abytes;
   s.CTP = ((CT + s.PV - 1) / s.PV) * s.PV;
-  int c = CT;
+  int c = s.CTP;
   while ((s.R * c) % s.P) ++c;
   s.CTQ = c;
   s.V = s.R * s.CTQ;
@@ -244,6 +278,7 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
                 V = Sh::V, VP = Sh::VP;
   constexpr int BM = kBM;
   constexpr int QW = int(sizeof(XT));     // 32-bit words of one quad of X
+  constexpr int XB = BM < 8 ? BM : 8;     // rows of X a gradient thread holds in registers
   constexpr int MAXW = logit_warps(max_grad_warps(int(sizeof(AT)), CT));
   extern __shared__ __align__(128) unsigned char smem[];
 
@@ -382,30 +417,68 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
       }
       const unsigned char* xst = xs + size_t(slot) * BM * xpitch;
       AT acc[R][CT];
+      if constexpr (sizeof(AT) == 4) {
+        // FP32 state: even and odd columns accumulate in the two halves of
+        // an f32x2 pair, added at the end.
+        uint64_t acc2[R][CT];
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < CT; ++c) acc[r][c] = AT(0);
-      for (int q0 = warp * 32; q0 < nq; q0 += NWL * 32) {
+          for (int c = 0; c < CT; ++c) acc2[r][c] = 0ull;
+        for (int q0 = warp * 32; q0 < nq; q0 += NWL * 32) {
 #pragma unroll
-      for (int m = 0; m < QPL; ++m) {
-        const int q = q0 + gc + m * P;
-        if (q < nq) {
-          AT xv[R][4];
+          for (int m = 0; m < QPL; ++m) {
+            const int q = q0 + gc + m * P;
+            if (q < nq) {
+              uint64_t xv[R][2];
 #pragma unroll
-          for (int r = 0; r < R; ++r)
-            load_quad<XT, AT>(xst + size_t(ga * R + r) * xpitch + size_t(q) * 4 * sizeof(XT), xv[r]);
+              for (int r = 0; r < R; ++r)
+                load_quad2<XT>(xst + size_t(ga * R + r) * xpitch + size_t(q) * 4 * sizeof(XT), xv[r]);
 #pragma unroll
-          for (int c = 0; c < CT; ++c) {
-            AT b[4];
-            load_vec<AT, 4>(bs + size_t(c) * PC + 4 * q, b);
+              for (int c = 0; c < CT; ++c) {
+                const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(bs + size_t(c) * PC + 4 * q);
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) acc[r][c] = fma(xv[r][j], b[j], acc[r][c]);
+                for (int r = 0; r < R; ++r) {
+                  acc2[r][c] = ffma2(xv[r][0], b.x, acc2[r][c]);
+                  acc2[r][c] = ffma2(xv[r][1], b.y, acc2[r][c]);
+                }
+              }
+            }
           }
         }
-      }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < CT; ++c) {
+            const float2 f = unpack2(acc2[r][c]);
+            acc[r][c] = AT(f.x + f.y);
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < CT; ++c) acc[r][c] = AT(0);
+        for (int q0 = warp * 32; q0 < nq; q0 += NWL * 32) {
+#pragma unroll
+          for (int m = 0; m < QPL; ++m) {
+            const int q = q0 + gc + m * P;
+            if (q < nq) {
+              AT xv[R][4];
+#pragma unroll
+              for (int r = 0; r < R; ++r)
+                load_quad<XT, AT>(xst + size_t(ga * R + r) * xpitch + size_t(q) * 4 * sizeof(XT), xv[r]);
+#pragma unroll
+              for (int c = 0; c < CT; ++c) {
+                AT b[4];
+                load_vec<AT, 4>(bs + size_t(c) * PC + 4 * q, b);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) acc[r][c] = fma(xv[r][j], b[j], acc[r][c]);
+              }
+            }
+          }
+        }
       }
       // Sweep 1 is done with this ring slot.
       __syncwarp();
@@ -491,11 +564,19 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
     // ---------------------------------------------------------------- gradient group
     const int gw = warp - NWL, gt = tid - NTL;     // warp / thread within the group
     const int qq = gw * 32 + lane;                 // this thread's quad
-    AT G[4][CT];
+    // FP32 state: class pairs (c, c+1) of a column accumulate in one f32x2
+    // register (CTH pairs per column); FP64 state: one register per class.
+    constexpr int CTH = (CT + 1) / 2;
+    constexpr bool kPair = sizeof(AT) == 4;
+    uint64_t G2[4][kPair ? CTH : 1];
+    AT G[4][kPair ? 1 : CT];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q) {
 #pragma unroll
-      for (int k = 0; k < CT; ++k) G[q][k] = AT(0);
+      for (int k = 0; k < (kPair ? CTH : 1); ++k) G2[q][k] = 0ull;
+#pragma unroll
+      for (int k = 0; k < (kPair ? 1 : CT); ++k) G[q][k] = AT(0);
+    }
     double lacc = 0.0;
     const int Km1 = A.Km1, chains = A.chains;
     int W = 1;
@@ -510,11 +591,12 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
       // This thread's column quad of the tile's rows, read again from L2
       // (the producer streamed the tile at most a few tiles earlier); the
       // loads are issued before the exchange wait so their latency overlaps it.
-      uint32_t xw[BM][QW];
+      // Up to XB rows are in flight; row i + XB is loaded once row i is used.
+      uint32_t xw[XB][QW];
+      const XT* src = Xq + size_t(row0_of(t)) * A.p_pad;
       if (qq < nq) {
-        const XT* src = Xq + size_t(row0_of(t)) * A.p_pad;
 #pragma unroll
-        for (int i = 0; i < BM; ++i)
+        for (int i = 0; i < XB; ++i)
           if (i < rv) ldg_quad<XT>(src + size_t(i) * A.p_pad, xw[i]);
       }
       if (!(S > 1 ? mbar_wait_cluster(&zfull[buf], uint32_t((t / kNZ) & 1), lim)
@@ -569,16 +651,33 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
 #pragma unroll
         for (int i = 0; i < BM; ++i) {
           AT xv[4];
-          quad_of_words<XT, AT>(xw[i], xv);
+          quad_of_words<XT, AT>(xw[i % XB], xv);
+          if (i + XB < BM && i + XB < rv) ldg_quad<XT>(src + size_t(i + XB) * A.p_pad, xw[i % XB]);
           if (i >= rv)
 #pragma unroll
             for (int q = 0; q < 4; ++q) xv[q] = AT(0);
-          AT r[CTP];
-          load_vec<AT, CTP>(rsb + size_t(i) * CTP, r);
+          if constexpr (kPair) {
+            uint64_t r2[CTP / 2];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+            for (int k = 0; k < CTP / 4; ++k) {
+              const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(rsb + size_t(i) * CTP + 4 * k);
+              r2[2 * k] = v.x;
+              r2[2 * k + 1] = v.y;
+            }
 #pragma unroll
-            for (int c = 0; c < CT; ++c) G[q][c] = fma(xv[q], r[c], G[q][c]);
+            for (int q = 0; q < 4; ++q) {
+              const uint64_t xd = pack2(float(xv[q]), float(xv[q]));
+#pragma unroll
+              for (int k = 0; k < CTH; ++k) G2[q][k] = ffma2(xd, r2[k], G2[q][k]);
+            }
+          } else {
+            AT r[CTP];
+            load_vec<AT, CTP>(rsb + size_t(i) * CTP, r);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int c = 0; c < CT; ++c) G[q][c] = fma(xv[q], r[c], G[q][c]);
+          }
         }
       }
       if (rank == 0 && gt < chains) {
@@ -599,9 +698,15 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
       for (int kk = 0; kk < CT; ++kk) {
         if (kk < A.C) {
           AT* d = gp + size_t(kk) * A.p_pad + col;
-          if constexpr (sizeof(AT) == 4) {
-            *reinterpret_cast<float4*>(d) = make_float4(float(G[0][kk] * sc[0]), float(G[1][kk] * sc[1]),
-                                                        float(G[2][kk] * sc[2]), float(G[3][kk] * sc[3]));
+          if constexpr (kPair) {
+            float g[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float2 f = unpack2(G2[q][kk / 2]);
+              g[q] = (kk & 1) ? f.y : f.x;
+            }
+            *reinterpret_cast<float4*>(d) = make_float4(g[0] * float(sc[0]), g[1] * float(sc[1]),
+                                                        g[2] * float(sc[2]), g[3] * float(sc[3]));
           } else {
             reinterpret_cast<double2*>(d)[0] = make_double2(double(G[0][kk] * sc[0]), double(G[1][kk] * sc[1]));
             reinterpret_cast<double2*>(d)[1] = make_double2(double(G[2][kk] * sc[2]), double(G[3][kk] * sc[3]));

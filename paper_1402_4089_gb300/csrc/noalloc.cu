@@ -92,7 +92,7 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
 
   // Tile: cluster size S with column slice PC = ldx / S (no repacking of X).
-  const int64_t ntiles = (n + 7) / 8;
+  const int64_t ntiles = (n + kSimtRows - 1) / kSimtRows;
   SimtTile tile{};
   NA_CUDA(simt_choose(HMC_F32, C, p, ntiles, 0, 0, ldx, &tile));
   if (!tile.S)

@@ -62,7 +62,7 @@ def test_create_rejects_bad_opts(hmclib):
     o.x_storage = hmc.F64               # F64 storage needs F64 state
     assert _create(opts=o)[0] == hmc.EINVAL
     o = hmc.default_opts()
-    o.tile[0] = 3                        # cluster sizes are powers of two up to 16
+    o.tile[0] = 17                       # cluster sizes are 1..16
     assert _create(opts=o)[0] == hmc.EINVAL
 
 
