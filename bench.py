@@ -33,7 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "gradient evals/s"
 UNIT = "grad_evals/s"
 XBYTES = {"f64": 8, "f32": 4, "bf16": 2, "fp8": 1}
-KERNEL_SOURCES = ["paper_1402_4089_gb300/csrc/lpg_simt.cuh", "paper_1402_4089_gb300/csrc/device_common.cuh"]
+# Sources of each engine's fused kernel: a recorded DRAM-traffic figure is used
+# only while these files are unchanged since the ncu capture.
+KERNEL_SOURCES = {
+    "simt": ["paper_1402_4089_gb300/csrc/lpg_simt.cuh", "paper_1402_4089_gb300/csrc/device_common.cuh"],
+    "tcgen05": ["paper_1402_4089_gb300/csrc/lpg_tc.cu", "paper_1402_4089_gb300/csrc/tc_common.cuh",
+                "paper_1402_4089_gb300/csrc/device_common.cuh"],
+}
 
 
 def parse_args():
@@ -151,15 +157,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(engine):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES[engine]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
+def recorded_traffic(workload, engine):
     """DRAM bytes per fused launch from a committed ncu summary, if it was taken on the
     current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -168,7 +174,7 @@ def recorded_traffic(workload):
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload)
-    if not e or e.get("source_sha") != kernel_source_hash():
+    if not e or e.get("engine") != engine or e.get("source_sha") != kernel_source_hash(engine):
         return None
     return e.get("bytes_per_launch")
 
@@ -269,7 +275,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, desc_all["engine"]),
             "kernel": ("lpg_tc_kernel (tcgen05)" if h.describe()["engine"] == "tcgen05" else "lpg_kernel (CUDA cores)")
             + f" X={xdt} C={c_launch}", "avg_launch_us": round(avg_launch_s * 1e6, 2),
             "launches_timed": fused_n, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
