@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's tile choice instead of measuring")
+    ap.add_argument("--ess-iters", type=int, default=200, help="HMC iterations of the ESS/s run (0: skip)")
     return ap.parse_args()
 
 
@@ -207,7 +209,7 @@ def cpu_baseline(X64, y, spec, seconds):
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
-    from paper_1402_4089_gb300 import build, hmc, synthetic
+    from paper_1402_4089_gb300 import build, diagnostics, hmc, synthetic, tune
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,8 +231,15 @@ def run_ours(args):
     state = "f64" if xdt == "f64" else "f32"
     tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
     stream = torch.cuda.Stream(device=dev)
-    h = hmc.create(X if xdt != "f64" else X.astype(np.float64), y, K, kind, scale, x_storage=xdt, state=state,
-                   max_chains=chains, stream=stream, tile=tile)
+    Xin = X if xdt != "f64" else X.astype(np.float64)
+    tile_source, tune_table = ("given", None) if tile else ("library", None)
+    if tile is None and not args.no_autotune:
+        with torch.cuda.stream(stream):
+            t_tile, tune_table = tune.autotune(Xin, y, K, kind, scale, x_storage=xdt, state=state, chains=chains,
+                                               stream=stream)
+        if t_tile is not None:
+            tile, tile_source = t_tile, "autotuned"
+    h = hmc.create(Xin, y, K, kind, scale, x_storage=xdt, state=state, max_chains=chains, stream=stream, tile=tile)
     desc_all = h.describe()
     desc = desc_all["problems"][0]
     tdt = torch.float64 if state == "f64" else torch.float32
@@ -309,6 +318,33 @@ def run_ours(args):
                "note": "per step: upload the chain state (pinned host), one HMC iteration from it (plus the "
                        "gradient at the uploaded state), read the sample back"}
 
+    # effective samples per second: a fresh run from beta = 0, draws kept on the device
+    ess_info = None
+    if args.ess_iters > 0:
+        iters = args.ess_iters
+        draws = torch.empty((iters, chains, K - 1, p), dtype=tdt, device=dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.sample(chains, L, eps, iters, seed + 7, beta0=zeros, samples=draws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        burn = iters // 10
+        flat = draws[burn:].reshape(iters - burn, chains, -1)
+        m = flat.shape[2]
+        if m > 20000:      # a seeded subset of coordinates keeps the host-side FFTs small
+            idx = torch.from_numpy(np.sort(np.random.default_rng(0).choice(m, 20000, replace=False))).to(dev)
+            flat = flat[:, :, idx]
+        ess = diagnostics.ess(flat.double().cpu().numpy())
+        ess_info = {"iters": iters, "burn_in": burn, "coords": int(ess.size), "min": round(float(ess.min()), 2),
+                    "median": round(float(np.median(ess)), 2), "seconds": round(secs, 4),
+                    "min_per_s": round(float(ess.min()) / secs, 3), "median_per_s": round(float(np.median(ess)) / secs, 3),
+                    "note": "from beta = 0 over all iterations' sampling time; Geyer initial monotone sequence on the "
+                            "draws after burn-in, chains pooled"}
+        del draws, flat
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         X64 = X.astype(np.float64)
@@ -322,7 +358,8 @@ def run_ours(args):
         "high-dimensional multinomial setting)", "config": config_of(args, spec, n * p * xb),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
         "xpass_gbs": round(achieved, 1), "accept_rate": round(acc, 4), "impl": "ours",
-        "clocks": clk.summary(), "engine": desc_all["engine"],
+        "clocks": clk.summary(), "engine": desc_all["engine"], "ess": ess_info, "tile_source": tile_source,
+        "tune": sorted(tune_table, key=lambda r: r["us"])[:6] if tune_table else None,
         "tile": {k: desc[k] for k in ("S", "BM", "CR", "NSTAGE", "PC", "nclusters", "group_chains", "smem") if k in desc},
     }
     if rank == 0:

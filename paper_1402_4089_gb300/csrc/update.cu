@@ -81,8 +81,19 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
     const int j = int(e % A.p_pad);
     if (j >= A.p) continue;  // padding columns stay zero
     const size_t idx = base + size_t(e);
+    // Fixed-order sum over the partials (b ascending); the loads of a group
+    // of 8 are issued together, the additions stay in order.
     ST g = ST(0);
-    for (int b = 0; b < A.nparts; ++b) g += gp[size_t(b) * A.gpart_cstride + idx];
+    const ST* gpi = gp + idx;
+    int b = 0;
+    for (; b + 8 <= A.nparts; b += 8) {
+      ST v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = gpi[size_t(b + k) * A.gpart_cstride];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) g += v[k];
+    }
+    for (; b < A.nparts; ++b) g += gpi[size_t(b) * A.gpart_cstride];
     const ST bv = beta[idx];
     g += prior_deriv(bv, A.prior_kind, A.prior_scale);
     grad[idx] = g;
@@ -330,9 +341,10 @@ int grid_for(int64_t work, int cap = 4096) {
 }  // namespace
 
 int update_blocks_per_chain(int64_t per_chain) {
-  int64_t g = (per_chain + 4 * kThreads - 1) / (4 * kThreads);
+  // About one coefficient per thread: the split-K sum is latency-bound.
+  int64_t g = (per_chain + kThreads - 1) / kThreads;
   if (g < 1) g = 1;
-  if (g > 256) g = 256;
+  if (g > 1024) g = 1024;
   return int(g);
 }
 

@@ -1,0 +1,125 @@
+"""Tile autotuner for the fused log-posterior + gradient pass.
+
+The library picks a tile (cluster size S, ring slots) from an occupancy model;
+this module measures instead.  For one problem shape it creates a handle per
+candidate tile, times the fused pass with the library's own CUDA-event timer
+(events on the handle's stream around each fused launch) and keeps the
+fastest.  Results are cached per device and problem shape in a JSON file
+(``HMC_TUNE_CACHE``, default ``~/.cache/paper_1402_4089_gb300/tune.json``).
+
+The figure of merit is the fused-kernel time of one call for all chains (a
+tile that fits fewer chains per launch pays for more launches).
+
+Candidates: CUDA-core engine, S in {1, 2, 3, 4, 5, 6, 8, 10, 12, 16} x ring
+slots {2, 3, 4}; tensor-core engine (BF16 X), S in {16, 8, 4, 2, 1} x ring
+slots {2, 3, 4}.  Tiles the library rejects for the shape are skipped.
+"""
+import json
+import os
+
+import numpy as np
+
+from . import hmc
+
+SIMT_S = (1, 2, 3, 4, 5, 6, 8, 10, 12, 16)
+TC_S = (16, 8, 4, 2, 1)
+RING = (2, 3, 4)
+
+
+def _cache_path():
+    p = os.environ.get("HMC_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_1402_4089_gb300", "tune.json")
+
+
+def _key(device_name, n, p, K, x_storage, state, chains, engine):
+    return f"{device_name}|n={n}|p={p}|K={K}|x={x_storage}|st={state}|chains={chains}|engine={engine}"
+
+
+def _load():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d):
+    p = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, engine, tile, stream=None, reps=5, warmup=2):
+    """Median time (us) of the fused launches of one log-posterior + gradient call for all
+    `chains` (a tile may split the chains into several launches), or None if the library
+    rejects the tile."""
+    import torch
+    try:
+        h = hmc.create(X, y, K, prior, prior_scale, x_storage=x_storage, state=state, max_chains=chains,
+                       engine=engine, stream=stream, tile=tile)
+    except hmc.HmcError:
+        return None, None
+    try:
+        d = h.describe()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        p = int(X.shape[1])
+        beta = torch.zeros((chains, K - 1, p), dtype=h.torch_dtype(), device=dev)
+        for _ in range(warmup):
+            h.logpost_grad(beta)
+        times = []
+        for _ in range(reps):
+            h.set_timing(True)          # resets the accumulated time
+            h.logpost_grad(beta)
+            torch.cuda.synchronize()
+            ms, _ = h.fused_kernel_time()
+            times.append(ms * 1e3)
+        h.set_timing(False)
+        return float(np.median(times)), d
+    finally:
+        h.close()
+
+
+def autotune(X, y, K, prior="gaussian", prior_scale=1.0, x_storage="f32", state="f32", chains=1, engine=0,
+             stream=None, reps=5, use_cache=True, verbose=False):
+    """Fastest tile for this problem: returns (tile tuple for hmc.create, table of measurements)."""
+    import torch
+    n, p = int(X.shape[0]), int(X.shape[1])
+    eng = engine
+    if eng == 0:
+        eng = 2 if x_storage == "bf16" else 1
+    key = _key(torch.cuda.get_device_name(), n, p, K, x_storage, state, chains, eng)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        e = cache[key]
+        return tuple(e["tile"]), e.get("table", [])
+    table = []
+    S_list = TC_S if eng == 2 else SIMT_S
+    for S in S_list:
+        for ns in RING:
+            us, d = time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, eng, (S, 0, 0, ns),
+                              stream=stream, reps=reps)
+            if us is None:
+                continue
+            pr = d["problems"][0]
+            row = dict(S=S, ring=ns, us=round(us, 2), clusters=pr.get("nclusters"), smem=pr.get("smem"))
+            table.append(row)
+            if verbose:
+                print("tune", json.dumps(row), flush=True)
+    if not table:
+        # The engine cannot run this shape with an explicit tile: leave the choice to the library.
+        return None, table
+    best = min(table, key=lambda r: r["us"])
+    tile = (best["S"], 0, 0, best["ring"])
+    if use_cache:
+        cache = _load()
+        cache[key] = dict(tile=list(tile), table=table)
+        _store(cache)
+    return tile, table
