@@ -54,7 +54,9 @@ def e4m3_table():
 
 def e4m3_encode(v):
     """uint8 codes of float32 values: nearest E4M3 value, ties to the even
-    (low mantissa bit 0) code, saturating to +-448."""
+    (low mantissa bit 0) code, saturating to +-448.  E4M3 is sign-magnitude
+    with a negative zero (code 0x80); as in IEEE 754 conversions, a result
+    that rounds to zero keeps the operand's sign."""
     v = np.asarray(v, dtype=np.float64)
     table = e4m3_table()
     pos_codes = np.arange(0, 0x7F)                       # 0x00..0x7E: +0 .. +448
@@ -69,7 +71,7 @@ def e4m3_encode(v):
     take_hi = take_hi | (tie & hi_even)
     code = np.where(take_hi, pos_codes[idx], pos_codes[idx - 1])
     code = np.where(a == 0.0, 0, code)
-    sign = (np.signbit(v) & (code != 0)).astype(np.int64) << 7
+    sign = np.signbit(v).astype(np.int64) << 7
     return (code | sign).astype(np.uint8)
 
 

@@ -324,6 +324,10 @@ def test_e4m3_table_and_rounding():
     # 1.1875 is halfway between 1.125 (m=1) and 1.25 (m=2): -> 1.25
     # 2^-10 is halfway between 0 and 2^-9 (m=1): -> 0; 3*2^-10 between m=1 and m=2 -> m=2
     assert list(quant.e4m3_decode(codes)) == [1.0, 1.0, 1.25, 448.0, -448.0, 0.0, 2 * 2 ** -9, 0.0]
+    # signed zero: -0.0 and a negative value that rounds to zero keep the sign (code 0x80)
+    z = quant.e4m3_encode(np.array([0.0, -0.0, -2 ** -11, 2 ** -11]))
+    assert list(z) == [0x00, 0x80, 0x80, 0x00]
+    assert np.signbit(quant.e4m3_decode(z)).tolist() == [False, True, True, False]
 
 
 def test_fp8_column_scales_reconstruct():
