@@ -233,13 +233,15 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     Xin = X if xdt != "f64" else X.astype(np.float64)
     tile_source, tune_table = ("given", None) if tile else ("library", None)
+    engine = 0
     if tile is None and not args.no_autotune:
         with torch.cuda.stream(stream):
-            t_tile, tune_table = tune.autotune(Xin, y, K, kind, scale, x_storage=xdt, state=state, chains=chains,
-                                               stream=stream)
+            t_eng, t_tile, tune_table = tune.autotune(Xin, y, K, kind, scale, x_storage=xdt, state=state,
+                                                      chains=chains, stream=stream)
         if t_tile is not None:
-            tile, tile_source = t_tile, "autotuned"
-    h = hmc.create(Xin, y, K, kind, scale, x_storage=xdt, state=state, max_chains=chains, stream=stream, tile=tile)
+            engine, tile, tile_source = t_eng, t_tile, "autotuned"
+    h = hmc.create(Xin, y, K, kind, scale, x_storage=xdt, state=state, max_chains=chains, stream=stream, tile=tile,
+                   engine=engine)
     desc_all = h.describe()
     desc = desc_all["problems"][0]
     tdt = torch.float64 if state == "f64" else torch.float32

@@ -68,7 +68,9 @@ typedef struct {
   hmc_dtype x_storage;    /* storage type of X on the device (default HMC_F32)   */
   hmc_dtype state;        /* HMC_F64 or HMC_F32 (default HMC_F32)                */
   int32_t max_chains;     /* largest `chains` any later call may pass (default 1) */
-  int32_t engine;         /* 0 auto, 1 CUDA-core fused kernel, 2 tensor-core fused kernel */
+  int32_t engine;         /* 0 auto (tensor cores for BF16 / FP8 storage when the chains' columns fit
+                             TMEM, else CUDA cores), 1 CUDA-core fused kernel, 2 tensor-core fused
+                             kernel (BF16 or FP8 storage; MMA operands BF16, FP32 accumulation) */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
   int32_t tile[4];        /* {cluster size 1..16, 0, 0, ring slots}; 0 = chosen (entries 1, 2 reserved,

@@ -94,6 +94,28 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint3
       : "memory");
 }
 
+// Order this thread's generic-proxy shared-memory writes before later async-proxy reads.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Four E4M3 values (bytes of w, byte 0 first) -> four BF16 values as two
+// bf16x2 words (element 0 in the low half of lo).  Exact: E4M3 -> FP16 by the
+// hardware conversion, then FP16 -> BF16 by moving the fields (every E4M3
+// value is a normal FP16 number whose significand fits BF16's 7 bits; the
+// exponent bias grows from 15 to 127).  Zero stays zero; X is finite.
+__device__ __forceinline__ uint32_t f16x2_to_bf16x2_exact(uint32_t h) {
+  const uint32_t sign = h & 0x80008000u;
+  const uint32_t mag = h & 0x7fff7fffu;
+  const uint32_t t = ((mag >> 3) & 0x0fff0fffu) + 0x38003800u;
+  const uint32_t nz = __vcmpne2(mag, 0u);
+  return (t & nz) | sign;
+}
+__device__ __forceinline__ void fp8x4_to_bf16x4(uint32_t w, uint32_t& lo, uint32_t& hi) {
+  const __half2_raw a = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w & 0xffffu), __NV_E4M3);
+  const __half2_raw b = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w >> 16), __NV_E4M3);
+  lo = f16x2_to_bf16x2_exact(uint32_t(a.x) | (uint32_t(a.y) << 16));
+  hi = f16x2_to_bf16x2_exact(uint32_t(b.x) | (uint32_t(b.y) << 16));
+}
+
 // Bulk prefetch of a contiguous global range into L2 (16-byte aligned address,
 // bytes a multiple of 16); no shared memory and no completion to wait for.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* gsrc, uint32_t bytes) {

@@ -222,7 +222,7 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
         if (h->tile[3] && s != h->tile[3]) continue;
         // At least half of an SM's shared memory: one CTA per SM, so no CTA
         // ever waits for TMEM held by a CTA of another cluster.
-        const size_t sm = std::max(tc_smem_bytes(pl, s, g), size_t(116 * 1024));
+        const size_t sm = std::max(tc_smem_bytes(pl, s, g, h->xt == HMC_FP8E4M3), size_t(116 * 1024));
         if (sm <= size_t(smem_max)) {
           nst = s;
           smem = sm;
@@ -230,9 +230,9 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
         }
       }
       if (!nst) continue;
-      HMC_CUDA(tc_prepare(smem, S));
+      HMC_CUDA(tc_prepare(smem, S, h->xt == HMC_FP8E4M3));
       int maxclu = 0;
-      if (tc_max_active_clusters(smem, S, &maxclu) != cudaSuccess) {
+      if (tc_max_active_clusters(smem, S, h->xt == HMC_FP8E4M3, &maxclu) != cudaSuccess) {
         cudaGetLastError();
         maxclu = 0;
       }
@@ -259,12 +259,12 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
   P.p_pad = best.S * best.PC;
   P.BM = 128;
   P.CR = 128;
-  P.NT = 192;
+  P.NT = tc_threads(h->xt == HMC_FP8E4M3);
   P.NSTAGE = best_nst;
   P.smem = best_smem;
   P.ntiles = (P.n + 127) / 128;
   P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>(best_maxclu, P.ntiles)));
-  HMC_CUDA(tc_prepare(P.smem, P.S));
+  HMC_CUDA(tc_prepare(P.smem, P.S, h->xt == HMC_FP8E4M3));
   *ok = true;
   return HMC_OK;
 }
@@ -272,10 +272,10 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
 hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, const int32_t* y) {
   const int xb = dtype_bytes(h->xt);
   bool tc_ok = false;
-  if (h->xt == HMC_BF16 && h->engine != 1 && P.n > 0) HMC_TRY(choose_tc(h, P, &tc_ok));
+  if ((h->xt == HMC_BF16 || h->xt == HMC_FP8E4M3) && h->engine != 1 && P.n > 0) HMC_TRY(choose_tc(h, P, &tc_ok));
   if (h->engine == 2 && !tc_ok)
-    return fail(HMC_EUNSUPPORTED, "the tensor-core engine needs BF16 storage of X, n > 0 and chains * (K-1) columns "
-                                  "that fit TMEM next to the cluster's gradient slice");
+    return fail(HMC_EUNSUPPORTED, "the tensor-core engine needs BF16 or FP8 storage of X, n > 0 and chains * (K-1) "
+                                  "columns that fit TMEM next to the cluster's gradient slice");
   if (!tc_ok) {
     const int maxct = simt_max_ct(h->xt);
     if (P.Km1 > maxct)
@@ -320,7 +320,9 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(launch_fp8_scales(x_dtype, Xd, P.xscale, P.n, P.p, P.p_pad, h->stream));
   }
   if (P.n > 0) {
-    if (P.engine == 2)
+    if (P.engine == 2 && h->xt == HMC_FP8E4M3)
+      HMC_CUDA(tc_x_to_tiles_fp8(x_dtype, Xd, P.xscale, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
+    else if (P.engine == 2)
       HMC_CUDA(tc_x_to_tiles(x_dtype, Xd, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
     else
       HMC_CUDA(launch_convert_x(x_dtype, Xd, h->xt, P.X, P.xscale, P.n, P.p, P.p_pad, h->err_d, h->stream));
@@ -412,7 +414,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     void* gpart = static_cast<char*>(P.gpart) + size_t(c0) * P.Km1 * P.p_pad * sb;
     const bool inject = h->inject_timeout;
     h->inject_timeout = false;
-    if (P.engine == 2) HMC_CUDA(tc_beta_to_tiles(static_cast<const float*>(beta), P.bbf, C, P.tp.N, P.p_pad, stream));
+    if (P.engine == 2)
+      HMC_CUDA(tc_beta_to_tiles(static_cast<const float*>(beta), P.xscale, P.bbf, C, P.tp.N, P.p_pad, stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     // Inside a stream capture the events must become graph nodes.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -426,6 +429,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     if (P.engine == 2) {
       TcLaunch L{};
       L.xs = P.X;
+      L.xscale = P.xscale;
+      L.fp8 = h->xt == HMC_FP8E4M3 ? 1 : 0;
       L.bs = P.bbf;
       L.n = P.n;
       L.p_pad = P.p_pad;
@@ -730,7 +735,8 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
   }
   // A batch on the CUDA-core engine shares one cluster size (the largest any
   // problem needs) so that one fused launch can serve every problem.
-  const bool want_batch = nprob > 1 && !(h->xt == HMC_BF16 && h->engine != 1) && !h->tile[0];
+  const bool want_batch =
+      nprob > 1 && !((h->xt == HMC_BF16 || h->xt == HMC_FP8E4M3) && h->engine != 1) && !h->tile[0];
   if (want_batch) {
     // Smallest cluster whose column slices fit the block for every problem.
     int S = 1;
@@ -1131,7 +1137,7 @@ hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales) {
   if (P.n > 0 && P.engine == 2) {
     void* tmp = nullptr;
     HMC_CUDA(cudaMalloc(&tmp, size_t(P.n) * P.p * xb));
-    cudaError_t e = tc_tiles_to_rows(P.X, tmp, P.n, P.p, P.p_pad, h->stream);
+    cudaError_t e = tc_tiles_to_rows(P.X, tmp, P.n, P.p, P.p_pad, h->xt == HMC_FP8E4M3, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, size_t(P.n) * P.p * xb, cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);

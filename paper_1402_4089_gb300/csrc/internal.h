@@ -73,13 +73,15 @@ cudaError_t simt_max_active_clusters_batched(int xt, int C, size_t smem, int S, 
 cudaError_t simt_launch_batched(int xt, int C, const LpgArgs* table, const int* first, int nprob, int chains,
                                 int total_clusters, int S, int NT, size_t smem, cudaStream_t stream);
 
-// Tensor-core fused kernel (BF16 X, tcgen05 + TMEM + TMA), lpg_tc.cu.
+// Tensor-core fused kernel (BF16 or FP8 X, tcgen05 + TMEM + bulk copies), lpg_tc.cu.
 struct TcPlan {
   int N, NP, PC, MB, S;
   uint32_t tmem_cols, stage_bytes;
 };
 struct TcLaunch {
-  const void* xs;           // X boxes (tc_x_to_tiles layout)
+  const void* xs;           // X boxes (tc_x_to_tiles / tc_x_to_tiles_fp8 layout)
+  const float* xscale;      // FP8 column scales (nullptr for BF16)
+  int32_t fp8;
   const void* bs;           // coefficient operand boxes (tc_beta_to_tiles layout)
   int64_t n;
   int32_t p_pad, C, Km1, chains, NST, nclusters;
@@ -93,13 +95,18 @@ struct TcLaunch {
   int32_t inject_timeout;
 };
 bool tc_plan(int64_t p, int C, int S, TcPlan* out);
-size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains);
-cudaError_t tc_prepare(size_t smem, int S);
-cudaError_t tc_max_active_clusters(size_t smem, int S, int* out);
+size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains, bool fp8);
+int tc_threads(bool fp8);                   // threads of one CTA (FP8 adds converter warps)
+cudaError_t tc_prepare(size_t smem, int S, bool fp8);
+cudaError_t tc_max_active_clusters(size_t smem, int S, bool fp8, int* out);
 cudaError_t tc_x_to_tiles(int in_dtype, const void* X, void* out, int64_t n, int32_t p, int32_t p_pad, int* err,
                           cudaStream_t s);
-cudaError_t tc_tiles_to_rows(const void* tiles, void* out_bits, int64_t n, int32_t p, int32_t p_pad, cudaStream_t s);
-cudaError_t tc_beta_to_tiles(const float* beta, void* out, int C, int N, int p_pad, cudaStream_t s);
+cudaError_t tc_x_to_tiles_fp8(int in_dtype, const void* X, const float* scales, void* out, int64_t n, int32_t p,
+                              int32_t p_pad, int* err, cudaStream_t s);
+cudaError_t tc_tiles_to_rows(const void* tiles, void* out_bits, int64_t n, int32_t p, int32_t p_pad, bool fp8,
+                             cudaStream_t s);
+cudaError_t tc_beta_to_tiles(const float* beta, const float* scales, void* out, int C, int N, int p_pad,
+                             cudaStream_t s);
 cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStream_t stream);
 
 // Element-wise / reduction kernels (update.cu).

@@ -40,8 +40,11 @@
 namespace hmc {
 namespace tc {
 
-constexpr int kThreads = 448;
+constexpr int kThreadsBf16 = 448;   // warps 0-13
+constexpr int kThreadsFp8 = 576;    // + warps 14-17 (FP8 converters)
 constexpr int kSoftThreads = 256;   // warps 6-13
+constexpr int kConvWarps = 4;       // warps 14-17: FP8 -> BF16 converters (idle for BF16 X)
+constexpr int kFp8BoxBytes = 128 * 64;   // one FP8 box: 128 rows x 64 bytes, row-major
 constexpr int kLA = 1;           // tiles of lookahead between the two sweeps of a tile
 constexpr int kSlots = 1;        // partial-logit receive slots (reuse gated by a cluster 'consumed' barrier)
 constexpr int kRbuf = 1;         // R operand buffers (reuse gated by a cluster 'free' barrier)
@@ -50,7 +53,9 @@ constexpr int kBox = 64;          // BF16 elements per 128-byte box row
 constexpr int kBoxBytes = kRows * 128;
 
 struct TcArgs {
-  const __nv_bfloat16* xs;  // X in swizzled 128 x 64 boxes: [row tile][p_pad / 64][16 KB]
+  const void* xs;           // X boxes, [row tile][p_pad / 64][box]: BF16 in its swizzled shared-memory
+                            // image (16 KB), or FP8 E4M3 row-major (8 KB) when fp8
+  const float* xscale;      // FP8: per-column scales s_j (X = X_q diag(s)); nullptr for BF16
   const __nv_bfloat16* bs;  // coefficient operand boxes: [p_pad / 64][N rows x 128 B]
   int64_t n;
   int32_t p_pad, PC, S, N, NP, C, Km1, chains, MB, NST, nclusters;
@@ -64,27 +69,30 @@ struct TcArgs {
   int* err;
   long long spin_limit;
   int32_t inject_timeout;
+  int32_t fp8;
 };
 
 struct Smem {
-  size_t ring, rbuf, zx, rloc, lacc, ylab, bars, total;
+  size_t ring, stage, rbuf, zx, rloc, lacc, ylab, bars, total;
 };
 
 __host__ __device__ inline size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // zx: [kSlots][S][RS][N] fp32 partial logits received for the owned rows;
 // rloc: [RS][NP] bf16 residual rows of the owned rows before they are pushed.
-__host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int NP, int N, int S, int chains) {
+__host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int NP, int N, int S, int chains, bool fp8) {
   Smem L;
   const int RS = kRows / S;
   size_t off = 0;
   L.ring = off;  off = al(off + size_t(NST) * stage_bytes, 1024);
+  // FP8: each ring slot has a 16 KB landing area for its FP8 box (sweep 1) or box pair (sweep 2).
+  L.stage = off; off = al(off + (fp8 ? size_t(NST) * 2 * kFp8BoxBytes : 0), 1024);
   L.rbuf = off;  off = al(off + kRbuf * size_t(NP / kBox) * kBoxBytes, 1024);
   L.zx = off;    off = al(off + size_t(kSlots) * kRows * N * 4, 16);
   L.rloc = off;  off = al(off + size_t(RS) * NP * 2, 16);
   L.lacc = off;  off = al(off + size_t(RS) * chains * 8, 16);
   L.ylab = off;  off = al(off + size_t(RS) * 4, 16);
-  L.bars = off;  off = al(off + size_t(2 * NST + 20) * 8 + 16, 16);
+  L.bars = off;  off = al(off + size_t(3 * NST + 20) * 8 + 16, 16);
   L.total = off + 1024;  // slack for aligning the dynamic base to 1024
   return L;
 }
@@ -115,8 +123,10 @@ __device__ __forceinline__ bool named_bar_soft_and(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+template <bool kFP8>
+__global__ void __launch_bounds__(kFP8 ? kThreadsFp8 : kThreadsBf16, 1)
     lpg_tc_kernel(const TcArgs A) {
+  constexpr int kThreads = kFP8 ? kThreadsFp8 : kThreadsBf16;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -126,8 +136,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int RS = kRows / S;                        // rows this CTA owns in the exchange
   const int chains = A.chains, C = A.C, Km1 = A.Km1;
   const int C8 = (C + 7) / 8;                      // 16-byte chunks of one R row
-  const Smem Lo = smem_layout(NST, A.stage_bytes, NP, N, S, chains);
+  constexpr bool fp8 = kFP8;
+  const Smem Lo = smem_layout(NST, A.stage_bytes, NP, N, S, chains, fp8);
   unsigned char* ring = smem + Lo.ring;
+  unsigned char* stage = smem + Lo.stage;
   unsigned char* rbuf = smem + Lo.rbuf;
   float* zx = reinterpret_cast<float*>(smem + Lo.zx);
   __nv_bfloat16* rloc = reinterpret_cast<__nv_bfloat16*>(smem + Lo.rloc);
@@ -136,7 +148,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lo.bars);
   uint64_t* full = bars;
   uint64_t* empty = bars + NST;
-  uint64_t* zdone = bars + 2 * NST;
+  uint64_t* conv = bars + 2 * NST;      // FP8: ring slot converted to BF16 (kConvWarps arrivals)
+  uint64_t* zdone = bars + 3 * NST;
   uint64_t* zfree = zdone + 1;
   uint64_t* zrdy = zdone + 2;    // partial logits of the owned rows received
   uint64_t* zxfree = zdone + 3;  // every owner has consumed the previous tile's partials
@@ -154,6 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], kConvWarps);
     }
     mbar_init(zdone, 1);
     mbar_init(zfree, 4);
@@ -230,17 +244,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           unsigned char* sp = ring + size_t(st) * A.stage_bytes;
           const int64_t t = cl + u * nclu;  // row tile
-          const unsigned char* xt = reinterpret_cast<const unsigned char*>(A.xs) + size_t(t) * nkb_all * kBoxBytes;
+          const uint32_t xbox = fp8 ? uint32_t(kFp8BoxBytes) : uint32_t(kBoxBytes);
+          const unsigned char* xt = reinterpret_cast<const unsigned char*>(A.xs) + size_t(t) * nkb_all * xbox;
+          // BF16 X lands in the slot itself; FP8 X lands in the slot's staging area
+          // and the converter warps widen it into the slot.
+          unsigned char* xdst = fp8 ? stage + size_t(st) * 2 * kFp8BoxBytes : sp;
           if (!s2) {
             const int kb = int(rank) * NKB + b;
-            mbar_arrive_expect_tx(&full[st], uint32_t(kBoxBytes + N * 128));
-            bulk_g2s(sp, xt + size_t(kb) * kBoxBytes, uint32_t(kBoxBytes), &full[st]);
+            mbar_arrive_expect_tx(&full[st], xbox + uint32_t(N * 128));
+            bulk_g2s(xdst, xt + size_t(kb) * xbox, xbox, &full[st]);
             bulk_g2s(sp + kBoxBytes, reinterpret_cast<const unsigned char*>(A.bs) + size_t(kb) * N * 128,
                      uint32_t(N * 128), &full[st]);
           } else {
             const int kb = int(rank) * NKB + 2 * b;
-            mbar_arrive_expect_tx(&full[st], uint32_t(2 * kBoxBytes));
-            bulk_g2s(sp, xt + size_t(kb) * kBoxBytes, uint32_t(2 * kBoxBytes), &full[st]);
+            mbar_arrive_expect_tx(&full[st], 2 * xbox);
+            bulk_g2s(xdst, xt + size_t(kb) * xbox, 2 * xbox, &full[st]);
           }
           issued = j + 1;
         }
@@ -281,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_after_sync();
           for (int kb = 0; kb < NKB; ++kb, ++j) {
             const int st = int(j % NST);
-            if (!wait_bounded(&full[st], uint32_t((j / NST) & 1), A.spin_limit, abort_flag, false)) {
+            if (!wait_bounded(fp8 ? &conv[st] : &full[st], uint32_t((j / NST) & 1), A.spin_limit, abort_flag, false)) {
               fail(ERR_TIMEOUT_STAGE);
               break;
             }
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_after_sync();
           for (int mb = 0; mb < A.MB; ++mb, ++j) {
             const int st = int(j % NST);
-            if (!wait_bounded(&full[st], uint32_t((j / NST) & 1), A.spin_limit, abort_flag, false)) {
+            if (!wait_bounded(fp8 ? &conv[st] : &full[st], uint32_t((j / NST) & 1), A.spin_limit, abort_flag, false)) {
               fail(ERR_TIMEOUT_STAGE);
               break;
             }
@@ -330,6 +348,52 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(gdone);
       mma_commit(drain);
       (void)wait_bounded(drain, 0u, A.spin_limit, abort_flag, false);
+    }
+  } else if (kFP8 && warp >= 14) {
+    // --------------------------------------- FP8 converters (warps 14-17)
+    // Each FP8 box (128 rows x 64 bytes) of a ring slot's staging area is
+    // widened to BF16 (exact: every E4M3 value is a BF16 value) and written in
+    // the 128-byte-swizzled layout the MMAs read; sweep-2 slots hold two boxes.
+    {
+      const int ct = tid - kThreadsBf16;   // 0..127
+      int64_t j = 0;
+      for (int64_t k = 0; k < nphase && !*abort_flag; ++k) {
+        bool s2;
+        (void)phase(k, &s2);
+        const int nb = s2 ? A.MB : NKB;
+        const int nbox = s2 ? 2 : 1;
+        bool ok = true;
+        for (int b = 0; b < nb; ++b, ++j) {
+          const int st = int(j % NST);
+          if (!wait_bounded(&full[st], uint32_t((j / NST) & 1), A.spin_limit, abort_flag, false)) {
+            fail(ERR_TIMEOUT_STAGE);
+            ok = false;
+            break;
+          }
+          const unsigned char* src = stage + size_t(st) * 2 * kFp8BoxBytes;
+          unsigned char* dst = ring + size_t(st) * A.stage_bytes;
+          for (int bx = 0; bx < nbox; ++bx) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int ci = ct + 128 * i;       // 16-byte input chunk: row ci / 4, elements 16 (ci % 4) ..
+              const int r = ci >> 2, qq = ci & 3;
+              const uint4 w = *reinterpret_cast<const uint4*>(src + size_t(bx) * kFp8BoxBytes + size_t(ci) * 16);
+              uint32_t o[8];
+              fp8x4_to_bf16x4(w.x, o[0], o[1]);
+              fp8x4_to_bf16x4(w.y, o[2], o[3]);
+              fp8x4_to_bf16x4(w.z, o[4], o[5]);
+              fp8x4_to_bf16x4(w.w, o[6], o[7]);
+              unsigned char* rowp = dst + size_t(bx) * kBoxBytes + size_t(r) * 128;
+              *reinterpret_cast<uint4*>(rowp + ((((2 * qq) ^ (r & 7))) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+              *reinterpret_cast<uint4*>(rowp + ((((2 * qq + 1) ^ (r & 7))) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_local(&conv[st]);
+        }
+        if (!ok) break;
+      }
     }
   } else if (warp < 6) {
     // ------------------------------------------------ drain group (warps 2-5)
@@ -373,12 +437,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_after_sync();
       for (int mb = 0; mb < A.MB; ++mb) {
         const int col = int(rank) * A.PC + mb * 128 + row;
+        const float sc = A.xscale ? A.xscale[col] : 1.0f;   // g = diag(s) X_q^T R
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
           tmem_ld16(tq + uint32_t(N + mb * N + c0), v);
 #pragma unroll
           for (int e = 0; e < 16; ++e)
-            if (c0 + e < C) gp[size_t(c0 + e) * A.p_pad + col] = v[e];
+            if (c0 + e < C) gp[size_t(c0 + e) * A.p_pad + col] = v[e] * sc;
         }
       }
     } else {
@@ -510,6 +575,40 @@ __global__ void x_to_tiles_kernel(const IT* X, __nv_bfloat16* out, int64_t n, in
   if (bad) atomicOr(err, ERR_NONFINITE_X);
 }
 
+// X (row-major n x p, float or double) -> FP8 E4M3 boxes of 128 rows x 64
+// columns, row-major inside a box, [n_pad / 128][p_pad / 64][8 KB]: x_q =
+// RNE-satfinite(x / s_j), the per-column scale s_j computed beforehand.
+template <typename IT>
+__global__ void x_to_tiles_fp8_kernel(const IT* X, const float* scales, unsigned char* out, int64_t n, int32_t p,
+                                      int32_t p_pad, int64_t n_pad, int* err) {
+  const int64_t total = n_pad * p_pad;
+  const int64_t nkb = p_pad / kBox;
+  int bad = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = i / p_pad, col = i - row * p_pad;
+    unsigned char q = 0;
+    if (row < n && col < p) {
+      const IT x = X[row * p + col];
+      if (!isfinite(double(x))) bad = 1;
+      q = static_cast<unsigned char>(__nv_cvt_float_to_fp8(float(x) / scales[col], __NV_SATFINITE, __NV_E4M3));
+    }
+    const int64_t t = row / kRows, kb = col / kBox;
+    out[size_t(t * nkb + kb) * kFp8BoxBytes + size_t(row % kRows) * 64 + size_t(col % kBox)] = q;
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE_X);
+}
+
+__global__ void fp8_tiles_to_rows_kernel(const unsigned char* tiles, unsigned char* out, int64_t n, int32_t p,
+                                         int32_t p_pad) {
+  const int64_t total = n * p;
+  const int64_t nkb = p_pad / kBox;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = i / p, col = i - row * p;
+    const int64_t t = row / kRows, kb = col / kBox;
+    out[i] = tiles[size_t(t * nkb + kb) * kFp8BoxBytes + size_t(row % kRows) * 64 + size_t(col % kBox)];
+  }
+}
+
 // Inverse of x_to_tiles for the stored values (BF16 bits, row-major n x p).
 __global__ void tiles_to_rows_kernel(const __nv_bfloat16* tiles, uint16_t* out, int64_t n, int32_t p, int32_t p_pad) {
   const int64_t total = n * p;
@@ -523,13 +622,15 @@ __global__ void tiles_to_rows_kernel(const __nv_bfloat16* tiles, uint16_t* out, 
 }
 
 // FP32 coefficients [C][p_pad] -> BF16 operand boxes [p_pad / 64][N rows x 128 B]
-// (rows C..N-1 zero), K-major with the 128-byte swizzle.
-__global__ void beta_to_tiles_kernel(const float* beta, __nv_bfloat16* out, int C, int N, int p_pad) {
+// (rows C..N-1 zero), K-major with the 128-byte swizzle.  With FP8 X the
+// column scales are folded in: X B = X_q (diag(s) B).
+__global__ void beta_to_tiles_kernel(const float* beta, const float* scales, __nv_bfloat16* out, int C, int N,
+                                     int p_pad) {
   const int64_t total = int64_t(N) * p_pad;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int k = int(i / p_pad);
     const int64_t col = i - int64_t(k) * p_pad;
-    const float v = (k < C) ? beta[size_t(k) * p_pad + col] : 0.f;
+    const float v = (k < C) ? beta[size_t(k) * p_pad + col] * (scales ? scales[col] : 1.0f) : 0.f;
     const int64_t kb = col / kBox;
     const size_t off = size_t(kb) * N * 128 + sw128_offset(k, int(col % kBox));
     *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(out) + off) = __float2bfloat16_rn(v);
@@ -558,22 +659,26 @@ bool tc_plan(int64_t p, int C, int S, TcPlan* out) {
   return true;
 }
 
-size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains) {
-  return tc::smem_layout(NST, pl.stage_bytes, pl.NP, pl.N, pl.S, chains).total;
+size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains, bool fp8) {
+  return tc::smem_layout(NST, pl.stage_bytes, pl.NP, pl.N, pl.S, chains, fp8).total;
 }
 
-cudaError_t tc_prepare(size_t smem, int S) {
-  cudaError_t e = cudaFuncSetAttribute(tc::lpg_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+static void (*tc_kernel(bool fp8))(const tc::TcArgs) { return fp8 ? tc::lpg_tc_kernel<true> : tc::lpg_tc_kernel<false>; }
+
+int tc_threads(bool fp8) { return fp8 ? tc::kThreadsFp8 : tc::kThreadsBf16; }
+
+cudaError_t tc_prepare(size_t smem, int S, bool fp8) {
+  cudaError_t e = cudaFuncSetAttribute(tc_kernel(fp8), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  if (S > 8) e = cudaFuncSetAttribute(tc::lpg_tc_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (S > 8) e = cudaFuncSetAttribute(tc_kernel(fp8), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
-cudaError_t tc_max_active_clusters(size_t smem, int S, int* out) {
+cudaError_t tc_max_active_clusters(size_t smem, int S, bool fp8, int* out) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = dim3(S, 1, 1);
-  cfg.blockDim = dim3(tc::kThreads, 1, 1);
+  cfg.blockDim = dim3(tc_threads(fp8), 1, 1);
   cfg.dynamicSmemBytes = smem;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = S;
@@ -581,7 +686,7 @@ cudaError_t tc_max_active_clusters(size_t smem, int S, int* out) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaOccupancyMaxActiveClusters(out, tc::lpg_tc_kernel, &cfg);
+  return cudaOccupancyMaxActiveClusters(out, tc_kernel(fp8), &cfg);
 }
 
 cudaError_t tc_x_to_tiles(int in_dtype, const void* X, void* out, int64_t n, int32_t p, int32_t p_pad, int* err,
@@ -597,23 +702,44 @@ cudaError_t tc_x_to_tiles(int in_dtype, const void* X, void* out, int64_t n, int
   return cudaGetLastError();
 }
 
-cudaError_t tc_tiles_to_rows(const void* tiles, void* out_bits, int64_t n, int32_t p, int32_t p_pad, cudaStream_t s) {
-  const int g = std::max(1, int(std::min<int64_t>(8192, (n * p + 255) / 256)));
-  tc::tiles_to_rows_kernel<<<g, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(tiles), static_cast<uint16_t*>(out_bits),
-                                            n, p, p_pad);
+cudaError_t tc_x_to_tiles_fp8(int in_dtype, const void* X, const float* scales, void* out, int64_t n, int32_t p,
+                              int32_t p_pad, int* err, cudaStream_t s) {
+  const int64_t n_pad = (n + tc::kRows - 1) / tc::kRows * tc::kRows;
+  const int g = std::max(1, int(std::min<int64_t>(8192, (n_pad * p_pad + 255) / 256)));
+  if (in_dtype == HMC_F64)
+    tc::x_to_tiles_fp8_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(X), scales,
+                                                        static_cast<unsigned char*>(out), n, p, p_pad, n_pad, err);
+  else
+    tc::x_to_tiles_fp8_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(X), scales,
+                                                       static_cast<unsigned char*>(out), n, p, p_pad, n_pad, err);
   return cudaGetLastError();
 }
 
-cudaError_t tc_beta_to_tiles(const float* beta, void* out, int C, int N, int p_pad, cudaStream_t s) {
+cudaError_t tc_tiles_to_rows(const void* tiles, void* out_bits, int64_t n, int32_t p, int32_t p_pad, bool fp8,
+                             cudaStream_t s) {
+  const int g = std::max(1, int(std::min<int64_t>(8192, (n * p + 255) / 256)));
+  if (fp8)
+    tc::fp8_tiles_to_rows_kernel<<<g, 256, 0, s>>>(static_cast<const unsigned char*>(tiles),
+                                                   static_cast<unsigned char*>(out_bits), n, p, p_pad);
+  else
+    tc::tiles_to_rows_kernel<<<g, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(tiles),
+                                              static_cast<uint16_t*>(out_bits), n, p, p_pad);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_beta_to_tiles(const float* beta, const float* scales, void* out, int C, int N, int p_pad,
+                             cudaStream_t s) {
   const int64_t total = int64_t(N) * p_pad;
   const int g = std::max(1, int(std::min<int64_t>(4096, (total + 255) / 256)));
-  tc::beta_to_tiles_kernel<<<g, 256, 0, s>>>(beta, static_cast<__nv_bfloat16*>(out), C, N, p_pad);
+  tc::beta_to_tiles_kernel<<<g, 256, 0, s>>>(beta, scales, static_cast<__nv_bfloat16*>(out), C, N, p_pad);
   return cudaGetLastError();
 }
 
 cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStream_t stream) {
   tc::TcArgs a{};
-  a.xs = static_cast<const __nv_bfloat16*>(L.xs);
+  a.xs = L.xs;
+  a.xscale = L.xscale;
+  a.fp8 = L.fp8;
   a.bs = static_cast<const __nv_bfloat16*>(L.bs);
   a.n = L.n;
   a.p_pad = L.p_pad;
@@ -641,7 +767,7 @@ cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStre
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = dim3(L.nclusters * pl.S, 1, 1);
-  cfg.blockDim = dim3(tc::kThreads, 1, 1);
+  cfg.blockDim = dim3(tc_threads(L.fp8 != 0), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -650,7 +776,7 @@ cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStre
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, tc::lpg_tc_kernel, a);
+  return cudaLaunchKernelEx(&cfg, tc_kernel(L.fp8 != 0), a);
 }
 
 }  // namespace hmc

@@ -11,8 +11,9 @@ The figure of merit is the fused-kernel time of one call for all chains (a
 tile that fits fewer chains per launch pays for more launches).
 
 Candidates: CUDA-core engine, S in {1, 2, 3, 4, 5, 6, 8, 10, 12, 16} x ring
-slots {2, 3, 4}; tensor-core engine (BF16 X), S in {16, 8, 4, 2, 1} x ring
-slots {2, 3, 4}.  Tiles the library rejects for the shape are skipped.
+slots {2, 3, 4}; tensor-core engine (BF16 or FP8 X), S in {16, 8, 4, 2, 1} x
+ring slots {2, 3, 4}.  With engine 0 both engines are candidates where the
+storage type allows.  Tiles the library rejects for the shape are skipped.
 """
 import json
 import os
@@ -89,37 +90,40 @@ def time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, engine, til
 
 def autotune(X, y, K, prior="gaussian", prior_scale=1.0, x_storage="f32", state="f32", chains=1, engine=0,
              stream=None, reps=5, use_cache=True, verbose=False):
-    """Fastest tile for this problem: returns (tile tuple for hmc.create, table of measurements)."""
+    """Fastest (engine, tile) for this problem: returns (engine, tile tuple for hmc.create, table of
+    measurements); (engine, None, table) when no explicit tile runs."""
     import torch
     n, p = int(X.shape[0]), int(X.shape[1])
-    eng = engine
-    if eng == 0:
-        eng = 2 if x_storage == "bf16" else 1
-    key = _key(torch.cuda.get_device_name(), n, p, K, x_storage, state, chains, eng)
+    if engine:
+        engines = (engine,)
+    else:
+        engines = (2, 1) if x_storage in ("bf16", "fp8") else (1,)
+    key = _key(torch.cuda.get_device_name(), n, p, K, x_storage, state, chains, engine)
     cache = _load() if use_cache else {}
     if key in cache:
         e = cache[key]
-        return tuple(e["tile"]), e.get("table", [])
+        return int(e["engine"]), tuple(e["tile"]), e.get("table", [])
     table = []
-    S_list = TC_S if eng == 2 else SIMT_S
-    for S in S_list:
-        for ns in RING:
-            us, d = time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, eng, (S, 0, 0, ns),
-                              stream=stream, reps=reps)
-            if us is None:
-                continue
-            pr = d["problems"][0]
-            row = dict(S=S, ring=ns, us=round(us, 2), clusters=pr.get("nclusters"), smem=pr.get("smem"))
-            table.append(row)
-            if verbose:
-                print("tune", json.dumps(row), flush=True)
+    for eng in engines:
+        for S in (TC_S if eng == 2 else SIMT_S):
+            for ns in RING:
+                us, d = time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, eng, (S, 0, 0, ns),
+                                  stream=stream, reps=reps)
+                if us is None:
+                    continue
+                pr = d["problems"][0]
+                row = dict(engine=eng, S=S, ring=ns, us=round(us, 2), clusters=pr.get("nclusters"),
+                           group_chains=pr.get("group_chains"), smem=pr.get("smem"))
+                table.append(row)
+                if verbose:
+                    print("tune", json.dumps(row), flush=True)
     if not table:
-        # The engine cannot run this shape with an explicit tile: leave the choice to the library.
-        return None, table
+        # No explicit tile runs for this shape: leave the choice to the library.
+        return engine, None, table
     best = min(table, key=lambda r: r["us"])
     tile = (best["S"], 0, 0, best["ring"])
     if use_cache:
         cache = _load()
-        cache[key] = dict(tile=list(tile), table=table)
+        cache[key] = dict(engine=best["engine"], tile=list(tile), table=table)
         _store(cache)
-    return tile, table
+    return best["engine"], tile, table

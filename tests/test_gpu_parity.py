@@ -96,7 +96,7 @@ def test_fp8_storage_bits_and_error(cuda):
     X[:, 7] = 0.0
     rng = np.random.default_rng(3)
     beta = (0.05 * rng.standard_normal((1, 4, 513))).astype(np.float32)
-    with hmc.create(X, y, 5, "gaussian", 10.0, x_storage="fp8") as h:
+    with hmc.create(X, y, 5, "gaussian", 10.0, x_storage="fp8", engine=1) as h:   # CUDA cores, FP32 arithmetic
         codes, scales = h.get_x()
         c_o, s_o = quant.fp8_quantize(X)
         assert np.array_equal(scales, s_o)

@@ -1,8 +1,9 @@
-"""Tensor-core engine (tcgen05, BF16 X) against the FP64 oracle on the same
-stored BF16 values.  The MMA operands are BF16 (coefficients and the residual
-are rounded to BF16 before the contractions; accumulation is FP32 in TMEM),
-so the tolerance is the BF16 bar: gradient relative error <= 1e-2 and
-log K relative error <= 1e-3."""
+"""Tensor-core engine (tcgen05, BF16 or per-column-scaled FP8 X) against the
+FP64 oracle on the same stored values (FP8: the dequantised codes x_q s_j).
+The MMA operands are BF16 (coefficients, with FP8 column scales folded in,
+and the residual are rounded to BF16 before the contractions; accumulation is
+FP32 in TMEM), so the tolerance is the BF16 bar: gradient relative error
+<= 1e-2 and log K relative error <= 1e-3."""
 import numpy as np
 import pytest
 
@@ -18,16 +19,22 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _run(cuda, n, p, K, chains, seed, bscale=0.05, tile=None, prior=("gaussian", 10.0)):
+def _run(cuda, n, p, K, chains, seed, bscale=0.05, tile=None, prior=("gaussian", 10.0), storage="bf16"):
     import torch
     X, y, _ = synthetic.make_problem(n, p, K, seed=seed)
     rng = np.random.default_rng(seed + 1)
     beta = (bscale * rng.standard_normal((chains, K - 1, p))).astype(np.float32)
-    with hmc.create(X, y, K, prior[0], prior[1], x_storage="bf16", max_chains=chains, engine=2, tile=tile) as h:
+    with hmc.create(X, y, K, prior[0], prior[1], x_storage=storage, max_chains=chains, engine=2, tile=tile) as h:
         d = h.describe()
         assert d["engine"] == "tcgen05"
-        bits, _ = h.get_x()
-        Xq = quant.bf16_decode(bits).astype(np.float64)
+        bits, scales = h.get_x()
+        if storage == "fp8":
+            # stored codes and scales are exactly the oracle's quantisation of X
+            c_o, s_o = quant.fp8_quantize(X)
+            assert np.array_equal(scales, s_o) and np.array_equal(bits, c_o)
+            Xq = quant.fp8_dequantize(bits, scales).astype(np.float64)
+        else:
+            Xq = quant.bf16_decode(bits).astype(np.float64)
         lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
         torch.cuda.synchronize()
         lp, g = lp.cpu().numpy(), g.cpu().numpy()
@@ -52,6 +59,24 @@ def test_tc_deterministic(cuda):
     X, y, _ = synthetic.make_problem(3000, 1500, 8, seed=3)
     beta = torch.from_numpy((0.05 * np.random.default_rng(4).standard_normal((3, 7, 1500))).astype(np.float32)).to(cuda)
     with hmc.create(X, y, 8, "gaussian", 10.0, x_storage="bf16", max_chains=3, engine=2) as h:
+        a = [t.cpu().numpy() for t in h.logpost_grad(beta)]
+        b = [t.cpu().numpy() for t in h.logpost_grad(beta)]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("n,p,K,chains,S", [(1000, 700, 6, 2, 0), (333, 129, 3, 1, 1), (2049, 1000, 20, 4, 0),
+                                            (5000, 2000, 10, 7, 4)])
+def test_tc_fp8_matches_oracle(cuda, n, p, K, chains, S):
+    d, errs = _run(cuda, n, p, K, chains, seed=n + 3 * p, tile=(S, 0, 0, 0), storage="fp8")
+    for c, (el, eg) in enumerate(errs):
+        assert el <= TOL_L and eg <= TOL_G, (d["problems"][0], c, el, eg)
+
+
+def test_tc_fp8_deterministic(cuda):
+    import torch
+    X, y, _ = synthetic.make_problem(3000, 1500, 8, seed=13)
+    beta = torch.from_numpy((0.05 * np.random.default_rng(14).standard_normal((3, 7, 1500))).astype(np.float32)).to(cuda)
+    with hmc.create(X, y, 8, "gaussian", 10.0, x_storage="fp8", max_chains=3, engine=2) as h:
         a = [t.cpu().numpy() for t in h.logpost_grad(beta)]
         b = [t.cpu().numpy() for t in h.logpost_grad(beta)]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
