@@ -284,7 +284,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     P.group_chains = std::max(1, std::min(h->max_chains, maxct / P.Km1));
     P.ct_launch = P.group_chains * P.Km1;
     if (h->tile[1] || h->tile[2])
-      return fail(HMC_EINVAL, "tile[1] and tile[2] must be 0 on the CUDA-core engine (8-row super-tiles)");
+      return fail(HMC_EINVAL, "tile[1] and tile[2] must be 0 on the CUDA-core engine (fixed super-tile height)");
     P.ntiles = (P.n + kSimtRows - 1) / kSimtRows;
     SimtTile tc{};
     HMC_CUDA(simt_choose(h->xt, P.ct_launch, P.p, P.ntiles, h->tile[0], h->tile[3], 0, &tc));

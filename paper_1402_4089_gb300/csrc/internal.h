@@ -43,7 +43,7 @@ struct LpgArgs {
 
 // CUDA-core fused kernel (any X storage type, small C).
 constexpr int kSimtMaxThreads = 512;   // up to 10 gradient + 5 logit + 1 producer warps
-constexpr int kSimtRows = 8;           // rows per super-tile of the CUDA-core kernel (host and device)
+constexpr int kSimtRows = 16;          // rows per super-tile of the CUDA-core kernel (host and device)
 int simt_max_ct(int xt);                                     // largest C one launch handles
 // Shared memory of one CTA: PC columns, cluster size S, NWL logit warps, NSTAGE ring slots.
 size_t simt_smem_bytes(int xt, int st, int C, int PC, int S, int NWL, int NSTAGE);

@@ -6,7 +6,7 @@
 // reading every element of X from HBM once.
 //
 // Work decomposition (GB300): a thread-block cluster of S CTAs walks
-// super-tiles of BM = 8 rows; CTA `rank` owns the column slice
+// super-tiles of BM = kSimtRows rows; CTA `rank` owns the column slice
 // [rank*PC, (rank+1)*PC) of X and of the coefficients.  Inside a CTA three
 // warp roles run their own loops over the cluster's tiles, handing tiles
 // over through mbarriers:
@@ -43,7 +43,7 @@ namespace simt {
 
 constexpr int kMaxThreads = kSimtMaxThreads;   // 2 x 7 consumer warps + producer
 constexpr int kBM = kSimtRows;   // rows per super-tile
-constexpr int kNZ = 4;   // exchange slots: tiles the logit group may run ahead of the gradient group
+constexpr int kNZ = 2;   // exchange slots: tiles the logit group may run ahead of the gradient group
 
 __device__ __forceinline__ float bf16lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
@@ -278,7 +278,7 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
                 V = Sh::V, VP = Sh::VP;
   constexpr int BM = kBM;
   constexpr int QW = int(sizeof(XT));     // 32-bit words of one quad of X
-  constexpr int XB = BM < 8 ? BM : 8;     // rows of X a gradient thread holds in registers
+  constexpr int XB = BM < (QW > 4 ? 4 : 8) ? BM : (QW > 4 ? 4 : 8);   // rows of X a gradient thread holds in registers
   constexpr int MAXW = logit_warps(max_grad_warps(int(sizeof(AT)), CT));
   extern __shared__ __align__(128) unsigned char smem[];
 

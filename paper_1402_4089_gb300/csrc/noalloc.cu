@@ -155,8 +155,8 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
     a.C = C;
     a.Km1 = Km1;
     a.chains = chains;
-    a.BM = 8;
-    a.CR = 8;
+    a.BM = kSimtRows;
+    a.CR = kSimtRows;
     a.S = S;
     a.NT = NT;
     a.NWL = tile.NWL;

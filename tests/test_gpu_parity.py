@@ -67,7 +67,7 @@ def test_fp32_tiles_ragged(cuda, S, NS):
     beta = (0.2 * rng.standard_normal((2, 3, 300))).astype(np.float32)
     with hmc.create(X, y, 4, "gaussian", 1.0, max_chains=2, tile=(S, 0, 0, NS)) as h:
         d = h.describe()["problems"][0]
-        assert (d["S"], d["BM"], d["NSTAGE"]) == (S, 8, NS)
+        assert (d["S"], d["BM"], d["NSTAGE"]) == (S, 16, NS)          # 1013 rows: 63 tiles of 16 + 5
         check(h, X, y, beta, "gaussian", 1.0, cuda, 1e-5, 1e-5)
 
 
