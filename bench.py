@@ -399,7 +399,7 @@ def run_batch_uneven(args):
     probs = [synthetic.make_problem(n, p, K, seed=0, sub=100 + i) for i, (n, p, K) in enumerate(shapes)]
     stream = torch.cuda.Stream(device=dev)
     h = hmc.create_batch([pr[0] for pr in probs], [pr[1] for pr in probs], [K for (_, _, K) in shapes], kind, scale,
-                         x_storage=xdt, max_chains=chains, stream=stream, engine=1)
+                         x_storage=xdt, max_chains=chains, stream=stream)
     desc = h.describe()
     seed = 20140217
     h.sample(chains, L, eps, args.warmup, seed)
@@ -443,12 +443,13 @@ def run_batch_uneven(args):
                    "l2": "inputs larger than L2: X of all problems re-streamed every gradient"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "lpg_kernel_batched (CUDA cores), all problems per launch",
+                     "kernel": ("lpg_tc_kernel_batched (tcgen05)" if desc.get("engine") == "tcgen05" else
+                                "lpg_kernel_batched (CUDA cores)") + ", all problems per launch",
                      "avg_launch_us": round(per_launch * 1e6, 2), "launches_timed": fused_n,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "cpu_baseline": None, "e2e": None, "gpu_launches": None,
         "accept_rate": round(sum(s["accepted"] for s in stats) / max(1, sum(s["iterations"] for s in stats)), 4),
-        "impl": "ours", "clocks": clk.summary(), "batched_launch": desc.get("batched_launch"),
+        "impl": "ours", "clocks": clk.summary(), "batched_launch": desc.get("batched_launch"), "engine": desc.get("engine"),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

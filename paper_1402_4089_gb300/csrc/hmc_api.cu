@@ -127,6 +127,11 @@ struct hmc_ctx {
   size_t b_smem = 0;
   LpgArgs* b_table = nullptr;   // device [2][nprob]: chain state, user scratch
   int* b_first = nullptr;       // device [nprob + 1] first cluster of each problem
+  // The same for the tensor-core engine (BF16 / FP8 storage).
+  bool tc_batched = false;
+  void* tb_table = nullptr;     // device TcArgs [nprob]
+  void* tb_beta = nullptr;      // device coefficient-box jobs [2][nprob]: chain state, user scratch
+  int64_t tb_max_elems = 0;     // largest N x p_pad of the operand boxes
   // Cached graph of one HMC iteration and the parameters baked into it.
   cudaGraphExec_t gexec = nullptr;
   int g_chains = 0, g_L = 0, g_thin = 0;
@@ -576,13 +581,103 @@ hmc_status setup_batched(hmc_ctx* h) {
   return HMC_OK;
 }
 
+// Tensor-core engine: one launch for every problem when they share the
+// cluster size and each runs all chains in one group.  Clusters are split by
+// work (n p); the dynamic shared memory is the largest any problem needs.
+hmc_status setup_batched_tc(hmc_ctx* h) {
+  const int m = int(h->probs.size());
+  if (m < 2) return HMC_OK;
+  const int S = h->probs[0].S;
+  for (Problem& P : h->probs)
+    if (P.engine != 2 || P.n == 0 || P.group_chains < h->max_chains || P.S != S) return HMC_OK;
+  int dev = 0, smem_max = 0;
+  HMC_CUDA(cudaGetDevice(&dev));
+  HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const bool fp8 = h->xt == HMC_FP8E4M3;
+  // The batched kernel keeps the problem's arguments in static shared memory:
+  // leave room for them by taking ring slots off problems that need it.
+  const size_t limit = size_t(smem_max) - 512;
+  size_t smem = 0;
+  for (Problem& P : h->probs) {
+    while (P.smem > limit && P.NSTAGE > 2) {
+      P.NSTAGE -= 1;
+      P.smem = std::max(tc_smem_bytes(P.tp, P.NSTAGE, h->max_chains, fp8), size_t(116 * 1024));
+    }
+    if (P.smem > limit) return HMC_OK;
+    smem = std::max(smem, P.smem);
+  }
+  HMC_CUDA(tc_prepare_batched(smem, S, fp8));
+  int cap = 0;
+  if (tc_max_active_clusters_batched(smem, S, fp8, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return HMC_OK;
+  }
+  if (cap < 1) return HMC_OK;
+  double total = 0.0;
+  for (Problem& P : h->probs) total += double(P.n) * P.p_pad;
+  std::vector<int> first(m + 1, 0);
+  std::vector<TcPlan> plans(m);
+  std::vector<TcLaunch> launches(m);
+  std::vector<TcBetaBox> boxes(2 * m);
+  int64_t max_elems = 1;
+  for (int b = 0; b < m; ++b) {
+    Problem& P = h->probs[b];
+    int nc = int(std::lround(double(P.n) * P.p_pad / total * cap));
+    nc = std::max(1, std::min(nc, P.nclusters));   // partial buffers hold P.nclusters
+    P.nclusters = nc;
+    P.nlparts = nc * S;
+    first[b + 1] = first[b] + nc;
+    plans[b] = P.tp;
+    TcLaunch& L = launches[b];
+    L = TcLaunch{};
+    L.xs = P.X;
+    L.xscale = P.xscale;
+    L.fp8 = fp8 ? 1 : 0;
+    L.bs = P.bbf;
+    L.n = P.n;
+    L.p_pad = P.p_pad;
+    L.C = h->max_chains * P.Km1;
+    L.Km1 = P.Km1;
+    L.chains = h->max_chains;
+    L.NST = P.NSTAGE;
+    L.nclusters = nc;
+    L.gpart = P.gpart;
+    L.gpart_cstride = P.state_elems;
+    L.lpart = P.lpart;
+    L.lpart_cstride = h->max_chains;
+    L.y = P.y;
+    L.err = h->err_d;
+    L.spin_limit = h->spin_limit;
+    L.inject_timeout = 0;
+    for (int w = 0; w < 2; ++w)
+      boxes[w * m + b] = TcBetaBox{static_cast<const float*>(w == 0 ? P.cs.beta : P.us.beta), P.xscale, P.bbf, P.Km1,
+                                   P.tp.N, P.p_pad};
+    max_elems = std::max<int64_t>(max_elems, int64_t(P.tp.N) * P.p_pad);
+  }
+  HMC_CUDA(tc_upload_batch(plans.data(), launches.data(), m, &h->tb_table));
+  HMC_CUDA(tc_upload_beta_table(boxes.data(), 2 * m, &h->tb_beta));
+  HMC_CUDA(cudaMalloc(&h->b_first, first.size() * sizeof(int)));
+  HMC_CUDA(cudaMemcpy(h->b_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice));
+  h->b_S = S;
+  h->b_smem = smem;
+  h->b_total_clusters = first[m];
+  h->tb_max_elems = max_elems;
+  h->tc_batched = true;
+  return HMC_OK;
+}
+
 // The fused pass for every problem: one launch for a batched handle, else one
 // launch per problem (and per chain group).
 hmc_status run_lpg_all(hmc_ctx* h, bool chain_state, int chains, cudaStream_t stream) {
-  if (!h->batched) {
+  if (!h->batched && !h->tc_batched) {
     for (Problem& P : h->probs) HMC_TRY(run_lpg(h, P, chain_state ? P.cs : P.us, chains, stream));
     return HMC_OK;
   }
+  const int mtc = int(h->probs.size());
+  if (h->tc_batched)   // operand boxes of every problem's coefficients (one launch, not timed)
+    HMC_CUDA(tc_beta_to_tiles_batched(static_cast<const char*>(h->tb_beta) + (chain_state ? 0 : 1) * mtc *
+                                          size_t(tc_beta_job_bytes()),
+                                      mtc, chains, h->tb_max_elems, stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (h->timing) {
@@ -592,8 +687,12 @@ hmc_status run_lpg_all(hmc_ctx* h, bool chain_state, int chains, cudaStream_t st
                                                   : cudaEventRecord(e0, stream));
   }
   const int m = int(h->probs.size());
-  const cudaError_t le = simt_launch_batched(h->xt, h->b_CT, h->b_table + (chain_state ? 0 : m), h->b_first, m, chains,
-                                             h->b_total_clusters, h->b_S, h->b_NT, h->b_smem, stream);
+  const cudaError_t le =
+      h->tc_batched
+          ? tc_launch_batched(h->tb_table, h->b_first, m, chains, h->b_total_clusters, h->b_S,
+                              h->xt == HMC_FP8E4M3, h->b_smem, stream)
+          : simt_launch_batched(h->xt, h->b_CT, h->b_table + (chain_state ? 0 : m), h->b_first, m, chains,
+                                h->b_total_clusters, h->b_S, h->b_NT, h->b_smem, stream);
   if (le != cudaSuccess) return fail(HMC_ECUDA, std::string("batched fused launch failed: ") + cudaGetErrorString(le));
   if (h->timing)
     HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
@@ -662,7 +761,7 @@ hmc_status validate_opts(const hmc_opts* o) {
 
 void build_description(hmc_ctx* h) {
   std::string s = "{\"engine\": \"" + std::string(h->probs.empty() || h->probs[0].engine == 1 ? "simt" : "tcgen05") +
-                  "\", \"batched_launch\": " + std::string(h->batched ? "true" : "false") +
+                  "\", \"batched_launch\": " + std::string(h->batched || h->tc_batched ? "true" : "false") +
                   ", \"x_storage\": " + std::to_string(h->xt) +
                   ", \"state\": " + std::to_string(h->st) + ", \"max_chains\": " + std::to_string(h->max_chains) +
                   ", \"problems\": [";
@@ -737,6 +836,30 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
   // problem needs) so that one fused launch can serve every problem.
   const bool want_batch =
       nprob > 1 && !((h->xt == HMC_BF16 || h->xt == HMC_FP8E4M3) && h->engine != 1) && !h->tile[0];
+  // A batch on the tensor-core engine shares the smallest cluster size whose
+  // tile plan fits every problem with all chains in one launch.
+  bool want_tc_batch = nprob > 1 && (h->xt == HMC_BF16 || h->xt == HMC_FP8E4M3) && h->engine != 1 && !h->tile[0];
+  if (want_tc_batch) {
+    int S_tc = 0;
+    for (int S : {1, 2, 4, 8, 16}) {
+      bool ok = true;
+      for (Problem& P : h->probs) {
+        TcPlan pl;
+        if (P.n == 0 || !tc_plan(P.p, h->max_chains * P.Km1, S, &pl)) {
+          ok = false;
+          break;
+        }
+      }
+      if (ok) {
+        S_tc = S;
+        break;
+      }
+    }
+    if (S_tc)
+      h->tile[0] = S_tc;
+    else
+      want_tc_batch = false;
+  }
   if (want_batch) {
     // Smallest cluster whose column slices fit the block for every problem.
     int S = 1;
@@ -757,6 +880,11 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
   if (want_batch) {
     h->tile[0] = 0;
     hmc_status s = setup_batched(h);
+    if (s != HMC_OK) return cleanup(s);
+  }
+  if (want_tc_batch) {
+    h->tile[0] = 0;
+    hmc_status s = setup_batched_tc(h);
     if (s != HMC_OK) return cleanup(s);
   }
   build_description(h);
@@ -869,6 +997,8 @@ hmc_status hmc_destroy(hmc_handle h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->b_table) cudaFree(h->b_table);
   if (h->b_first) cudaFree(h->b_first);
+  if (h->tb_table) cudaFree(h->tb_table);
+  if (h->tb_beta) cudaFree(h->tb_beta);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return HMC_OK;

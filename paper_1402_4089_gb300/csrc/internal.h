@@ -108,6 +108,21 @@ cudaError_t tc_tiles_to_rows(const void* tiles, void* out_bits, int64_t n, int32
 cudaError_t tc_beta_to_tiles(const float* beta, const float* scales, void* out, int C, int N, int p_pad,
                              cudaStream_t s);
 cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStream_t stream);
+// One launch for several problems (shared cluster size and storage type).
+struct TcBetaBox {
+  const float* beta;        // [chains][Km1][p_pad] state
+  const float* scales;      // FP8 column scales or nullptr
+  void* out;                // operand boxes of the problem
+  int32_t Km1, N, p_pad;
+};
+cudaError_t tc_prepare_batched(size_t smem, int S, bool fp8);
+cudaError_t tc_max_active_clusters_batched(size_t smem, int S, bool fp8, int* out);
+cudaError_t tc_upload_batch(const TcPlan* plans, const TcLaunch* launches, int m, void** d_table);
+cudaError_t tc_upload_beta_table(const TcBetaBox* boxes, int m, void** d_table);
+int tc_beta_job_bytes();                    // bytes of one coefficient-box job in the device table
+cudaError_t tc_beta_to_tiles_batched(const void* d_table, int m, int chains, int64_t max_elems, cudaStream_t s);
+cudaError_t tc_launch_batched(const void* d_table, const int* d_first, int m, int chains, int total_clusters, int S,
+                              bool fp8, size_t smem, cudaStream_t stream);
 
 // Element-wise / reduction kernels (update.cu).
 struct UpdateArgs {

@@ -32,6 +32,7 @@
 // drain group (TMEM lanes 0-127; the gradient slice at the end), warps 6-13
 // softmax group.  All waits are bounded.
 #include <algorithm>
+#include <vector>
 #include <cstring>
 
 #include "internal.h"
@@ -123,16 +124,16 @@ __device__ __forceinline__ bool named_bar_soft_and(bool v) {
   return r != 0;
 }
 
+// One cluster's share of the fused pass for problem A; cl = the cluster's
+// index among the clusters working on this problem.
 template <bool kFP8>
-__global__ void __launch_bounds__(kFP8 ? kThreadsFp8 : kThreadsBf16, 1)
-    lpg_tc_kernel(const TcArgs A) {
+__device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
   constexpr int kThreads = kFP8 ? kThreadsFp8 : kThreadsBf16;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int S = A.S, N = A.N, NST = A.NST, NP = A.NP;
   const uint32_t rank = (S > 1) ? cluster_rank() : 0u;
-  const int cl = blockIdx.x / S;
   const int RS = kRows / S;                        // rows this CTA owns in the exchange
   const int chains = A.chains, C = A.C, Km1 = A.Km1;
   const int C8 = (C + 7) / 8;                      // 16-byte chunks of one R row
@@ -545,6 +546,45 @@ __global__ void __launch_bounds__(kFP8 ? kThreadsFp8 : kThreadsBf16, 1)
   if (S > 1) cluster_sync_all();
 }
 
+template <bool kFP8>
+__global__ void __launch_bounds__(kFP8 ? kThreadsFp8 : kThreadsBf16, 1) lpg_tc_kernel(const TcArgs A) {
+  tc_body<kFP8>(A, int(blockIdx.x) / A.S);
+}
+
+// Several independent problems in one launch: clusters [first[b], first[b+1])
+// of the grid work on problem b with its own arguments (X, labels, operand
+// boxes, tile plan, partial slots); every problem shares the cluster size and
+// the storage type.  `chains` is the call's chain count.
+template <bool kFP8>
+__global__ void __launch_bounds__(kFP8 ? kThreadsFp8 : kThreadsBf16, 1)
+    lpg_tc_kernel_batched(const TcArgs* __restrict__ table, const int* __restrict__ first, int nprob, int chains) {
+  __shared__ TcArgs args;
+  __shared__ int cl_local;
+  if (threadIdx.x == 0) {
+    const int gcl = int(blockIdx.x) / table[0].S;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {  // last b with first[b] <= gcl
+      const int mid = (lo + hi + 1) / 2;
+      if (first[mid] <= gcl) lo = mid; else hi = mid - 1;
+    }
+    args = table[lo];
+    args.chains = chains;
+    args.C = chains * args.Km1;
+    cl_local = gcl - first[lo];
+  }
+  __syncthreads();
+  tc_body<kFP8>(args, cl_local);
+}
+
+// Coefficients of every problem of a batch into their operand boxes: block
+// row b (blockIdx.y) converts problem b.
+struct BetaTiles {
+  const float* beta;
+  const float* scales;
+  __nv_bfloat16* out;
+  int32_t Km1, N, p_pad;
+};
+
 // Byte offset of element (row r, column c) of a 128-byte-swizzled box whose
 // rows hold 64 BF16 values: 16-byte chunk (c / 8) is stored at chunk
 // (c / 8) ^ (r % 8).
@@ -637,6 +677,20 @@ __global__ void beta_to_tiles_kernel(const float* beta, const float* scales, __n
   }
 }
 
+__global__ void beta_to_tiles_batched_kernel(const BetaTiles* __restrict__ table, int chains) {
+  const BetaTiles b = table[blockIdx.y];
+  const int C = chains * b.Km1;
+  const int64_t total = int64_t(b.N) * b.p_pad;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int k = int(i / b.p_pad);
+    const int64_t col = i - int64_t(k) * b.p_pad;
+    const float v = (k < C) ? b.beta[size_t(k) * b.p_pad + col] * (b.scales ? b.scales[col] : 1.0f) : 0.f;
+    const int64_t kb = col / kBox;
+    const size_t off = size_t(kb) * b.N * 128 + sw128_offset(k, int(col % kBox));
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(b.out) + off) = __float2bfloat16_rn(v);
+  }
+}
+
 }  // namespace tc
 
 // Plan: N = C rounded to 16, MB = PC / 128, TMEM = N * (1 + MB) <= 512.
@@ -664,6 +718,10 @@ size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains, bool fp8) {
 }
 
 static void (*tc_kernel(bool fp8))(const tc::TcArgs) { return fp8 ? tc::lpg_tc_kernel<true> : tc::lpg_tc_kernel<false>; }
+using TcBatchedFn = void (*)(const tc::TcArgs*, const int*, int, int);
+static TcBatchedFn tc_kernel_batched(bool fp8) {
+  return fp8 ? tc::lpg_tc_kernel_batched<true> : tc::lpg_tc_kernel_batched<false>;
+}
 
 int tc_threads(bool fp8) { return fp8 ? tc::kThreadsFp8 : tc::kThreadsBf16; }
 
@@ -735,7 +793,7 @@ cudaError_t tc_beta_to_tiles(const float* beta, const float* scales, void* out, 
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStream_t stream) {
+static tc::TcArgs make_args(const TcPlan& pl, const TcLaunch& L) {
   tc::TcArgs a{};
   a.xs = L.xs;
   a.xscale = L.xscale;
@@ -764,19 +822,79 @@ cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStre
   a.err = L.err;
   a.spin_limit = L.spin_limit;
   a.inject_timeout = L.inject_timeout;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.gridDim = dim3(L.nclusters * pl.S, 1, 1);
-  cfg.blockDim = dim3(tc_threads(L.fp8 != 0), 1, 1);
+  return a;
+}
+
+static void tc_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int clusters, int S, bool fp8, size_t smem,
+                      cudaStream_t stream) {
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3(clusters * S, 1, 1);
+  cfg.blockDim = dim3(tc_threads(fp8), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = pl.S;
+  attr[0].val.clusterDim.x = S;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+}
+
+cudaError_t tc_launch(const TcPlan& pl, const TcLaunch& L, size_t smem, cudaStream_t stream) {
+  const tc::TcArgs a = make_args(pl, L);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  tc_config(cfg, attr, L.nclusters, pl.S, L.fp8 != 0, smem, stream);
   return cudaLaunchKernelEx(&cfg, tc_kernel(L.fp8 != 0), a);
+}
+
+// ---- one launch for several problems
+cudaError_t tc_prepare_batched(size_t smem, int S, bool fp8) {
+  cudaError_t e = cudaFuncSetAttribute(tc_kernel_batched(fp8), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  if (S > 8) e = cudaFuncSetAttribute(tc_kernel_batched(fp8), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t tc_max_active_clusters_batched(size_t smem, int S, bool fp8, int* out) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  tc_config(cfg, attr, 1, S, fp8, smem, nullptr);
+  return cudaOccupancyMaxActiveClusters(out, tc_kernel_batched(fp8), &cfg);
+}
+
+cudaError_t tc_upload_batch(const TcPlan* plans, const TcLaunch* launches, int m, void** d_table) {
+  std::vector<tc::TcArgs> t(m);
+  for (int b = 0; b < m; ++b) t[b] = make_args(plans[b], launches[b]);
+  cudaError_t e = cudaMalloc(d_table, size_t(m) * sizeof(tc::TcArgs));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*d_table, t.data(), size_t(m) * sizeof(tc::TcArgs), cudaMemcpyHostToDevice);
+}
+
+cudaError_t tc_upload_beta_table(const TcBetaBox* boxes, int m, void** d_table) {
+  std::vector<tc::BetaTiles> t(m);
+  for (int b = 0; b < m; ++b)
+    t[b] = tc::BetaTiles{boxes[b].beta, boxes[b].scales, static_cast<__nv_bfloat16*>(boxes[b].out), boxes[b].Km1,
+                         boxes[b].N, boxes[b].p_pad};
+  cudaError_t e = cudaMalloc(d_table, size_t(m) * sizeof(tc::BetaTiles));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*d_table, t.data(), size_t(m) * sizeof(tc::BetaTiles), cudaMemcpyHostToDevice);
+}
+
+int tc_beta_job_bytes() { return int(sizeof(tc::BetaTiles)); }
+
+cudaError_t tc_beta_to_tiles_batched(const void* d_table, int m, int chains, int64_t max_elems, cudaStream_t s) {
+  const int gx = std::max(1, int(std::min<int64_t>(512, (max_elems + 255) / 256)));
+  tc::beta_to_tiles_batched_kernel<<<dim3(gx, m), 256, 0, s>>>(static_cast<const tc::BetaTiles*>(d_table), chains);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_batched(const void* d_table, const int* d_first, int m, int chains, int total_clusters, int S,
+                              bool fp8, size_t smem, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  tc_config(cfg, attr, total_clusters, S, fp8, smem, stream);
+  return cudaLaunchKernelEx(&cfg, tc_kernel_batched(fp8), static_cast<const tc::TcArgs*>(d_table), d_first, m, chains);
 }
 
 }  // namespace hmc

@@ -80,3 +80,37 @@ def test_tc_fp8_deterministic(cuda):
         a = [t.cpu().numpy() for t in h.logpost_grad(beta)]
         b = [t.cpu().numpy() for t in h.logpost_grad(beta)]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_tc_batch_of_uneven_problems_one_launch(cuda, storage):
+    """Independent problems of different n, p, K in one tensor-core launch."""
+    import torch
+    shapes = [(900, 130, 3), (2049, 700, 12), (300, 64, 2), (5000, 1500, 20)]
+    probs = [synthetic.make_problem(n, p, K, seed=31, sub=i) for i, (n, p, K) in enumerate(shapes)]
+    chains = 2
+    rng = np.random.default_rng(32)
+    betas = [(0.05 * rng.standard_normal((chains, K - 1, p))).astype(np.float32) for (n, p, K) in shapes]
+    flat = torch.from_numpy(np.concatenate([b.ravel() for b in betas])).to(cuda)
+    with hmc.create_batch([pr[0] for pr in probs], [pr[1] for pr in probs], [s[2] for s in shapes],
+                          "gaussian", 10.0, x_storage=storage, max_chains=chains) as h:
+        d = h.describe()
+        assert d["engine"] == "tcgen05" and d["batched_launch"] is True, d
+        xs = [h.get_x(b) for b in range(len(shapes))]
+        h.set_timing(True)
+        lp, g = h.logpost_grad(flat, chains=chains)
+        torch.cuda.synchronize()
+        _, launches = h.fused_kernel_time()
+        assert launches == 1
+        lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    off = 0
+    for b, ((X, y, _), (n, p, K)) in enumerate(zip(probs, shapes)):
+        bits, scales = xs[b]
+        Xq = (quant.fp8_dequantize(bits, scales) if storage == "fp8" else quant.bf16_decode(bits)).astype(np.float64)
+        gb = g[off:off + chains * (K - 1) * p].reshape(chains, K - 1, p)
+        off += chains * (K - 1) * p
+        for c in range(chains):
+            lk_o = model.log_kernel(Xq, y, betas[b][c], "gaussian", 10.0)
+            g_o = model.grad_log_kernel(Xq, y, betas[b][c], "gaussian", 10.0)
+            assert abs(lp[b * chains + c] - lk_o) / max(1.0, abs(lk_o)) <= TOL_L, (b, c)
+            assert _rel(gb[c], g_o) <= TOL_G, (b, c, _rel(gb[c], g_o))
