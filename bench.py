@@ -149,6 +149,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value, dist, device):
+    """The largest `value` over all ranks (every rank gets it); `value` itself
+    when not distributed."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------ measurements
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -204,6 +215,36 @@ def cpu_baseline(X64, y, spec, seconds):
     return {"value": steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} FP64 leapfrog steps (one gradient each) of the full workload in {el:.1f} s, "
                       f"numpy/BLAS on the host"}
+
+
+def oracle_accuracy(h, X64, y, spec, xdt, tdt, dev):
+    """Error of the GPU log K and gradient at chain 0's current state against the
+    FP64 oracle on the X values the device stores (part of the CPU-baseline leg)."""
+    import torch
+    from oracle import model, quant
+    K, chains = spec["K"], spec["chains"]
+    kind, scale = spec["prior"]
+    p = X64.shape[1]
+    beta = torch.empty((chains, K - 1, p), dtype=tdt, device=dev)
+    h.get_state(chains, beta=beta)
+    lp, g = h.logpost_grad(beta)
+    torch.cuda.synchronize()
+    bits, sc = h.get_x()
+    if xdt == "bf16":
+        Xs = quant.bf16_decode(bits).astype(np.float64)
+    elif xdt == "fp8":
+        Xs = quant.fp8_dequantize(bits, sc)
+    else:
+        Xs = X64
+    b0 = beta[0].double().cpu().numpy()
+    lk_o = model.log_kernel(Xs, y, b0, kind, scale)
+    g_o = model.grad_log_kernel(Xs, y, b0, kind, scale)
+    g0 = g[0].double().cpu().numpy()
+    return {"chain": 0, "state": "after the timed iterations",
+            "vs": "FP64 oracle on the stored X values",
+            "logk_rel_err": float(abs(float(lp[0]) - lk_o) / max(1.0, abs(lk_o))),
+            "grad_rel_err": float(np.linalg.norm(g0 - g_o) / max(np.linalg.norm(g_o), 1e-300)),
+            "tol_grad": {"f64": 1e-11, "f32": 1e-5, "bf16": 1e-2, "fp8": 1e-2}[xdt]}
 
 
 # ---------------------------------------------------------------- our arm
@@ -269,10 +310,7 @@ def run_ours(args):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     fused_ms, fused_n = h.fused_kernel_time()
     h.set_timing(False)
-    if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, dev)
     grads = chains * L * args.steps
     value = world * grads / elapsed
     groups = -(-chains // desc["group_chains"])
@@ -309,11 +347,7 @@ def run_ours(args):
             hbn[...] = hsn[0]
         e1.record(stream)
         torch.cuda.synchronize()
-        el = e0.elapsed_time(e1) / 1e3
-        if dist:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
         nbytes = chains * (K - 1) * p * (8 if state == "f64" else 4)
         e2e = {"value": round(world * chains * L * steps_e2e / el, 2), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + chains * 40,
@@ -347,10 +381,11 @@ def run_ours(args):
                             "draws after burn-in, chains pooled"}
         del draws, flat
 
-    cpu = None
+    cpu, accuracy = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         X64 = X.astype(np.float64)
         cpu = cpu_baseline(X64, y, spec, args.cpu_seconds)
+        accuracy = oracle_accuracy(h, X64, y, spec, xdt, tdt, dev)
 
     acc = sum(s["accepted"] for s in stats) / max(1, sum(s["iterations"] for s in stats))
     line = {
@@ -358,7 +393,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": xdt, "data": "synthetic (seeded, shaped like the paper's "
         "high-dimensional multinomial setting)", "config": config_of(args, spec, n * p * xb),
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
         "xpass_gbs": round(achieved, 1), "accept_rate": round(acc, 4), "impl": "ours",
         "clocks": clk.summary(), "engine": desc_all["engine"], "ess": ess_info, "tile_source": tile_source,
         "tune": sorted(tune_table, key=lambda r: r["us"])[:6] if tune_table else None,
@@ -420,10 +455,7 @@ def run_batch_uneven(args):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     fused_ms, fused_n = h.fused_kernel_time()
     h.set_timing(False)
-    if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, dev)
     nprob = len(shapes)
     grads = nprob * chains * L * args.steps
     xb = XBYTES[xdt]

@@ -88,7 +88,7 @@ struct Problem {
   // tensor-core engine
   int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel
   TcPlan tp{};
-  void* bbf = nullptr;      // BF16 coefficient operand boxes [p_pad / 64][N x 128 B]
+  void* bbf = nullptr;      // BF16 coefficient operand boxes [p_pad / 64][2N x 128 B] (hi, lo terms)
   int nlparts = 0;          // log-likelihood partials reduced per chain
 };
 
@@ -348,8 +348,8 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   HMC_CUDA(cudaMalloc(&P.lpart, size_t(P.nlparts) * h->max_chains * sizeof(double)));
   if (P.engine == 2) {
     const TcPlan& tp = P.tp;
-    HMC_CUDA(cudaMalloc(&P.bbf, size_t(tp.N) * P.p_pad * 2));
-    HMC_CUDA(cudaMemsetAsync(P.bbf, 0, size_t(tp.N) * P.p_pad * 2, h->stream));
+    HMC_CUDA(cudaMalloc(&P.bbf, size_t(2 * tp.N) * P.p_pad * 2));     // hi and lo terms
+    HMC_CUDA(cudaMemsetAsync(P.bbf, 0, size_t(2 * tp.N) * P.p_pad * 2, h->stream));
   }
   for (StateSet* s : {&P.cs, &P.us}) {
     for (void** q : {&s->beta, &s->eta, &s->grad, &s->beta0, &s->grad0}) {

@@ -8,8 +8,10 @@
 // of the coefficients, and accumulates the gradient rows of that slice in
 // TMEM across all of the cluster's tiles.  Per tile:
 //   sweep 1  bulk-async copies bring 128 x 64 boxes of X together with the
-//            matching 64-column box of the BF16 coefficients; MMA
-//            D_z[128 x N] += X_box . B_box^T (both operands K-major).
+//            matching 64-column box of the coefficients as two BF16 terms
+//            (B = B_hi + B_lo); MMAs D_z[128 x N] += X_box . B_hi^T and
+//            += X_box . B_lo^T (both operands K-major), so the logits carry
+//            the coefficients to ~16 bits.
 //            X and the coefficient operand are stored in device memory as
 //            the shared-memory image of these boxes (128-byte swizzle already
 //            applied, each box 16 KB contiguous), so every copy is a long
@@ -252,10 +254,10 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
           unsigned char* xdst = fp8 ? stage + size_t(st) * 2 * kFp8BoxBytes : sp;
           if (!s2) {
             const int kb = int(rank) * NKB + b;
-            mbar_arrive_expect_tx(&full[st], xbox + uint32_t(N * 128));
+            mbar_arrive_expect_tx(&full[st], xbox + uint32_t(2 * N * 128));
             bulk_g2s(xdst, xt + size_t(kb) * xbox, xbox, &full[st]);
-            bulk_g2s(sp + kBoxBytes, reinterpret_cast<const unsigned char*>(A.bs) + size_t(kb) * N * 128,
-                     uint32_t(N * 128), &full[st]);
+            bulk_g2s(sp + kBoxBytes, reinterpret_cast<const unsigned char*>(A.bs) + size_t(kb) * 2 * N * 128,
+                     uint32_t(2 * N * 128), &full[st]);
           } else {
             const int kb = int(rank) * NKB + 2 * b;
             mbar_arrive_expect_tx(&full[st], 2 * xbox);
@@ -306,12 +308,14 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
             }
             fence_after_sync();
             const uint32_t xa = smem_u32(ring + size_t(st) * A.stage_bytes);
-            const uint32_t ba = xa + kBoxBytes;
+            const uint32_t ba = xa + kBoxBytes;             // hi rows; lo rows N * 128 bytes further
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
               const uint64_t ad = smem_desc(xa + 32u * s, 16u, 1024u, 2u);
               const uint64_t bd = smem_desc(ba + 32u * s, 16u, 1024u, 2u);
+              const uint64_t bl = smem_desc(ba + uint32_t(N) * 128u + 32u * s, 16u, 1024u, 2u);
               mma_bf16(tmem, ad, bd, id_s1, (kb > 0 || s > 0) ? 1u : 0u);
+              mma_bf16(tmem, ad, bl, id_s1, 1u);
             }
             mma_commit(&empty[st]);
           }
@@ -661,9 +665,21 @@ __global__ void tiles_to_rows_kernel(const __nv_bfloat16* tiles, uint16_t* out, 
   }
 }
 
-// FP32 coefficients [C][p_pad] -> BF16 operand boxes [p_pad / 64][N rows x 128 B]
-// (rows C..N-1 zero), K-major with the 128-byte swizzle.  With FP8 X the
-// column scales are folded in: X B = X_q (diag(s) B).
+// Coefficient value v of class row k, column col -> its two BF16 terms in the
+// operand box of column block col / 64: rows [0, N) hold hi = bf16(v), rows
+// [N, 2N) hold lo = bf16(v - hi), so hi + lo carries v to about 16 bits and the
+// logits X (hi + lo)^T lose nothing to the rounding of the coefficients.
+__device__ __forceinline__ void put_coef(unsigned char* out, int N, int k, int64_t col, float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  const size_t box = size_t(col / kBox) * 2 * N * 128;
+  *reinterpret_cast<__nv_bfloat16*>(out + box + sw128_offset(k, int(col % kBox))) = hi;
+  *reinterpret_cast<__nv_bfloat16*>(out + box + sw128_offset(N + k, int(col % kBox))) = lo;
+}
+
+// FP32 coefficients [C][p_pad] -> BF16 operand boxes [p_pad / 64][2N rows x 128 B]
+// (hi rows then lo rows; rows C..N-1 of each zero), K-major with the 128-byte
+// swizzle.  With FP8 X the column scales are folded in: X B = X_q (diag(s) B).
 __global__ void beta_to_tiles_kernel(const float* beta, const float* scales, __nv_bfloat16* out, int C, int N,
                                      int p_pad) {
   const int64_t total = int64_t(N) * p_pad;
@@ -671,9 +687,7 @@ __global__ void beta_to_tiles_kernel(const float* beta, const float* scales, __n
     const int k = int(i / p_pad);
     const int64_t col = i - int64_t(k) * p_pad;
     const float v = (k < C) ? beta[size_t(k) * p_pad + col] * (scales ? scales[col] : 1.0f) : 0.f;
-    const int64_t kb = col / kBox;
-    const size_t off = size_t(kb) * N * 128 + sw128_offset(k, int(col % kBox));
-    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(out) + off) = __float2bfloat16_rn(v);
+    put_coef(reinterpret_cast<unsigned char*>(out), N, k, col, v);
   }
 }
 
@@ -685,9 +699,7 @@ __global__ void beta_to_tiles_batched_kernel(const BetaTiles* __restrict__ table
     const int k = int(i / b.p_pad);
     const int64_t col = i - int64_t(k) * b.p_pad;
     const float v = (k < C) ? b.beta[size_t(k) * b.p_pad + col] * (b.scales ? b.scales[col] : 1.0f) : 0.f;
-    const int64_t kb = col / kBox;
-    const size_t off = size_t(kb) * b.N * 128 + sw128_offset(k, int(col % kBox));
-    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(b.out) + off) = __float2bfloat16_rn(v);
+    put_coef(reinterpret_cast<unsigned char*>(b.out), b.N, k, col, v);
   }
 }
 
@@ -709,7 +721,7 @@ bool tc_plan(int64_t p, int C, int S, TcPlan* out) {
   out->MB = MB;
   out->S = S;
   out->tmem_cols = tcols;
-  out->stage_bytes = uint32_t(tc::al(size_t(tc::kBoxBytes) + std::max<size_t>(tc::kBoxBytes, size_t(N) * 128), 1024));
+  out->stage_bytes = uint32_t(tc::al(size_t(tc::kBoxBytes) + std::max<size_t>(tc::kBoxBytes, size_t(2 * N) * 128), 1024));
   return true;
 }
 
