@@ -370,11 +370,12 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
   if (producer) {
     // ---------------------------------------------------------------- producer
     const XT* Xs = static_cast<const XT*>(A.X) + size_t(rank) * PC;
-    // The ring holds few tiles; HBM latency under full load is several
-    // microseconds, so tiles further ahead are pulled into L2 with bulk
-    // prefetches (about 256 KB per CTA in flight) and the ring's copies hit L2.
+    // Tiles ahead of the ring are pulled into L2 with bulk prefetches, up to
+    // about 64 KB per CTA beyond the ring (small ring slots).  More is slower:
+    // prefetched tiles then evict tiles the gradient sweep has yet to re-read
+    // from L2 (measured on the n=10^4 p=5000 FP32 problem).
     const int64_t tile_bytes = int64_t(BM) * row_bytes;
-    const int64_t PF = max(int64_t(NSTAGE), min(int64_t(24), (int64_t(256) * 1024 + tile_bytes - 1) / tile_bytes));
+    const int64_t PF = max(int64_t(NSTAGE), min(int64_t(24), (int64_t(64) * 1024 + tile_bytes - 1) / tile_bytes));
     auto prefetch = [&](int64_t t) {
       const int rv = rows_of(t);
       const XT* src = Xs + size_t(row0_of(t)) * A.p_pad;
