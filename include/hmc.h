@@ -206,9 +206,14 @@ hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales);
 const char* hmc_describe(hmc_handle h);
 
 /*
- * hmc_last_launch_stats -- device time of the fused kernel over the most
- * recent call, measured with CUDA events on the handle's stream when
- * enabled with hmc_set_timing(h, 1): total milliseconds and launches.
+ * hmc_set_timing / hmc_fused_kernel_time -- device time of the fused kernel,
+ * measured with CUDA events on the handle's stream around every fused launch
+ * once enabled with hmc_set_timing(h, 1), or around every k-th one with
+ * hmc_set_timing(h, k) for k > 1 (fewer events in a captured iteration);
+ * enabling resets the totals: total milliseconds and timed launches since then.  hmc_sample replays a captured
+ * graph per iteration without synchronising between replays; its events are
+ * read after the last iteration, so a sampling call contributes the launches
+ * of its last iteration.
  */
 hmc_status hmc_set_timing(hmc_handle h, int32_t enable);
 hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launches);

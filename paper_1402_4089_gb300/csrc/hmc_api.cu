@@ -114,6 +114,8 @@ struct hmc_ctx {
   void* staging[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t staging_cap[4] = {0, 0, 0, 0};
   bool timing = false;
+  int timing_period = 1;    // events around every timing_period-th fused launch
+  int64_t timing_seq = 0;   // fused launches issued since timing was enabled
   double timing_ms = 0.0;
   int64_t timing_launches = 0;
   FusedTimer timer;
@@ -138,6 +140,7 @@ struct hmc_ctx {
   double g_eps = 0.0;
   const void* g_samples = nullptr;
   bool g_temps = false, g_timing = false;
+  int g_period = 1;
   const double* g_temps_ptr = nullptr;
   cudaStream_t g_stream = nullptr;
   size_t g_pairs = 0;
@@ -424,7 +427,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     // Inside a stream capture the events must become graph nodes.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (h->timing) {
+    const bool timed = h->timing && (h->timing_seq++ % h->timing_period) == 0;
+    if (timed) {
       HMC_CUDA(cudaStreamIsCapturing(stream, &cap));
       HMC_TRY(timer_pair(h, &e0, &e1));
       HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal)
@@ -488,7 +492,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
                     cudaGetErrorString(le), P.engine, P.nclusters, P.S, P.smem, C, P.BM, P.NSTAGE);
       return fail(HMC_ECUDA, buf);
     }
-    if (h->timing)
+    if (timed)
       HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
                                                     : cudaEventRecord(e1, stream));
   }
@@ -680,7 +684,8 @@ hmc_status run_lpg_all(hmc_ctx* h, bool chain_state, int chains, cudaStream_t st
                                       mtc, chains, h->tb_max_elems, stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (h->timing) {
+  const bool timed = h->timing && (h->timing_seq++ % h->timing_period) == 0;
+  if (timed) {
     HMC_CUDA(cudaStreamIsCapturing(stream, &cap));
     HMC_TRY(timer_pair(h, &e0, &e1));
     HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal)
@@ -694,7 +699,7 @@ hmc_status run_lpg_all(hmc_ctx* h, bool chain_state, int chains, cudaStream_t st
           : simt_launch_batched(h->xt, h->b_CT, h->b_table + (chain_state ? 0 : m), h->b_first, m, chains,
                                 h->b_total_clusters, h->b_S, h->b_NT, h->b_smem, stream);
   if (le != cudaSuccess) return fail(HMC_ECUDA, std::string("batched fused launch failed: ") + cudaGetErrorString(le));
-  if (h->timing)
+  if (timed)
     HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
                                                   : cudaEventRecord(e1, stream));
   return HMC_OK;
@@ -1142,7 +1147,7 @@ hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double e
     const bool use_temps = temps != nullptr;
     const bool timing = h->timing;
     if (h->gexec && !(h->g_chains == chains && h->g_L == L && h->g_eps == eps && h->g_thin == thin &&
-                      h->g_samples == sd && h->g_temps == use_temps && h->g_temps_ptr == h->temps_d && h->g_timing == timing &&
+                      h->g_samples == sd && h->g_temps == use_temps && h->g_temps_ptr == h->temps_d && h->g_timing == timing && h->g_period == h->timing_period &&
                       h->g_stream == rs_stream)) {
       cudaGraphExecDestroy(h->gexec);
       h->gexec = nullptr;
@@ -1195,6 +1200,7 @@ hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double e
       h->g_temps = use_temps;
       h->g_temps_ptr = h->temps_d;
       h->g_timing = timing;
+      h->g_period = h->timing_period;
       h->g_stream = rs_stream;
       h->g_pairs = h->timer.used;
       h->timer.used = 0;
@@ -1209,7 +1215,10 @@ hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double e
         rs = fail(HMC_ECUDA, "cudaGraphLaunch failed");
         break;
       }
-      if (timing) {
+      // The graph's timing events are rewritten by every replay: read them once,
+      // after the last replay, so the replays run back to back (no host
+      // synchronisation inside the call).
+      if (timing && t == iters - 1) {
         h->timer.used = h->g_pairs;
         if ((rs = timer_harvest(h)) != HMC_OK) break;
       }
@@ -1287,6 +1296,8 @@ const char* hmc_describe(hmc_handle h) { return h ? h->desc.c_str() : "{}"; }
 hmc_status hmc_set_timing(hmc_handle h, int32_t enable) {
   if (!h) return fail(HMC_EINVAL, "NULL handle");
   h->timing = enable != 0;
+  h->timing_period = enable > 1 ? enable : 1;
+  h->timing_seq = 0;
   h->timing_ms = 0.0;
   h->timing_launches = 0;
   h->timer.used = 0;

@@ -239,8 +239,9 @@ class Handle:
         _check(lib().hmc_get_x(self._h, b, _ptr(out), _ptr(sc)))
         return out, sc
 
-    def set_timing(self, on):
-        _check(lib().hmc_set_timing(self._h, 1 if on else 0))
+    def set_timing(self, on, every=1):
+        """Time the fused launches with CUDA events (every `every`-th launch)."""
+        _check(lib().hmc_set_timing(self._h, (max(1, int(every)) if on else 0)))
 
     def fused_kernel_time(self):
         ms = ctypes.c_double(0)
