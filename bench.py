@@ -315,7 +315,10 @@ def run_ours(args):
     grads = chains * L * args.steps
     value = world * grads / elapsed
     groups = -(-chains // desc["group_chains"])
-    launches_per_step = 1 + L * (groups + 1) + 1
+    # traj_start + per leapfrog step (per chain group: [operand boxes +] fused pass, then the
+    # reduce/update) + select
+    per_group = 2 if desc_all["engine"] == "tcgen05" else 1
+    launches_per_step = 1 + L * (groups * per_group + 1) + 1
 
     # roofline of the fused pass (X streamed once per gradient)
     xb = XBYTES[xdt]
