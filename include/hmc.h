@@ -73,8 +73,10 @@ typedef struct {
                              kernel (BF16 or FP8 storage; MMA operands BF16, FP32 accumulation) */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
-  int32_t tile[4];        /* {cluster size 1..16, 0, 0, ring slots}; 0 = chosen (entries 1, 2 reserved,
-                             must be 0 on the CUDA-core engine) */
+  int32_t tile[4];        /* {cluster size 1..16, exchange depth, sweep lookahead, ring slots}; 0 =
+                             chosen.  Depth (partial-logit slots and R buffers, 1..4) and lookahead
+                             (tiles between the two sweeps, 1..4) apply to the tensor-core engine and
+                             must be 0 on the CUDA-core engine */
 } hmc_opts;
 
 /* Per-chain counters of hmc_sample (host memory, one entry per chain). */

@@ -224,17 +224,30 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
     for (int g = h->max_chains; g >= 1; --g) {
       TcPlan pl;
       if (!tc_plan(P.p, g * P.Km1, S, &pl)) continue;
+      // Exchange depth (partial-logit slots and R buffers) and sweep lookahead:
+      // 2 when TMEM holds a second logit accumulator, unless overridden by
+      // opts.tile[1] / tile[2]; the deepest ring that fits shared memory next
+      // to them, falling back to depth 1 when depth 2 leaves no room.
+      const int d_want = h->tile[1] ? h->tile[1] : (pl.nz >= 2 ? 2 : 1);
+      const int la_want = h->tile[2] ? h->tile[2] : (pl.nz >= 2 ? 2 : 1);
       int nst = 0;
       size_t smem = 0;
-      for (int s = 6; s >= 2; --s) {
-        if (h->tile[3] && s != h->tile[3]) continue;
-        // At least half of an SM's shared memory: one CTA per SM, so no CTA
-        // ever waits for TMEM held by a CTA of another cluster.
-        const size_t sm = std::max(tc_smem_bytes(pl, s, g, h->xt == HMC_FP8E4M3), size_t(116 * 1024));
-        if (sm <= size_t(smem_max)) {
-          nst = s;
-          smem = sm;
-          break;
+      for (int d = d_want; d >= 1 && !nst; --d) {
+        if (h->tile[1] && d != h->tile[1]) continue;
+        pl.slots = pl.rbufs = d;
+        // Sweep 2 of tile u waits for the R rows of u, which need every CTA's
+        // sweep 2 of tile u - d: lookahead below nz + 2d - 1 keeps that chain acyclic.
+        pl.la = std::max(1, std::min(d == d_want ? la_want : 1, pl.nz + 2 * d - 2));
+        for (int s = 6; s >= 2; --s) {
+          if (h->tile[3] && s != h->tile[3]) continue;
+          // At least half of an SM's shared memory: one CTA per SM, so no CTA
+          // ever waits for TMEM held by a CTA of another cluster.
+          const size_t sm = std::max(tc_smem_bytes(pl, s, g, h->xt == HMC_FP8E4M3), size_t(116 * 1024));
+          if (sm <= size_t(smem_max)) {
+            nst = s;
+            smem = sm;
+            break;
+          }
         }
       }
       if (!nst) continue;
@@ -756,10 +769,10 @@ hmc_status validate_opts(const hmc_opts* o) {
   if (o->spin_limit < 0) return fail(HMC_EINVAL, "opts.spin_limit must be >= 0");
   const int* t = o->tile;
   if (t[0] < 0 || t[0] > 16) return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be in [0, 16]");
-  if (t[1] != 0 && t[1] != 16 && t[1] != 32 && t[1] != 64)
-    return fail(HMC_EINVAL, "opts.tile[1] (rows per super-tile) must be 0, 16, 32 or 64");
-  if (t[2] != 0 && t[2] != 8 && t[2] != 16 && t[2] != 32)
-    return fail(HMC_EINVAL, "opts.tile[2] (rows per chunk) must be 0, 8, 16 or 32");
+  if (t[1] < 0 || t[1] > kTcMaxDepth)
+    return fail(HMC_EINVAL, "opts.tile[1] (tensor-core exchange depth) must be in [0, " + std::to_string(kTcMaxDepth) + "]");
+  if (t[2] < 0 || t[2] > kTcMaxDepth)
+    return fail(HMC_EINVAL, "opts.tile[2] (tensor-core sweep lookahead) must be in [0, " + std::to_string(kTcMaxDepth) + "]");
   if (t[3] != 0 && (t[3] < 2 || t[3] > 6)) return fail(HMC_EINVAL, "opts.tile[3] (ring chunks) must be 0 or in [2, 6]");
   return HMC_OK;
 }
@@ -776,9 +789,10 @@ void build_description(hmc_ctx* h) {
     std::snprintf(buf, sizeof(buf),
                   "%s{\"n\": %lld, \"p\": %d, \"K\": %d, \"p_pad\": %d, \"S\": %d, \"BM\": %d, \"CR\": %d, "
                   "\"NT\": %d, \"NSTAGE\": %d, \"PC\": %d, \"nclusters\": %d, \"smem\": %zu, \"group_chains\": %d, "
-                  "\"ct\": %d}",
+                  "\"ct\": %d, \"nz\": %d, \"depth\": %d, \"lookahead\": %d}",
                   b ? ", " : "", (long long)P.n, P.p, P.K, P.p_pad, P.S, P.BM, P.CR, P.NT, P.NSTAGE, P.PC, P.nclusters,
-                  P.smem, P.group_chains, P.ct_launch);
+                  P.smem, P.group_chains, P.ct_launch, P.engine == 2 ? P.tp.nz : 0, P.engine == 2 ? P.tp.slots : 0,
+                  P.engine == 2 ? P.tp.la : 0);
     s += buf;
   }
   s += "]}";

@@ -77,7 +77,12 @@ cudaError_t simt_launch_batched(int xt, int C, const LpgArgs* table, const int* 
 struct TcPlan {
   int N, NP, PC, MB, S;
   uint32_t tmem_cols, stage_bytes;
+  int nz = 1;      // logit accumulators in TMEM
+  int slots = 1;   // partial-logit receive slots
+  int rbufs = 1;   // R operand buffers
+  int la = 1;      // lookahead (tiles) between the two sweeps
 };
+constexpr int kTcMaxDepth = 4;
 struct TcLaunch {
   const void* xs;           // X boxes (tc_x_to_tiles / tc_x_to_tiles_fp8 layout)
   const float* xscale;      // FP8 column scales (nullptr for BF16)

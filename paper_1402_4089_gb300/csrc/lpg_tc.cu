@@ -48,9 +48,7 @@ constexpr int kThreadsFp8 = 576;    // + warps 14-17 (FP8 converters)
 constexpr int kSoftThreads = 256;   // warps 6-13
 constexpr int kConvWarps = 4;       // warps 14-17: FP8 -> BF16 converters (idle for BF16 X)
 constexpr int kFp8BoxBytes = 128 * 64;   // one FP8 box: 128 rows x 64 bytes, row-major
-constexpr int kLA = 1;           // tiles of lookahead between the two sweeps of a tile
-constexpr int kSlots = 1;        // partial-logit receive slots (reuse gated by a cluster 'consumed' barrier)
-constexpr int kRbuf = 1;         // R operand buffers (reuse gated by a cluster 'free' barrier)
+constexpr int kMaxDepth = kTcMaxDepth;   // largest number of logit accumulators / exchange slots / R buffers
 constexpr int kRows = 128;
 constexpr int kBox = 64;          // BF16 elements per 128-byte box row
 constexpr int kBoxBytes = kRows * 128;
@@ -73,6 +71,11 @@ struct TcArgs {
   long long spin_limit;
   int32_t inject_timeout;
   int32_t fp8;
+  // Pipeline depths (host-chosen from the TMEM and shared-memory budgets):
+  int32_t nz;      // logit accumulators in TMEM (sweep 1 of the next tiles runs while one drains)
+  int32_t slots;   // partial-logit receive slots (reuse gated by a cluster 'consumed' barrier)
+  int32_t rbufs;   // R operand buffers (reuse gated by a cluster 'free' barrier)
+  int32_t la;      // tiles of lookahead between the two sweeps of a tile
 };
 
 struct Smem {
@@ -81,21 +84,22 @@ struct Smem {
 
 __host__ __device__ inline size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// zx: [kSlots][S][RS][N] fp32 partial logits received for the owned rows;
+// zx: [slots][S][RS][N] fp32 partial logits received for the owned rows;
 // rloc: [RS][NP] bf16 residual rows of the owned rows before they are pushed.
-__host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int NP, int N, int S, int chains, bool fp8) {
+__host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int NP, int N, int S, int chains, bool fp8,
+                                            int slots, int rbufs) {
   Smem L;
   const int RS = kRows / S;
   size_t off = 0;
   L.ring = off;  off = al(off + size_t(NST) * stage_bytes, 1024);
   // FP8: each ring slot has a 16 KB landing area for its FP8 box (sweep 1) or box pair (sweep 2).
   L.stage = off; off = al(off + (fp8 ? size_t(NST) * 2 * kFp8BoxBytes : 0), 1024);
-  L.rbuf = off;  off = al(off + kRbuf * size_t(NP / kBox) * kBoxBytes, 1024);
-  L.zx = off;    off = al(off + size_t(kSlots) * kRows * N * 4, 16);
+  L.rbuf = off;  off = al(off + size_t(rbufs) * (NP / kBox) * kBoxBytes, 1024);
+  L.zx = off;    off = al(off + size_t(slots) * kRows * N * 4, 16);
   L.rloc = off;  off = al(off + size_t(RS) * NP * 2, 16);
   L.lacc = off;  off = al(off + size_t(RS) * chains * 8, 16);
   L.ylab = off;  off = al(off + size_t(RS) * 4, 16);
-  L.bars = off;  off = al(off + size_t(3 * NST + 20) * 8 + 16, 16);
+  L.bars = off;  off = al(off + size_t(3 * NST + 7 * kMaxDepth + 6) * 8 + 16, 16);
   L.total = off + 1024;  // slack for aligning the dynamic base to 1024
   return L;
 }
@@ -140,7 +144,8 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
   const int chains = A.chains, C = A.C, Km1 = A.Km1;
   const int C8 = (C + 7) / 8;                      // 16-byte chunks of one R row
   constexpr bool fp8 = kFP8;
-  const Smem Lo = smem_layout(NST, A.stage_bytes, NP, N, S, chains, fp8);
+  const int NZ = A.nz, SLOTS = A.slots, RBUFS = A.rbufs, LA = A.la;
+  const Smem Lo = smem_layout(NST, A.stage_bytes, NP, N, S, chains, fp8, SLOTS, RBUFS);
   unsigned char* ring = smem + Lo.ring;
   unsigned char* stage = smem + Lo.stage;
   unsigned char* rbuf = smem + Lo.rbuf;
@@ -152,18 +157,18 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
   uint64_t* full = bars;
   uint64_t* empty = bars + NST;
   uint64_t* conv = bars + 2 * NST;      // FP8: ring slot converted to BF16 (kConvWarps arrivals)
-  uint64_t* zdone = bars + 3 * NST;
-  uint64_t* zfree = zdone + 1;
-  uint64_t* zrdy = zdone + 2;    // partial logits of the owned rows received
-  uint64_t* zxfree = zdone + 3;  // every owner has consumed the previous tile's partials
-  uint64_t* rfull = zdone + 4;   // [2] every owner's R rows received (R buffer b)
-  uint64_t* rfree = zdone + 6;   // [2] this CTA's gradient sweep finished reading R buffer b
-  uint64_t* rfreec = zdone + 8;  // [2] every CTA's gradient sweep finished reading R buffer b
-  uint64_t* gdone = zdone + 10;
-  uint64_t* drain = zdone + 11;
-  uint64_t* never = zdone + 12;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(zdone + 13);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(zdone + 14);
+  uint64_t* zdone = bars + 3 * NST;        // [nz] sweep 1 of a tile finished in accumulator z
+  uint64_t* zfree = zdone + kMaxDepth;      // [nz] accumulator z drained
+  uint64_t* zrdy = zfree + kMaxDepth;       // [slots] partial logits of the owned rows received
+  uint64_t* zxfree = zrdy + kMaxDepth;      // [slots] every owner has consumed the slot's partials
+  uint64_t* rfull = zxfree + kMaxDepth;     // [rbufs] every owner's R rows received (R buffer b)
+  uint64_t* rfree = rfull + kMaxDepth;      // [rbufs] this CTA's gradient sweep finished reading R buffer b
+  uint64_t* rfreec = rfree + kMaxDepth;     // [rbufs] every CTA's gradient sweep finished reading R buffer b
+  uint64_t* gdone = rfreec + kMaxDepth;
+  uint64_t* drain = gdone + 1;
+  uint64_t* never = gdone + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gdone + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gdone + 4);
   const size_t rbuf_bytes = size_t(NP / kBox) * kBoxBytes;
 
   if (tid == 0) {
@@ -172,11 +177,11 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
       mbar_init(&empty[s], 1);
       mbar_init(&conv[s], kConvWarps);
     }
-    mbar_init(zdone, 1);
-    mbar_init(zfree, 4);
-    mbar_init(zrdy, 1);
-    mbar_init(zxfree, S);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kMaxDepth; ++b) {
+      mbar_init(&zdone[b], 1);
+      mbar_init(&zfree[b], 4);
+      mbar_init(&zrdy[b], 1);
+      mbar_init(&zxfree[b], S);
       mbar_init(&rfull[b], 1);
       mbar_init(&rfree[b], 1);
       mbar_init(&rfreec[b], S);
@@ -188,7 +193,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
     fence_mbar_init_cluster();
   }
   // R operand buffer and the local R rows start (and stay, past column C) zero.
-  for (size_t i = tid; i < kRbuf * rbuf_bytes / 16; i += kThreads)
+  for (size_t i = tid; i < RBUFS * rbuf_bytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(rbuf)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < RS * NP / 8; i += kThreads) reinterpret_cast<uint4*>(rloc)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < RS * chains; i += kThreads) lacc[i] = 0.0;
@@ -213,9 +218,9 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
   const int64_t nphase = 2 * T;
   const int NKB = A.PC / kBox;
   const int64_t nkb_all = A.p_pad / kBox;
-  // Phase k of the sweep order: S1(0..first-1), then pairs S1(v), S2(v-kLA),
+  // Phase k of the sweep order: S1(0..first-1), then pairs S1(v), S2(v-la),
   // then the remaining S2 phases.  Returns the tile; *s2 marks a gradient sweep.
-  const int64_t first = T < kLA ? T : kLA;
+  const int64_t first = T < LA ? T : LA;
   auto phase = [&](int64_t k, bool* s2) -> int64_t {
     if (k < first) { *s2 = false; return k; }
     const int64_t k1 = k - first;
@@ -271,10 +276,10 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
         (void)wait_bounded(&full[jj % NST], uint32_t((jj / NST) & 1), A.spin_limit, abort_flag, false);
     } else if (lane == 1) {
       // As soon as this CTA's gradient sweep of tile u has finished reading R
-      // buffer u % kRbuf, tell every CTA that may push the R rows of tile u + kRbuf.
-      for (int64_t u = 0; u + kRbuf < T && !*abort_flag; ++u) {
-        const int b = int(u % kRbuf);
-        if (!wait_bounded(&rfree[b], uint32_t((u / kRbuf) & 1), A.spin_limit, abort_flag, false)) {
+      // buffer u % rbufs, tell every CTA that may push the R rows of tile u + rbufs.
+      for (int64_t u = 0; u + RBUFS < T && !*abort_flag; ++u) {
+        const int b = int(u % RBUFS);
+        if (!wait_bounded(&rfree[b], uint32_t((u / RBUFS) & 1), A.spin_limit, abort_flag, false)) {
           fail(ERR_TIMEOUT_MMA);
           break;
         }
@@ -295,10 +300,13 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
         bool s2;
         const int64_t u = phase(k, &s2);
         if (!s2) {
-          if (u >= 1 && !wait_bounded(zfree, uint32_t((u - 1) & 1), A.spin_limit, abort_flag, false)) {
+          // Accumulator z = u % nz was last used by tile u - nz: it must be drained.
+          const int z = int(u % NZ);
+          if (u >= NZ && !wait_bounded(&zfree[z], uint32_t(((u / NZ) - 1) & 1), A.spin_limit, abort_flag, false)) {
             fail(ERR_TIMEOUT_MMA);
             break;
           }
+          const uint32_t dz = tmem + uint32_t(z * N);
           fence_after_sync();
           for (int kb = 0; kb < NKB; ++kb, ++j) {
             const int st = int(j % NST);
@@ -314,17 +322,17 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
               const uint64_t ad = smem_desc(xa + 32u * s, 16u, 1024u, 2u);
               const uint64_t bd = smem_desc(ba + 32u * s, 16u, 1024u, 2u);
               const uint64_t bl = smem_desc(ba + uint32_t(N) * 128u + 32u * s, 16u, 1024u, 2u);
-              mma_bf16(tmem, ad, bd, id_s1, (kb > 0 || s > 0) ? 1u : 0u);
-              mma_bf16(tmem, ad, bl, id_s1, 1u);
+              mma_bf16(dz, ad, bd, id_s1, (kb > 0 || s > 0) ? 1u : 0u);
+              mma_bf16(dz, ad, bl, id_s1, 1u);
             }
             mma_commit(&empty[st]);
           }
           if (*abort_flag) break;
-          mma_commit(zdone);
+          mma_commit(&zdone[z]);
         } else {
-          const int rbi = int(u % kRbuf);
+          const int rbi = int(u % RBUFS);
           mbar_arrive_expect_tx(&rfull[rbi], rbytes);
-          if (!wait_bounded(&rfull[rbi], uint32_t((u / kRbuf) & 1), A.spin_limit, abort_flag, true)) {
+          if (!wait_bounded(&rfull[rbi], uint32_t((u / RBUFS) & 1), A.spin_limit, abort_flag, true)) {
             fail(ERR_TIMEOUT_EXCHANGE);
             break;
           }
@@ -337,7 +345,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
             }
             fence_after_sync();
             const uint32_t xa = smem_u32(ring + size_t(st) * A.stage_bytes);
-            const uint32_t dcol = tmem + uint32_t(N + mb * N);
+            const uint32_t dcol = tmem + uint32_t((NZ + mb) * N);
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
               const uint64_t ad = smem_desc(xa + 2048u * s, uint32_t(kBoxBytes), 1024u, 2u);
@@ -407,13 +415,15 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
     const uint32_t tq = tmem + (uint32_t(32 * q) << 16);
     const uint32_t owner = uint32_t(row / RS), rl = uint32_t(row % RS);
     for (int64_t u = 0; u < T && !*abort_flag; ++u) {
-      const int slot = int(u % kSlots);
-      if (!wait_bounded(zdone, uint32_t(u & 1), A.spin_limit, abort_flag, false)) {
+      const int slot = int(u % SLOTS);
+      const int z = int(u % NZ);
+      if (!wait_bounded(&zdone[z], uint32_t((u / NZ) & 1), A.spin_limit, abort_flag, false)) {
         fail(ERR_TIMEOUT_MMA);
         break;
       }
       fence_after_sync();
-      if (u >= 1 && !wait_bounded(zxfree, uint32_t((u - 1) & 1), A.spin_limit, abort_flag, true)) {
+      // The owners' slot was last filled with tile u - slots: they must have consumed it.
+      if (u >= SLOTS && !wait_bounded(&zxfree[slot], uint32_t(((u / SLOTS) - 1) & 1), A.spin_limit, abort_flag, true)) {
         fail(ERR_TIMEOUT_SLOT);
         break;
       }
@@ -423,13 +433,13 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
       const uint32_t rbar = (S > 1) ? map_peer(smem_u32(&zrdy[slot]), owner) : smem_u32(&zrdy[slot]);
       for (int c0 = 0; c0 < N; c0 += 16) {
         float v[16];
-        tmem_ld16(tq + uint32_t(c0), v);
+        tmem_ld16(tq + uint32_t(z * N + c0), v);
 #pragma unroll
         for (int e = 0; e < 16; e += 4) st_async_v4f(raddr + uint32_t(c0 + e) * 4u, v[e], v[e + 1], v[e + 2], v[e + 3], rbar);
       }
       fence_before_sync();
       __syncwarp();
-      if (lane == 0) mbar_arrive_local(zfree);
+      if (lane == 0) mbar_arrive_local(&zfree[z]);
     }
     // Drain the gradient accumulators of this CTA's column slice.
     bool gok = false;
@@ -445,7 +455,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
         const float sc = A.xscale ? A.xscale[col] : 1.0f;   // g = diag(s) X_q^T R
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
-          tmem_ld16(tq + uint32_t(N + mb * N + c0), v);
+          tmem_ld16(tq + uint32_t((NZ + mb) * N + c0), v);
 #pragma unroll
           for (int e = 0; e < 16; ++e)
             if (c0 + e < C) gp[size_t(c0 + e) * A.p_pad + col] = v[e] * sc;
@@ -464,8 +474,8 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
     const int sw = warp - 6;                // 0..7
     const uint32_t rb_local = smem_u32(rbuf);
     for (int64_t u = 0; u < T && !*abort_flag; ++u) {
-      const int slot = int(u % kSlots);
-      const uint32_t use_par = uint32_t((u / kSlots) & 1);
+      const int slot = int(u % SLOTS);
+      const uint32_t use_par = uint32_t((u / SLOTS) & 1);
       const int64_t row0 = (cl + u * nclu) * kRows;
       if (st == 0) mbar_arrive_expect_tx(&zrdy[slot], uint32_t(kRows) * N * 4);
       if (st < RS) {
@@ -510,13 +520,13 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
       // The partials of tile u are consumed: peers may push tile u + 1.
       named_bar_soft();
       if (sw == 1 && lane < S)
-        mbar_arrive_remote(S > 1 ? map_peer(smem_u32(zxfree), uint32_t(lane)) : smem_u32(zxfree));
-      // R buffer b = u % kRbuf: every CTA's gradient sweep of tile u - kRbuf
+        mbar_arrive_remote(S > 1 ? map_peer(smem_u32(&zxfree[slot]), uint32_t(lane)) : smem_u32(&zxfree[slot]));
+      // R buffer b = u % rbufs: every CTA's gradient sweep of tile u - rbufs
       // must be done reading it.
-      const int rbi = int(u % kRbuf);
+      const int rbi = int(u % RBUFS);
       bool fok = true;
-      if (u >= kRbuf && st == 0) {
-        fok = wait_bounded(&rfreec[rbi], uint32_t(((u - kRbuf) / kRbuf) & 1), A.spin_limit, abort_flag, true);
+      if (u >= RBUFS && st == 0) {
+        fok = wait_bounded(&rfreec[rbi], uint32_t(((u - RBUFS) / RBUFS) & 1), A.spin_limit, abort_flag, true);
         if (!fok) fail(ERR_TIMEOUT_EXCHANGE);
       }
       if (!named_bar_soft_and(fok && !*abort_flag)) break;
@@ -711,10 +721,14 @@ bool tc_plan(int64_t p, int C, int S, TcPlan* out) {
   if (N > 256) return false;
   const int PC = int((p + int64_t(128) * S - 1) / (int64_t(128) * S) * 128);
   const int MB = PC / 128;
-  const int cols = N * (1 + MB);
-  if (cols > 512) return false;
+  if (N * (1 + MB) > 512) return false;
+  // As many logit accumulators as TMEM holds next to the gradient slice.
+  const int nz = std::max(1, std::min(kTcMaxDepth, (512 - N * MB) / N));
+  const int cols = N * (nz + MB);
   uint32_t tcols = 32;
   while (tcols < uint32_t(cols)) tcols <<= 1;
+  out->nz = nz;
+  out->slots = out->rbufs = out->la = 1;
   out->N = N;
   out->NP = (N + 63) / 64 * 64;
   out->PC = PC;
@@ -726,7 +740,7 @@ bool tc_plan(int64_t p, int C, int S, TcPlan* out) {
 }
 
 size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains, bool fp8) {
-  return tc::smem_layout(NST, pl.stage_bytes, pl.NP, pl.N, pl.S, chains, fp8).total;
+  return tc::smem_layout(NST, pl.stage_bytes, pl.NP, pl.N, pl.S, chains, fp8, pl.slots, pl.rbufs).total;
 }
 
 static void (*tc_kernel(bool fp8))(const tc::TcArgs) { return fp8 ? tc::lpg_tc_kernel<true> : tc::lpg_tc_kernel<false>; }
@@ -834,6 +848,10 @@ static tc::TcArgs make_args(const TcPlan& pl, const TcLaunch& L) {
   a.err = L.err;
   a.spin_limit = L.spin_limit;
   a.inject_timeout = L.inject_timeout;
+  a.nz = pl.nz;
+  a.slots = pl.slots;
+  a.rbufs = pl.rbufs;
+  a.la = pl.la;
   return a;
 }
 
