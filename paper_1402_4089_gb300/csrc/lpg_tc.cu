@@ -44,9 +44,10 @@ namespace hmc {
 namespace tc {
 
 constexpr int kThreadsBf16 = 448;   // warps 0-13
-constexpr int kThreadsFp8 = 576;    // + warps 14-17 (FP8 converters)
+constexpr int kThreadsFp8 = 704;    // + warps 14-21 (FP8 converters)
 constexpr int kSoftThreads = 256;   // warps 6-13
-constexpr int kConvWarps = 4;       // warps 14-17: FP8 -> BF16 converters (idle for BF16 X)
+constexpr int kConvWarps = 8;       // warps 14-21: FP8 -> BF16 converters (FP8 X only)
+constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kFp8BoxBytes = 128 * 64;   // one FP8 box: 128 rows x 64 bytes, row-major
 constexpr int kMaxDepth = kTcMaxDepth;   // largest number of logit accumulators / exchange slots / R buffers
 constexpr int kRows = 128;
@@ -92,8 +93,8 @@ __host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int N
   const int RS = kRows / S;
   size_t off = 0;
   L.ring = off;  off = al(off + size_t(NST) * stage_bytes, 1024);
-  // FP8: each ring slot has a 16 KB landing area for its FP8 box (sweep 1) or box pair (sweep 2).
-  L.stage = off; off = al(off + (fp8 ? size_t(NST) * 2 * kFp8BoxBytes : 0), 1024);
+  // FP8 boxes land in the upper half of their slot's X area and are widened in place.
+  L.stage = off;
   L.rbuf = off;  off = al(off + size_t(rbufs) * (NP / kBox) * kBoxBytes, 1024);
   L.zx = off;    off = al(off + size_t(slots) * kRows * N * 4, 16);
   L.rloc = off;  off = al(off + size_t(RS) * NP * 2, 16);
@@ -116,6 +117,21 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, lon
 
 __device__ __forceinline__ void named_bar_drain() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 __device__ __forceinline__ void named_bar_soft() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+// Barrier of the FP8 converter group (named barrier 3), and the same barrier
+// ANDing a flag across the group (so every converter leaves its loop together).
+__device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 3, %0;" ::"n"(kConvThreads) : "memory"); }
+__device__ __forceinline__ bool conv_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 3, %2, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u), "n"(kConvThreads)
+      : "memory");
+  return r != 0;
+}
 // Named barrier of the softmax group that also ANDs a flag across its threads.
 __device__ __forceinline__ bool named_bar_soft_and(bool v) {
   uint32_t r;
@@ -147,7 +163,6 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
   const int NZ = A.nz, SLOTS = A.slots, RBUFS = A.rbufs, LA = A.la;
   const Smem Lo = smem_layout(NST, A.stage_bytes, NP, N, S, chains, fp8, SLOTS, RBUFS);
   unsigned char* ring = smem + Lo.ring;
-  unsigned char* stage = smem + Lo.stage;
   unsigned char* rbuf = smem + Lo.rbuf;
   float* zx = reinterpret_cast<float*>(smem + Lo.zx);
   __nv_bfloat16* rloc = reinterpret_cast<__nv_bfloat16*>(smem + Lo.rloc);
@@ -254,9 +269,9 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
           const int64_t t = cl + u * nclu;  // row tile
           const uint32_t xbox = fp8 ? uint32_t(kFp8BoxBytes) : uint32_t(kBoxBytes);
           const unsigned char* xt = reinterpret_cast<const unsigned char*>(A.xs) + size_t(t) * nkb_all * xbox;
-          // BF16 X lands in the slot itself; FP8 X lands in the slot's staging area
-          // and the converter warps widen it into the slot.
-          unsigned char* xdst = fp8 ? stage + size_t(st) * 2 * kFp8BoxBytes : sp;
+          // BF16 X lands in the slot itself; FP8 X lands in the upper half of the
+          // slot's X area and the converter warps widen it in place.
+          unsigned char* xdst = fp8 ? sp + size_t(s2 ? 2 : 1) * (kBoxBytes - kFp8BoxBytes) : sp;
           if (!s2) {
             const int kb = int(rank) * NKB + b;
             mbar_arrive_expect_tx(&full[st], xbox + uint32_t(2 * N * 128));
@@ -363,49 +378,59 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
       (void)wait_bounded(drain, 0u, A.spin_limit, abort_flag, false);
     }
   } else if (kFP8 && warp >= 14) {
-    // --------------------------------------- FP8 converters (warps 14-17)
-    // Each FP8 box (128 rows x 64 bytes) of a ring slot's staging area is
-    // widened to BF16 (exact: every E4M3 value is a BF16 value) and written in
-    // the 128-byte-swizzled layout the MMAs read; sweep-2 slots hold two boxes.
+    // --------------------------------------- FP8 converters (warps 14-21)
+    // Each FP8 box (128 rows x 64 bytes, landed in the upper half of its
+    // slot's X area) is widened to BF16 (exact: every E4M3 value is a BF16
+    // value) and written over the slot in the 128-byte-swizzled layout the
+    // MMAs read; sweep-2 slots hold two boxes.  Every converter thread reads
+    // all its input chunks before a converter-group barrier and only then
+    // writes, so the in-place widening never overwrites unread input.
     {
-      const int ct = tid - kThreadsBf16;   // 0..127
+      const int ct = tid - kThreadsBf16;   // 0 .. kConvThreads - 1
       int64_t j = 0;
-      for (int64_t k = 0; k < nphase && !*abort_flag; ++k) {
+      bool ok = true;
+      for (int64_t k = 0; k < nphase && ok; ++k) {
         bool s2;
         (void)phase(k, &s2);
         const int nb = s2 ? A.MB : NKB;
         const int nbox = s2 ? 2 : 1;
-        bool ok = true;
         for (int b = 0; b < nb; ++b, ++j) {
           const int st = int(j % NST);
-          if (!wait_bounded(&full[st], uint32_t((j / NST) & 1), A.spin_limit, abort_flag, false)) {
-            fail(ERR_TIMEOUT_STAGE);
+          const bool got = wait_bounded(&full[st], uint32_t((j / NST) & 1), A.spin_limit, abort_flag, false);
+          // Every converter agrees before the group barriers below.
+          if (!conv_bar_and(got && !*abort_flag)) {
+            if (!got) fail(ERR_TIMEOUT_STAGE);
             ok = false;
             break;
           }
-          const unsigned char* src = stage + size_t(st) * 2 * kFp8BoxBytes;
           unsigned char* dst = ring + size_t(st) * A.stage_bytes;
-          for (int bx = 0; bx < nbox; ++bx) {
+          const unsigned char* src = dst + size_t(nbox) * (kBoxBytes - kFp8BoxBytes);
+          // Input chunk ci (16 bytes) of box bx: row ci / 4, elements 16 (ci % 4) ...
+          constexpr int kPer = (2 * kFp8BoxBytes / 16) / kConvThreads;   // chunks per thread, two boxes
+          uint4 w[kPer];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int ci = ct + 128 * i;       // 16-byte input chunk: row ci / 4, elements 16 (ci % 4) ..
-              const int r = ci >> 2, qq = ci & 3;
-              const uint4 w = *reinterpret_cast<const uint4*>(src + size_t(bx) * kFp8BoxBytes + size_t(ci) * 16);
-              uint32_t o[8];
-              fp8x4_to_bf16x4(w.x, o[0], o[1]);
-              fp8x4_to_bf16x4(w.y, o[2], o[3]);
-              fp8x4_to_bf16x4(w.z, o[4], o[5]);
-              fp8x4_to_bf16x4(w.w, o[6], o[7]);
-              unsigned char* rowp = dst + size_t(bx) * kBoxBytes + size_t(r) * 128;
-              *reinterpret_cast<uint4*>(rowp + ((((2 * qq) ^ (r & 7))) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
-              *reinterpret_cast<uint4*>(rowp + ((((2 * qq + 1) ^ (r & 7))) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
-            }
+          for (int i = 0; i < kPer; ++i)
+            if (i < nbox * kPer / 2) w[i] = *reinterpret_cast<const uint4*>(src + size_t(ct + kConvThreads * i) * 16);
+          conv_bar();
+#pragma unroll
+          for (int i = 0; i < kPer; ++i) {
+            if (i >= nbox * kPer / 2) break;
+            const int g = ct + kConvThreads * i;               // chunk over both boxes
+            const int bx = g / (kFp8BoxBytes / 16), ci = g % (kFp8BoxBytes / 16);
+            const int r = ci >> 2, qq = ci & 3;
+            uint32_t o[8];
+            fp8x4_to_bf16x4(w[i].x, o[0], o[1]);
+            fp8x4_to_bf16x4(w[i].y, o[2], o[3]);
+            fp8x4_to_bf16x4(w[i].z, o[4], o[5]);
+            fp8x4_to_bf16x4(w[i].w, o[6], o[7]);
+            unsigned char* rowp = dst + size_t(bx) * kBoxBytes + size_t(r) * 128;
+            *reinterpret_cast<uint4*>(rowp + ((((2 * qq) ^ (r & 7))) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4*>(rowp + ((((2 * qq + 1) ^ (r & 7))) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
           }
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive_local(&conv[st]);
         }
-        if (!ok) break;
       }
     }
   } else if (warp < 6) {
