@@ -206,9 +206,17 @@ hmc_status check_device_error(hmc_ctx* h) {
 // ------------------------------------------------------------- configuration
 int round_up(int64_t v, int64_t m) { return int((v + m - 1) / m * m); }
 
+// Chains per launch when at most gmax fit one launch: the fewest launches, with
+// the chains spread evenly over them (16 chains at gmax 14 run as 8 + 8, not 14 + 2;
+// every launch streams X once, so a small remainder group costs a full pass).
+int balanced_group(int chains, int gmax) {
+  const int launches = (chains + gmax - 1) / gmax;
+  return (chains + launches - 1) / launches;
+}
+
 // Tensor-core plan: the largest chain group whose coefficient columns fit TMEM
-// next to the cluster's gradient slice, then the cluster size that keeps the
-// most SMs busy.
+// next to the cluster's gradient slice (evened out over the launches it takes),
+// then the cluster size that keeps the most SMs busy.
 hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
   *ok = false;
   int dev = 0, smem_max = 0;
@@ -221,7 +229,9 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
   int best_maxclu = 0;
   for (int S : {16, 8, 4, 2, 1}) {
     if (h->tile[0] && S != h->tile[0]) continue;
+    int g_even = 0;
     for (int g = h->max_chains; g >= 1; --g) {
+      if (g_even && g > g_even) continue;
       TcPlan pl;
       if (!tc_plan(P.p, g * P.Km1, S, &pl)) continue;
       // Exchange depth (partial-logit slots and R buffers) and sweep lookahead:
@@ -258,6 +268,11 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
         maxclu = 0;
       }
       if (maxclu < 1) continue;
+      if (!g_even) {
+        // Largest group that fits: plan again at the even split if it is smaller.
+        g_even = balanced_group(h->max_chains, g);
+        if (g_even < g) continue;
+      }
       const int sms = maxclu * S;
       if (g > best_g || (g == best_g && sms > best_sms)) {
         best_g = g;
@@ -302,7 +317,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     if (P.Km1 > maxct)
       return fail(HMC_EUNSUPPORTED, "K-1 = " + std::to_string(P.Km1) + " exceeds the CUDA-core kernel's class bound " +
                                         std::to_string(maxct));
-    P.group_chains = std::max(1, std::min(h->max_chains, maxct / P.Km1));
+    P.group_chains = balanced_group(h->max_chains, std::max(1, std::min(h->max_chains, maxct / P.Km1)));
     P.ct_launch = P.group_chains * P.Km1;
     if (h->tile[1] || h->tile[2])
       return fail(HMC_EINVAL, "tile[1] and tile[2] must be 0 on the CUDA-core engine (fixed super-tile height)");

@@ -442,14 +442,20 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
     for (int64_t u = 0; u < T && !*abort_flag; ++u) {
       const int slot = int(u % SLOTS);
       const int z = int(u % NZ);
-      if (!wait_bounded(&zdone[z], uint32_t((u / NZ) & 1), A.spin_limit, abort_flag, false)) {
-        fail(ERR_TIMEOUT_MMA);
+      // Lane 0 waits for each barrier and the warp follows it (one waiter per
+      // warp keeps the barrier probes off the shared-memory pipe).
+      bool ok = (lane == 0) ? wait_bounded(&zdone[z], uint32_t((u / NZ) & 1), A.spin_limit, abort_flag, false) : true;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) fail(ERR_TIMEOUT_MMA);
         break;
       }
       fence_after_sync();
       // The owners' slot was last filled with tile u - slots: they must have consumed it.
-      if (u >= SLOTS && !wait_bounded(&zxfree[slot], uint32_t(((u / SLOTS) - 1) & 1), A.spin_limit, abort_flag, true)) {
-        fail(ERR_TIMEOUT_SLOT);
+      ok = (lane == 0 && u >= SLOTS)
+               ? wait_bounded(&zxfree[slot], uint32_t(((u / SLOTS) - 1) & 1), A.spin_limit, abort_flag, true)
+               : true;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) fail(ERR_TIMEOUT_SLOT);
         break;
       }
       // This row's partial logits go to the owner's slot [slot][rank][rl].
@@ -507,40 +513,74 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
         const int64_t grow = row0 + int(rank) * RS + st;
         ylab[st] = grow < A.n ? __ldg(A.y + grow) : -1;
       }
-      const bool zok = wait_bounded(&zrdy[slot], use_par, A.spin_limit, abort_flag, true);
+      // One thread waits for the partials; after the group barrier every thread
+      // takes its own cluster-scope acquire of the completed phase.
+      const bool zok = (st == 0) ? wait_bounded(&zrdy[slot], use_par, A.spin_limit, abort_flag, true) : true;
       if (!named_bar_soft_and(zok)) {
         if (!zok) fail(ERR_TIMEOUT_EXCHANGE);
         break;
       }
+      (void)mbar_test_cluster(smem_u32(&zrdy[slot]), use_par);
       // Softmax with the zero logit of class K, residual and row log-likelihood:
       // one warp per (owned row, chain), lane <-> class; the S partials are
       // summed in rank order.
       const float* zsl = zx + size_t(slot) * S * RS * N;
-      for (int it = sw; it < RS * chains; it += 8) {
-        const int il = it / chains, c = it - il * chains;
-        const int yi = ylab[il];
-        const bool valid = yi >= 0;
-        const int cb = c * Km1;
-        float part[16];
+      const uint32_t zsl_s = smem_u32(zsl);
+      // Four (row, chain) tasks per warp in flight at once, so their load,
+      // shuffle and exp latencies overlap.
+      constexpr int kG = 4;
+      for (int it0 = sw; it0 < RS * chains; it0 += 8 * kG) {
+        float z[kG], mx[kG], se[kG], e[kG], zy[kG];
+        int yi[kG], cb[kG], il[kG];
+        bool act[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          const int it = it0 + 8 * g;
+          act[g] = it < RS * chains;
+          il[g] = act[g] ? it / chains : 0;
+          const int c = act[g] ? it - il[g] * chains : 0;
+          cb[g] = c * Km1;
+          yi[g] = act[g] ? ylab[il[g]] : -1;
+        }
+        // The S partials of each logit, summed in rank order.
+#pragma unroll
+        for (int g = 0; g < kG; ++g) z[g] = 0.f;
 #pragma unroll
         for (int pr = 0; pr < 16; ++pr)
-          part[pr] = (lane < Km1 && pr < S) ? zsl[(size_t(pr) * RS + il) * N + cb + lane] : 0.f;
-        float z = 0.f;
+          if (pr < S)
 #pragma unroll
-        for (int pr = 0; pr < 16; ++pr)
-          if (pr < S) z += part[pr];
-        float mx = (lane < Km1) ? fmaxf(z, 0.f) : 0.f;
+            for (int g = 0; g < kG; ++g)
+              if (act[g] && lane < Km1) {
+                float t;
+                asm volatile("ld.shared.f32 %0, [%1];" : "=f"(t) : "r"(zsl_s + uint32_t(((pr * RS + il[g]) * N + cb[g] + lane) * 4)));
+                z[g] += t;
+              }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const float e = (lane < Km1) ? expf(z - mx) : 0.f;
-        float se = e;
+        for (int g = 0; g < kG; ++g) mx[g] = (lane < Km1) ? fmaxf(z[g], 0.f) : 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
-        se += expf(-mx);
-        const float zy = __shfl_sync(0xffffffffu, z, (valid && yi < Km1) ? yi : 0);
-        if (lane < Km1)
-          rloc[il * NP + cb + lane] = __float2bfloat16_rn(valid ? ((lane == yi ? 1.f : 0.f) - e / se) : 0.f);
-        if (lane == 0 && valid) lacc[il * chains + c] += double((yi < Km1 ? zy : 0.f) - mx - logf(se));
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int g = 0; g < kG; ++g) mx[g] = fmaxf(mx[g], __shfl_xor_sync(0xffffffffu, mx[g], o));
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          e[g] = (lane < Km1) ? expf(z[g] - mx[g]) : 0.f;
+          se[g] = e[g];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int g = 0; g < kG; ++g) se[g] += __shfl_xor_sync(0xffffffffu, se[g], o);
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          se[g] += expf(-mx[g]);
+          const bool valid = yi[g] >= 0;
+          zy[g] = __shfl_sync(0xffffffffu, z[g], (valid && yi[g] < Km1) ? yi[g] : 0);
+          if (act[g] && lane < Km1)
+            rloc[il[g] * NP + cb[g] + lane] =
+                __float2bfloat16_rn(valid ? ((lane == yi[g] ? 1.f : 0.f) - e[g] / se[g]) : 0.f);
+          if (act[g] && lane == 0 && valid)
+            lacc[il[g] * chains + (cb[g] / Km1)] += double((yi[g] < Km1 ? zy[g] : 0.f) - mx[g] - logf(se[g]));
+        }
       }
       // The partials of tile u are consumed: peers may push tile u + 1.
       named_bar_soft();
@@ -561,7 +601,10 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
         const int peer = it % S, rest = it / S;
         const int c8 = rest % C8, il = rest / C8;
         const int r = int(rank) * RS + il;
-        const uint4 v = *reinterpret_cast<const uint4*>(rloc + il * NP + c8 * 8);
+        uint4 v;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "r"(smem_u32(rloc + il * NP + c8 * 8)));
         const uint32_t off = uint32_t((c8 >> 3) * kBoxBytes + r * 128 + (((c8 & 7) ^ (r & 7)) << 4));
         const uint32_t la = rb_local + uint32_t(rbi * rbuf_bytes) + off;
         const uint32_t ra = (S > 1) ? map_peer(la, uint32_t(peer)) : la;
