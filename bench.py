@@ -178,15 +178,15 @@ def kernel_source_hash(engine):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, engine):
-    """DRAM bytes per fused launch from a committed ncu summary, if it was taken on the
-    current kernel source."""
+def recorded_traffic(workload, xdt, engine):
+    """DRAM bytes per fused launch from a committed ncu summary of this workload and X
+    storage, if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get(workload)
+    e = d.get(f"{workload}:{xdt}")
     if not e or e.get("engine") != engine or e.get("source_sha") != kernel_source_hash(engine):
         return None
     return e.get("bytes_per_launch")
@@ -328,7 +328,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, desc_all["engine"]),
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, xdt, desc_all["engine"]),
             "kernel": ("lpg_tc_kernel (tcgen05)" if h.describe()["engine"] == "tcgen05" else "lpg_kernel (CUDA cores)")
             + f" X={xdt} C={c_launch}", "avg_launch_us": round(avg_launch_s * 1e6, 2),
             "launches_timed": fused_n, "timed_launches_from": "every 10th fused launch of the last HMC iteration "
@@ -480,7 +480,7 @@ def run_batch_uneven(args):
                    "total_x_bytes": sum(n * p * xb for (n, p, K) in shapes),
                    "l2": "inputs larger than L2: X of all problems re-streamed every gradient"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": recorded_traffic("batched_uneven", xdt, "tcgen05"),
                      "kernel": ("lpg_tc_kernel_batched (tcgen05)" if desc.get("engine") == "tcgen05" else
                                 "lpg_kernel_batched (CUDA cores)") + ", all problems per launch",
                      "avg_launch_us": round(per_launch * 1e6, 2), "launches_timed": fused_n,
