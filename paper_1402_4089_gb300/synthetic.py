@@ -128,6 +128,13 @@ def batched_shapes(count=32, seed=0):
     return [(int(a), int(b), int(c)) for a, b, c in zip(n, p, K)]
 
 
+def sweep_problem(n, p, K, seed=0):
+    """One problem of the timing sweep of Sec. 3.1: X and B iid N(0, 1e-3), the
+    1e-3 read as the variance; y drawn from the softmax model."""
+    sd = float(np.sqrt(1e-3))
+    return make_problem(n, p, K, seed=seed, x_sd=sd, beta_scale=sd)
+
+
 def sweep_shapes():
     """(n, p, K) of the timing sweep of Sec. 3.1 (Table 1); the repeated N value
     printed there is read as 10000 (4 x 7 x 8 = 224 combinations)."""
