@@ -204,8 +204,6 @@ hmc_status check_device_error(hmc_ctx* h) {
 }
 
 // ------------------------------------------------------------- configuration
-int round_up(int64_t v, int64_t m) { return int((v + m - 1) / m * m); }
-
 // Chains per launch when at most gmax fit one launch: the fewest launches, with
 // the chains spread evenly over them (16 chains at gmax 14 run as 8 + 8, not 14 + 2;
 // every launch streams X once, so a small remainder group costs a full pass).

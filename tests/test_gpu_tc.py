@@ -114,3 +114,28 @@ def test_tc_batch_of_uneven_problems_one_launch(cuda, storage):
             g_o = model.grad_log_kernel(Xq, y, betas[b][c], "gaussian", 10.0)
             assert abs(lp[b * chains + c] - lk_o) / max(1.0, abs(lk_o)) <= TOL_L, (b, c)
             assert _rel(gb[c], g_o) <= TOL_G, (b, c, _rel(gb[c], g_o))
+
+
+def test_tc_chain_groups_are_even(cuda):
+    """16 chains where one launch holds at most 14 (p = 5000, K = 10): two launches
+    of 8 chains each (a 14 + 2 split would stream X a second time for 2 chains)."""
+    import torch
+    n, p, K, chains = 1500, 5000, 10, 16
+    X, y, _ = synthetic.make_problem(n, p, K, seed=41)
+    rng = np.random.default_rng(42)
+    beta = (0.05 * rng.standard_normal((chains, K - 1, p))).astype(np.float32)
+    with hmc.create(X, y, K, "gaussian", 10.0, x_storage="bf16", max_chains=chains, engine=2) as h:
+        d = h.describe()["problems"][0]
+        assert d["group_chains"] == 8, d
+        bits, _ = h.get_x()
+        h.set_timing(True)
+        lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
+        torch.cuda.synchronize()
+        _, launches = h.fused_kernel_time()
+        assert launches == 2
+        lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    Xq = quant.bf16_decode(bits).astype(np.float64)
+    for c in (0, 7, 8, 15):
+        lk_o = model.log_kernel(Xq, y, beta[c], "gaussian", 10.0)
+        g_o = model.grad_log_kernel(Xq, y, beta[c], "gaussian", 10.0)
+        assert abs(lp[c] - lk_o) / max(1.0, abs(lk_o)) <= TOL_L and _rel(g[c], g_o) <= TOL_G, c
