@@ -100,7 +100,7 @@ __host__ __device__ inline Smem smem_layout(int NST, uint32_t stage_bytes, int N
   L.rloc = off;  off = al(off + size_t(RS) * NP * 2, 16);
   L.lacc = off;  off = al(off + size_t(RS) * chains * 8, 16);
   L.ylab = off;  off = al(off + size_t(RS) * 4, 16);
-  L.bars = off;  off = al(off + size_t(3 * NST + 7 * kMaxDepth + 6) * 8 + 16, 16);
+  L.bars = off;  off = al(off + size_t(3 * NST + 6 * kMaxDepth + 6) * 8 + 16, 16);
   L.total = off + 1024;  // slack for aligning the dynamic base to 1024
   return L;
 }
@@ -177,8 +177,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
   uint64_t* zrdy = zfree + kMaxDepth;       // [slots] partial logits of the owned rows received
   uint64_t* zxfree = zrdy + kMaxDepth;      // [slots] every owner has consumed the slot's partials
   uint64_t* rfull = zxfree + kMaxDepth;     // [rbufs] every owner's R rows received (R buffer b)
-  uint64_t* rfree = rfull + kMaxDepth;      // [rbufs] this CTA's gradient sweep finished reading R buffer b
-  uint64_t* rfreec = rfree + kMaxDepth;     // [rbufs] every CTA's gradient sweep finished reading R buffer b
+  uint64_t* rfreec = rfull + kMaxDepth;     // [rbufs] every CTA's gradient sweep finished reading R buffer b
   uint64_t* gdone = rfreec + kMaxDepth;
   uint64_t* drain = gdone + 1;
   uint64_t* never = gdone + 2;
@@ -198,7 +197,6 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
       mbar_init(&zrdy[b], 1);
       mbar_init(&zxfree[b], S);
       mbar_init(&rfull[b], 1);
-      mbar_init(&rfree[b], 1);
       mbar_init(&rfreec[b], S);
     }
     mbar_init(gdone, 1);
@@ -289,19 +287,6 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
       // Every copy issued must land before shared memory is released.
       for (int64_t jj = (issued > NST ? issued - NST : 0); jj < issued; ++jj)
         (void)wait_bounded(&full[jj % NST], uint32_t((jj / NST) & 1), A.spin_limit, abort_flag, false);
-    } else if (lane == 1) {
-      // As soon as this CTA's gradient sweep of tile u has finished reading R
-      // buffer u % rbufs, tell every CTA that may push the R rows of tile u + rbufs.
-      for (int64_t u = 0; u + RBUFS < T && !*abort_flag; ++u) {
-        const int b = int(u % RBUFS);
-        if (!wait_bounded(&rfree[b], uint32_t((u / RBUFS) & 1), A.spin_limit, abort_flag, false)) {
-          fail(ERR_TIMEOUT_MMA);
-          break;
-        }
-        fence_after_sync();
-        for (int r = 0; r < S; ++r)
-          mbar_arrive_remote(S > 1 ? map_peer(smem_u32(&rfreec[b]), uint32_t(r)) : smem_u32(&rfreec[b]));
-      }
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
@@ -370,7 +355,17 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
             mma_commit(&empty[st]);
           }
           if (*abort_flag) break;
-          mma_commit(&rfree[rbi]);
+          // R buffer rbi is free once these MMAs complete: the commit arrives on
+          // that buffer's barrier in every CTA of the cluster, so each owner may
+          // push the R rows of tile u + rbufs.  Only tiles whose buffer is used
+          // again signal, so every remote arrival has a waiter in its CTA (and
+          // lands before that CTA can leave the kernel).
+          if (u + RBUFS < T) {
+            if (S > 1)
+              mma_commit_multicast(&rfreec[rbi], uint16_t((1u << S) - 1u));
+            else
+              mma_commit(&rfreec[rbi]);
+          }
         }
       }
       mma_commit(gdone);
