@@ -170,11 +170,41 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash(engine):
+def code_only(text):
+    """C++/CUDA source without comments and blank lines (string literals kept), so a
+    comment edit does not count as a kernel change."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
+
+
+def kernel_source_hash(engine, read=None):
+    """Hash of the code (comments stripped) of an engine's kernel sources; `read`
+    maps a repository path to its text (default: the working tree)."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES[engine]:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        if read is None:
+            with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+                text = f.read()
+        else:
+            text = read(rel)
+        h.update(code_only(text).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,5 +1,6 @@
 // Fused log-posterior + gradient pass on the 5th-generation tensor cores
-// (tcgen05) for X stored in BF16, many chains at once (Eqs. softmax, loglike,
+// (tcgen05) for X stored in BF16 or per-column-scaled FP8 (widened to BF16 in
+// shared memory), many chains at once (Eqs. softmax, loglike,
 // logkernel and gradient of Sec. 2.1, evaluated for C = chains*(K-1)
 // coefficient columns).
 //
@@ -27,12 +28,16 @@
 //   sweep 2  X is re-read in 128-column blocks (an L2 hit: the tile was
 //            streamed one sweep earlier); MMA D_g[mb] (128 columns x N) +=
 //            X_blk^T . R with X_blk read MN-major from the same swizzled boxes
-//            and R MN-major from the operand buffer.
+//            and R MN-major from the operand buffer.  The commit of these MMAs
+//            is multicast to every CTA of the cluster, telling the owners
+//            that the R buffer may take the rows of a later tile.
 // Sweeps are interleaved S1(0), S1(1), S2(0), S1(2), S2(1), ... so the
 // exchange of one tile overlaps the next tile's first sweep.
-// Warp roles: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-5
-// drain group (TMEM lanes 0-127; the gradient slice at the end), warps 6-13
-// softmax group.  All waits are bounded.
+// Warp roles: warp 0 TMA producer (lane 0 alone: no other role shares its
+// warp, so nothing suspends the copy issue), warp 1 TMEM owner + MMA issuer,
+// warps 2-5 drain group (TMEM lanes 0-127; the gradient slice at the end),
+// warps 6-13 softmax group, warps 14-21 FP8 converters (FP8 X only).  All
+// waits are bounded.
 #include <algorithm>
 #include <vector>
 #include <cstring>

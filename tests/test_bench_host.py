@@ -1,0 +1,50 @@
+"""Host-side logic of bench.py that needs no GPU."""
+import importlib.util
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        spec.loader.exec_module(m)
+    finally:
+        sys.argv = argv
+    return m
+
+
+def test_code_only_ignores_comments_not_code():
+    b = _bench()
+    src = 'int a = 1;  // one\n/* block\n comment */\nconst char* s = "// not a comment";\n\nint b = a;\n'
+    out = b.code_only(src)
+    assert "one" not in out and "block" not in out
+    assert '"// not a comment"' in out and "int b = a;" in out
+    assert b.code_only(src.replace("// one", "// uno")) == out
+    assert b.code_only(src.replace("a = 1", "a = 2")) != out
+
+
+def test_recorded_traffic_follows_the_kernel_code(tmp_path, monkeypatch):
+    import json
+    import shutil
+    b = _bench()
+    for rel in b.KERNEL_SOURCES["simt"]:
+        os.makedirs(tmp_path / os.path.dirname(rel), exist_ok=True)
+        shutil.copy(os.path.join(ROOT, rel), tmp_path / rel)
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    os.makedirs(tmp_path / "profiles")
+    entry = {"engine": "simt", "source_sha": b.kernel_source_hash("simt"), "bytes_per_launch": 123}
+    with open(tmp_path / "profiles" / "traffic.json", "w") as f:
+        json.dump({"highdim_fp32:f32": entry}, f)
+    assert b.recorded_traffic("highdim_fp32", "f32", "simt") == 123
+    assert b.recorded_traffic("highdim_fp32", "bf16", "simt") is None      # other X storage
+    assert b.recorded_traffic("highdim_fp32", "f32", "tcgen05") is None    # other engine
+    k = tmp_path / b.KERNEL_SOURCES["simt"][0]
+    k.write_text(k.read_text() + "\n// a comment\n")
+    assert b.recorded_traffic("highdim_fp32", "f32", "simt") == 123        # comments do not count
+    k.write_text(k.read_text() + "\nstatic int changed_code = 1;\n")
+    assert b.recorded_traffic("highdim_fp32", "f32", "simt") is None       # code changed since capture
