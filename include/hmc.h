@@ -50,7 +50,7 @@ typedef enum {
   HMC_ECUDA = 3,         /* a CUDA runtime call failed; see hmc_last_error()   */
   HMC_ETIMEOUT = 4,      /* a bounded device wait ran out                      */
   HMC_ENONFINITE = 5,    /* non-finite value in X or a label outside [0, K)    */
-  HMC_EUNSUPPORTED = 6   /* valid request this build or device cannot run      */
+  HMC_EUNSUPPORTED = 6   /* valid request the library or device cannot run    */
 } hmc_status;
 
 /* Prior on each free coefficient.  Sec. 2.1 uses the standard Cauchy
