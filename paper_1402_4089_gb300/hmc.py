@@ -309,6 +309,19 @@ def create_batch(Xs, ys, Ks, prior="gaussian", prior_scale=1.0, x_storage="f32",
     return hd
 
 
+def annealing_temperatures(iters, t0=1.0e3, r=0.9):
+    """Acceptance temperatures of the annealed burn-in of Sec. 3.2 for `iters`
+    iterations: T_t = max(1, r T_{t-1}) with T_0 = t0, iteration t (1-based)
+    accepting at T_t; once T reaches 1 it stays there.  Pass the result as
+    ``temps`` to ``Handle.sample``."""
+    out = np.empty(int(iters), dtype=np.float64)
+    t = float(t0)
+    for i in range(out.size):
+        t = max(1.0, r * t)
+        out[i] = t
+    return out
+
+
 def header_functions(path=None):
     """Names of the functions declared in include/hmc.h."""
     import re

@@ -36,6 +36,11 @@ WORKLOADS = {
                       prior=("gaussian", 10.0), xdtype="bf16"),
     "batched": dict(n=20000, p=2000, K=10, chains=64, L=50, eps=1e-3, iters=200,
                     prior=("gaussian", 10.0), xdtype="bf16"),
+    # Sec. 3.2's run shape: 60000 x 785 (784 pixel columns + intercept), K = 10,
+    # L = 100, annealed burn-in of 100 iterations (T0 = 1e3, r = 0.9) at eps = 1e-4,
+    # then 100 sampling iterations at eps = 7e-5, Cauchy(0, 1) prior.
+    "mnist_shaped": dict(n=60000, p=785, K=10, chains=1, L=100, eps=1e-4, eps_sample=7e-5, iters=200,
+                         burn_in=100, t0=1.0e3, r=0.9, prior=("cauchy", 1.0), xdtype="f32"),
     "autodiff": dict(n=100000, p=20000, K=10, chains=8, L=100, eps=1e-3, iters=500,
                      prior=("gaussian", 10.0), xdtype="bf16"),
 }
@@ -62,6 +67,19 @@ def draw_X(n, p, seed=0, dtype=np.float32, correlated=False, sd=1.0, sub=0):
     if sd != 1.0:
         X *= X.dtype.type(sd)
     return X.astype(dtype, copy=False)
+
+
+def draw_pixels(n, seed=0, npix=784, density=0.19, sub=0):
+    """n x (1 + npix) FP32: an intercept column of ones, then pixel-like columns
+    that are 0 except, with probability ``density``, a grey level k / 255 with k
+    uniform on 1..255 (a synthetic stand-in with the shape and value range of
+    the handwritten-digit design of Sec. 3.2; no image data is involved)."""
+    g = _gen(seed, _TAG_X, sub)
+    X = np.zeros((n, 1 + npix), dtype=np.float32)
+    X[:, 0] = 1.0
+    on = g.random((n, npix)) < density
+    X[:, 1:] = np.where(on, g.integers(1, 256, size=(n, npix)).astype(np.float32) / np.float32(255.0), 0.0)
+    return X
 
 
 def draw_beta(p, K, seed=0, sparse=0.0, scale=1.0, sub=0):
@@ -113,6 +131,10 @@ def make_workload(name, seed=0, n=None, p=None):
         X, y, b = make_problem(nn, pp, K, seed=seed, dtype=np.float64)
     elif name == "highdim_fp32":
         X, y, b = make_problem(nn, pp, K, seed=seed, correlated=True, sparse=0.05, beta_scale=2.0)
+    elif name == "mnist_shaped":
+        X = draw_pixels(nn, seed=seed, npix=pp - 1)
+        b = draw_beta(pp, K, seed=seed, scale=0.3)
+        y = draw_labels(X, b, seed=seed)
     else:
         X, y, b = make_problem(nn, pp, K, seed=seed)
     return X, y, b, spec

@@ -35,3 +35,24 @@ def test_sweep_values_have_the_printed_variance():
     assert abs(X.var() / var - 1.0) < 0.05
     nz = B[B != 0]
     assert abs(nz.var() / var - 1.0) < 0.2
+
+
+def test_mnist_shaped_recipe():
+    X, y, B, spec = synthetic.make_workload("mnist_shaped", n=3000)
+    assert X.shape == (3000, 785) and X.dtype == np.float32 and spec["K"] == 10
+    assert np.all(X[:, 0] == 1.0)
+    px = X[:, 1:]
+    k = np.rint(px * 255.0)
+    assert np.all((k >= 0) & (k <= 255)) and np.allclose(px, (k / 255.0).astype(np.float32), rtol=0, atol=0)
+    assert abs((px > 0).mean() - 0.19) < 0.01
+    assert y.min() >= 0 and y.max() < 10 and len(np.unique(y)) == 10
+    assert spec["prior"] == ("cauchy", 1.0) and spec["burn_in"] == 100 and spec["L"] == 100
+
+
+def test_annealing_schedule_matches_oracle():
+    from oracle import hmc as ohmc
+    from paper_1402_4089_gb300 import hmc
+    for t0, r, n in ((1.0e3, 0.9, 100), (50.0, 0.7, 20), (1.0, 0.5, 5)):
+        assert np.array_equal(hmc.annealing_temperatures(n, t0, r), ohmc.annealing_temperatures(n, t0, r))
+    t = hmc.annealing_temperatures(100)
+    assert t[0] == 900.0 and t[-1] == 1.0 and np.all(np.diff(t) <= 0)
