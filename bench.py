@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true", help="use the library's tile choice instead of measuring")
     ap.add_argument("--ess-iters", type=int, default=200, help="HMC iterations of the ESS/s run (0: skip)")
+    ap.add_argument("--sweep-limit", type=int, default=0, help="sweep workload: first k shapes only (0: all 224)")
+    ap.add_argument("--sweep-oracle-np", type=float, default=2e7,
+                    help="sweep workload: time the oracle only where N p is at most this")
     return ap.parse_args()
 
 
@@ -552,6 +555,95 @@ def run_batch_uneven(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------- Table 1 timing sweep
+def run_sweep(args):
+    """The timing sweep of Sec. 3.1 (Table 1): for each of the 224 (N, K, p)
+    shapes, X and B iid N(0, 1e-3), one gradient evaluation and one leapfrog step
+    (which includes its gradient: the update is fused into the gradient's
+    reduction), each the mean of 5 runs timed with CUDA events; next to it the
+    FP64 oracle's gradient on the host for shapes with N p <= --sweep-oracle-np
+    (one run after a warm one).  Runs on one GPU (rank 0; other ranks wait)."""
+    import torch
+    from paper_1402_4089_gb300 import build, hmc, synthetic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    build.build()
+    from oracle import model
+    shapes = synthetic.sweep_shapes()
+    if args.sweep_limit:
+        shapes = shapes[:args.sweep_limit]
+    stream = torch.cuda.Stream(device=dev)
+    rows, grad_rates = [], []
+    t_start = time.perf_counter()
+    for (n, p, K) in shapes:
+        X, y, B = synthetic.sweep_problem(n, p, K)
+        try:
+            h = hmc.create(X, y, K, "cauchy", 1.0, x_storage="f32", max_chains=1, stream=stream)
+        except hmc.HmcError as e:
+            # FP32 X on CUDA cores keeps at most 128 x (10, or 5 for more than 12
+            # classes) gradient columns per CTA and 16 CTAs per cluster
+            rows.append([n, K, p, None, None, None, None, str(e)[:120]])
+            continue
+        with torch.cuda.stream(stream):
+            beta = torch.from_numpy(B.astype(np.float32)[None]).to(dev)
+            lp, g = h.logpost_grad(beta)
+            h.logpost_grad(beta, logpost=lp, grad=g)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                h.logpost_grad(beta, logpost=lp, grad=g)
+            e1.record(stream)
+            b2 = beta.clone()
+            eta = torch.zeros_like(b2)
+            h.leapfrog(b2, eta, 1, 1e-3, grad=g, logpost=lp)
+            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+            for _ in range(5):
+                h.leapfrog(b2, eta, 1, 1e-3, grad=g, logpost=lp)
+            e3.record(stream)
+            stream.synchronize()
+        g_us = e0.elapsed_time(e1) * 1e3 / 5
+        lf_us = e2.elapsed_time(e3) * 1e3 / 5
+        h.close()
+        cpu_us = None
+        if n * p <= args.sweep_oracle_np:
+            X64 = X.astype(np.float64)
+            model.grad_log_kernel(X64, y, B, "cauchy", 1.0)
+            t0 = time.perf_counter()
+            model.grad_log_kernel(X64, y, B, "cauchy", 1.0)
+            cpu_us = (time.perf_counter() - t0) * 1e6
+        rows.append([n, K, p, round(g_us, 2), round(lf_us, 2), None if cpu_us is None else round(cpu_us, 1),
+                     None if cpu_us is None else round(cpu_us / g_us, 2), None])
+        grad_rates.append(1e6 / g_us)
+    wall = time.perf_counter() - t_start
+    sp = [r[6] for r in rows if r[6] is not None]
+    big = [r for r in rows if r[0] * r[2] >= 5000 * 5000 and r[3] is not None]
+    line = {
+        "metric": METRIC, "value": round(float(np.median(grad_rates)), 2), "unit": UNIT, "n_gpus": 1,
+        "steps": 5, "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; X and B iid N(0, 1e-3), labels from the model)",
+        "config": {"workload": f"sweep: Table 1 grid, {len(rows)} (N, K, p) shapes, 1 chain, Cauchy(0,1) prior, X=f32",
+                   "value": "median over shapes of GPU gradient evaluations per second",
+                   "oracle_np_cap": args.sweep_oracle_np},
+        "impl": "ours", "gpu_launches": None, "cpu_baseline": None, "e2e": None, "roofline": None,
+        "sweep": {"columns": ["N", "K", "p", "gpu_grad_us", "gpu_leapfrog_step_us", "oracle_grad_us",
+                              "speedup_grad", "unsupported"],
+                  "rows": rows, "wall_s": round(wall, 1),
+                  "unsupported_shapes": sum(1 for r in rows if r[3] is None),
+                  "speedup_median": round(float(np.median(sp)), 1) if sp else None,
+                  "speedup_max": round(float(np.max(sp)), 1) if sp else None,
+                  "gpu_grad_us_median_large": round(float(np.median([r[3] for r in big])), 2) if big else None,
+                  "note": "oracle: plain numpy FP64 (BLAS matmuls) on the host cores, one gradient after a warm one; "
+                          "GPU: mean of 5 calls through the C ABI (fused pass + fixed-order reduction)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------- reference arm
 def run_reference(args):
     """The FP64 oracle, timed as it stands on the host cores (rank 0 only)."""
@@ -603,6 +695,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched_uneven":
         run_batch_uneven(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 
