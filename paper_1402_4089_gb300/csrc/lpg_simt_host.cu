@@ -160,8 +160,14 @@ cudaError_t simt_choose(int xt, int C, int64_t p, int64_t ntiles, int force_S, i
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   int64_t best_active = -1;
+  // Without a forced size, a cluster is no wider than gives each CTA ~256 real
+  // columns: below that the extra CTAs hold mostly padding and every tile pays
+  // a wider logit exchange (p = 50: 10.3 us per pass at S = 1 against 15.0 us at
+  // the S = 12 the occupancy model alone would pick; p = 100: 11.2 against 15.0).
+  const int64_t s_cap = (force_S || exact_ld > 0) ? 16 : std::max<int64_t>(1, (p + 255) / 256);
   for (int S : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16}) {
     if (force_S && S != force_S) continue;
+    if (S > s_cap) continue;
     int64_t PC;
     if (exact_ld > 0) {
       if (exact_ld % (16 * S)) continue;
