@@ -335,7 +335,14 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     P.smem = tc.smem;
     P.p_pad = P.S * P.PC;
     const int maxclu = tc.maxclu;
-    P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>(maxclu, P.ntiles)));
+    // Every cluster adds one partial slice to the fixed-order reduction, so
+    // clusters beyond one per S SMs are launched only while each still gets
+    // about four tiles.
+    int dev = 0, nsm = 0;
+    HMC_CUDA(cudaGetDevice(&dev));
+    HMC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t useful = std::max<int64_t>(nsm / P.S, (P.ntiles + 3) / 4);
+    P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>({int64_t(maxclu), P.ntiles, useful})));
   }
 
   // X: convert on the device into the storage type, zero-padded columns.
