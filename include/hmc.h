@@ -76,7 +76,11 @@ typedef struct {
   int32_t tile[4];        /* {cluster size 1..16, exchange depth, sweep lookahead, ring slots}; 0 =
                              chosen.  Depth (partial-logit slots and R buffers, 1..4) and lookahead
                              (tiles between the two sweeps, 1..4) apply to the tensor-core engine and
-                             must be 0 on the CUDA-core engine */
+                             must be 0 on the CUDA-core engine.  The chosen CUDA-core tile keeps the
+                             most SMs streaming X with clusters of at most ceil(p / 256) CTAs, and
+                             launches no more than one cluster per S SMs unless each still gets
+                             about four 16-row tiles; the chosen tensor-core tile takes the most
+                             chains TMEM holds, spread evenly over the launches a call needs */
 } hmc_opts;
 
 /* Per-chain counters of hmc_sample (host memory, one entry per chain). */
