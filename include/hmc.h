@@ -197,6 +197,23 @@ hmc_status hmc_get_state(hmc_handle h, int32_t chains, void* beta, void* grad, d
                          int64_t* next_iteration);
 
 /*
+ * hmc_state_save / hmc_state_load -- checkpoint and resume of the chain state
+ * that hmc_sample continues from: beta, grad and log K of the handle's chains
+ * (every problem) and the next global iteration index, which numbers the
+ * counter-based momentum and accept draws (Sec. 1.1 proposals).  The file at
+ * `path` (host path, overwritten by save) records the state type and every
+ * problem's (n, p, K); load requires a handle with the same problems, state
+ * type and max_chains >= the saved chain count, and replaces its chain state,
+ * so hmc_sample with beta0 = NULL, the saved chain count and the same seed then
+ * continues the saved chains exactly (bitwise, on the same device and tile
+ * configuration; another chain count starts over from zero).  Save
+ * needs a chain state (HMC_EINVAL before the first hmc_sample); a missing,
+ * truncated or mismatched file is HMC_EINVAL.  Synchronous.
+ */
+hmc_status hmc_state_save(hmc_handle h, const char* path);
+hmc_status hmc_state_load(hmc_handle h, const char* path);
+
+/*
  * hmc_get_x -- copy the device-resident X of problem b as stored (after
  * conversion): row-major n x p elements of opts.x_storage (8, 4, 2 or 1
  * bytes each), unpadded, into host or device memory `dst`; for HMC_FP8E4M3

@@ -1300,6 +1300,117 @@ hmc_status hmc_get_state(hmc_handle h, int32_t chains, void* beta, void* grad, d
   return HMC_OK;
 }
 
+// ------------------------------------------------------------- checkpoints
+// File layout (host byte order): the 8 bytes "HMCCKPT1"; int32 state type,
+// number of problems, chains, 0; per problem int64 n, int32 p, int32 K, int64
+// next global iteration; then beta and grad of every chain in the beta layout
+// of hmc_logpost_grad (state type), and log K as double[nprob * chains].
+namespace {
+constexpr char kCkptMagic[8] = {'H', 'M', 'C', 'C', 'K', 'P', 'T', '1'};
+struct FileCloser {
+  FILE* f = nullptr;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+}  // namespace
+
+hmc_status hmc_state_save(hmc_handle h, const char* path) {
+  g_last_error.clear();
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  if (!path) return fail(HMC_EINVAL, "path is NULL");
+  const int chains = h->chains_init;
+  if (chains < 1) return fail(HMC_EINVAL, "no chain state to save: run hmc_sample first");
+  const int nprob = int(h->probs.size());
+  const size_t bytes = size_t(chains) * h->chain_size * state_bytes(h);
+  std::vector<char> hb(bytes), hg(bytes);
+  std::vector<double> hl(size_t(nprob) * chains);
+  std::vector<int64_t> it(nprob);
+  void* d = nullptr;
+  HMC_TRY(grow_staging(h, 0, bytes, &d));
+  HMC_TRY(unpack_all(h, d, chains, true, &StateSet::beta));
+  HMC_CUDA(cudaMemcpyAsync(hb.data(), d, bytes, cudaMemcpyDeviceToHost, h->stream));
+  HMC_CUDA(cudaStreamSynchronize(h->stream));   // the staging buffer takes grad next
+  HMC_TRY(unpack_all(h, d, chains, true, &StateSet::grad));
+  HMC_CUDA(cudaMemcpyAsync(hg.data(), d, bytes, cudaMemcpyDeviceToHost, h->stream));
+  for (int b = 0; b < nprob; ++b) {
+    HMC_CUDA(cudaMemcpyAsync(hl.data() + size_t(b) * chains, h->probs[b].logk, size_t(chains) * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+    HMC_CUDA(cudaMemcpyAsync(&it[b], h->probs[b].iter, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  }
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  FileCloser fc;
+  fc.f = std::fopen(path, "wb");
+  if (!fc.f) return fail(HMC_EINVAL, std::string("cannot open ") + path + " for writing");
+  const int32_t hdr[4] = {int32_t(h->st), int32_t(nprob), int32_t(chains), 0};
+  bool ok = std::fwrite(kCkptMagic, 1, 8, fc.f) == 8 && std::fwrite(hdr, sizeof(int32_t), 4, fc.f) == 4;
+  for (int b = 0; b < nprob && ok; ++b) {
+    const Problem& P = h->probs[b];
+    const int64_t n = P.n;
+    const int32_t pk[2] = {P.p, P.K};
+    ok = std::fwrite(&n, sizeof(int64_t), 1, fc.f) == 1 && std::fwrite(pk, sizeof(int32_t), 2, fc.f) == 2 &&
+         std::fwrite(&it[b], sizeof(int64_t), 1, fc.f) == 1;
+  }
+  ok = ok && std::fwrite(hb.data(), 1, bytes, fc.f) == bytes && std::fwrite(hg.data(), 1, bytes, fc.f) == bytes &&
+       std::fwrite(hl.data(), sizeof(double), hl.size(), fc.f) == hl.size();
+  const int closed = std::fclose(fc.f);
+  fc.f = nullptr;
+  if (!ok || closed != 0) return fail(HMC_EINVAL, std::string("writing ") + path + " failed");
+  return HMC_OK;
+}
+
+hmc_status hmc_state_load(hmc_handle h, const char* path) {
+  g_last_error.clear();
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  if (!path) return fail(HMC_EINVAL, "path is NULL");
+  FileCloser fc;
+  fc.f = std::fopen(path, "rb");
+  if (!fc.f) return fail(HMC_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t hdr[4];
+  if (std::fread(magic, 1, 8, fc.f) != 8 || std::memcmp(magic, kCkptMagic, 8) != 0 ||
+      std::fread(hdr, sizeof(int32_t), 4, fc.f) != 4)
+    return fail(HMC_EINVAL, std::string(path) + " is not a chain-state checkpoint");
+  const int nprob = int(h->probs.size());
+  if (hdr[0] != h->st) return fail(HMC_EINVAL, "the checkpoint's state type differs from the handle's");
+  if (hdr[1] != nprob) return fail(HMC_EINVAL, "the checkpoint holds a different number of problems");
+  const int chains = hdr[2];
+  if (chains < 1 || chains > h->max_chains)
+    return fail(HMC_EINVAL, "the checkpoint's chain count is outside [1, max_chains]");
+  std::vector<int64_t> it(nprob);
+  for (int b = 0; b < nprob; ++b) {
+    int64_t n = 0;
+    int32_t pk[2] = {0, 0};
+    if (std::fread(&n, sizeof(int64_t), 1, fc.f) != 1 || std::fread(pk, sizeof(int32_t), 2, fc.f) != 2 ||
+        std::fread(&it[b], sizeof(int64_t), 1, fc.f) != 1)
+      return fail(HMC_EINVAL, std::string(path) + " is truncated");
+    const Problem& P = h->probs[b];
+    if (n != P.n || pk[0] != P.p || pk[1] != P.K)
+      return fail(HMC_EINVAL, "problem " + std::to_string(b) + " of the checkpoint has another shape (n, p, K)");
+    if (it[b] < 0) return fail(HMC_EINVAL, "negative iteration index in the checkpoint");
+  }
+  const size_t bytes = size_t(chains) * h->chain_size * state_bytes(h);
+  std::vector<char> hb(bytes), hg(bytes);
+  std::vector<double> hl(size_t(nprob) * chains);
+  if (std::fread(hb.data(), 1, bytes, fc.f) != bytes || std::fread(hg.data(), 1, bytes, fc.f) != bytes ||
+      std::fread(hl.data(), sizeof(double), hl.size(), fc.f) != hl.size())
+    return fail(HMC_EINVAL, std::string(path) + " is truncated");
+  void* d = nullptr;
+  HMC_TRY(grow_staging(h, 0, bytes, &d));
+  HMC_CUDA(cudaMemcpyAsync(d, hb.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+  HMC_TRY(pack_all(h, d, chains, true, &StateSet::beta));
+  HMC_CUDA(cudaMemcpyAsync(d, hg.data(), bytes, cudaMemcpyHostToDevice, h->stream));   // after the pack, in stream order
+  HMC_TRY(pack_all(h, d, chains, true, &StateSet::grad));
+  for (int b = 0; b < nprob; ++b) {
+    HMC_CUDA(cudaMemcpyAsync(h->probs[b].logk, hl.data() + size_t(b) * chains, size_t(chains) * sizeof(double),
+                             cudaMemcpyHostToDevice, h->stream));
+    HMC_CUDA(cudaMemcpyAsync(h->probs[b].iter, &it[b], sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  }
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  h->chains_init = chains;
+  return HMC_OK;
+}
+
 hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales) {
   g_last_error.clear();
   if (!h) return fail(HMC_EINVAL, "NULL handle");

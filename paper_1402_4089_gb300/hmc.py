@@ -72,6 +72,8 @@ def lib():
         "hmc_sample_tempered": (st, [P, I32, I32, D, I64, U64, P, P, I32, P, P]),
         "hmc_get_state": (st, [P, I32, P, P, P, P]),
         "hmc_get_x": (st, [P, I32, P, P]),
+        "hmc_state_save": (st, [P, ctypes.c_char_p]),
+        "hmc_state_load": (st, [P, ctypes.c_char_p]),
         "hmc_describe": (ctypes.c_char_p, [P]),
         "hmc_set_timing": (st, [P, I32]),
         "hmc_fused_kernel_time": (st, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
@@ -228,6 +230,14 @@ class Handle:
         nxt = ctypes.c_int64(0)
         _check(lib().hmc_get_state(self._h, chains, _ptr(beta), _ptr(grad), _ptr(logpost), ctypes.byref(nxt)))
         return nxt.value
+
+    def save_state(self, path):
+        """Checkpoint the chain state (beta, grad, log K, next iteration) to `path`."""
+        _check(lib().hmc_state_save(self._h, os.fsencode(path)))
+
+    def load_state(self, path):
+        """Resume from a checkpoint written by save_state for the same problems."""
+        _check(lib().hmc_state_load(self._h, os.fsencode(path)))
 
     def get_x(self, b=0):
         """X of problem b as stored on the device (raw element bits) and the FP8 scales."""
