@@ -654,6 +654,35 @@ def run_reference(args):
     from oracle import model
     from paper_1402_4089_gb300 import synthetic
 
+    if args.workload == "sweep":
+        # the oracle's gradient over the Table 1 shapes it finishes quickly (N p <= cap)
+        rates, used, t_all = [], 0, time.perf_counter()
+        for (n, p, K) in synthetic.sweep_shapes()[:args.sweep_limit or None]:
+            if n * p > args.sweep_oracle_np:
+                continue
+            X, y, B = synthetic.sweep_problem(n, p, K)
+            X64 = X.astype(np.float64)
+            model.grad_log_kernel(X64, y, B, "cauchy", 1.0)
+            t0 = time.perf_counter()
+            model.grad_log_kernel(X64, y, B, "cauchy", 1.0)
+            rates.append(1.0 / (time.perf_counter() - t0))
+            used += 1
+        value = float(np.median(rates)) if rates else 0.0
+        el = time.perf_counter() - t_all
+        sample = f"one FP64 gradient (after a warm one) at each of {used} Table 1 shapes with N p <= {args.sweep_oracle_np:g}"
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": used, "warmup": used, "ms_per_step": round(el / max(used, 1) * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sweep: Table 1 grid, {used} shapes, 1 chain, Cauchy(0,1) prior",
+                       "value": "median over shapes of oracle gradient evaluations per second"},
+            "impl": "reference",
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}), flush=True)
+        return
+
     spec = workload_spec(args)
     X, y, _, _ = synthetic.make_workload(args.workload)
     X64 = np.asarray(X, dtype=np.float64)
