@@ -48,3 +48,17 @@ def test_recorded_traffic_follows_the_kernel_code(tmp_path, monkeypatch):
     assert b.recorded_traffic("highdim_fp32", "f32", "simt") == 123        # comments do not count
     k.write_text(k.read_text() + "\nstatic int changed_code = 1;\n")
     assert b.recorded_traffic("highdim_fp32", "f32", "simt") is None       # code changed since capture
+
+
+def test_reference_arm_sweep_line():
+    """The oracle's side of the Table 1 sweep prints one contract line (CPU only)."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "sweep",
+                        "--sweep-limit", "3"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
