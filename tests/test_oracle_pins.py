@@ -345,3 +345,42 @@ def test_fp8_column_scales_reconstruct():
         # relative spacing of E4M3 normals is 2^-3: rounding error <= 2^-4 relative
         big = np.abs(X[:, j]) > 2.0 ** -6 * s[j]
         assert np.all(np.abs(Xq[big, j] - X[big, j]) <= 2 ** -4 * np.abs(X[big, j]) * (1 + 1e-6))
+
+
+def _small_problem():
+    rng = np.random.default_rng(77)
+    X = rng.standard_normal((200, 8))
+    beta_true = rng.standard_normal((2, 8))
+    z = np.concatenate([X @ beta_true.T, np.zeros((200, 1))], axis=1)
+    y = np.array([rng.choice(3, p=np.exp(r - r.max()) / np.exp(r - r.max()).sum()) for r in z], dtype=np.int32)
+    return X, y
+
+
+def test_resume_continues_the_chain():
+    """Counter-based draws numbered by the global iteration (c-12): 6 iterations
+    equal 3 iterations followed by 3 more started from the kept state at
+    iteration index 3 -- the property a checkpoint relies on."""
+    X, y = _small_problem()
+    full = hmc.sample(X, y, 3, "gaussian", 10.0, 2, 5, 0.05, 6, 123)
+    first = hmc.sample(X, y, 3, "gaussian", 10.0, 2, 5, 0.05, 3, 123)
+    rest = hmc.sample(X, y, 3, "gaussian", 10.0, 2, 5, 0.05, 3, 123, beta0=first["beta"], iter0=3)
+    assert np.array_equal(full["samples"][:3], first["samples"])
+    assert np.array_equal(full["samples"][3:], rest["samples"])
+    assert np.array_equal(full["accept"][3:], rest["accept"])
+
+
+def test_tempered_acceptance_reading():
+    """Annealed burn-in (Sec. 3.2): accept iff log u < (H0 - H1) / T.  T = 1 is the
+    plain test; a huge T accepts every finite proposal; raising T never turns an
+    accepted proposal into a rejected one."""
+    X, y = _small_problem()
+    args = (X, y, 3, "gaussian", 10.0, 4, 5, 0.4, 5, 9)
+    plain = hmc.sample(*args)
+    ones = hmc.sample(*args, temps=np.ones(5))
+    assert np.array_equal(plain["samples"], ones["samples"]) and np.array_equal(plain["accept"], ones["accept"])
+    hot = hmc.sample(*args, temps=np.full(5, 1e12))
+    assert np.all(hot["accept"] | hot["diverged"])
+    # first iteration: same proposal at every temperature
+    warm = hmc.sample(*args, temps=np.full(5, 3.0))
+    assert np.all(warm["accept"][0] >= plain["accept"][0])
+    assert np.array_equal(warm["dH"][0], plain["dH"][0])
