@@ -24,21 +24,26 @@ import numpy as np
 from . import model, philox
 
 
-def leapfrog(X, y, beta, eta, eps, L, kind, scale, grad0=None):
+def leapfrog(X, y, beta, eta, eps, L, kind, scale, grad0=None, layout="free"):
     """Apply L leapfrog updates (Eqs. hmc1-hmc3) to (beta, eta).
 
-    beta, eta: arrays of shape (K-1, p).  Returns (beta', eta', log K(beta'),
+    beta, eta: arrays of shape (K-1, p), or (K, p) for the "masked" and
+    "unconstrained" layouts of ``model``.  Returns (beta', eta', log K(beta'),
     grad log K(beta')).
     """
     beta = np.array(beta, dtype=np.float64, copy=True)
     eta = np.array(eta, dtype=np.float64, copy=True)
-    g = model.grad_log_kernel(X, y, beta, kind, scale) if grad0 is None else np.array(grad0, dtype=np.float64)
+
+    def grad(b):
+        return model.grad_log_kernel_layout(X, y, b, kind, scale, layout)
+
+    g = grad(beta) if grad0 is None else np.array(grad0, dtype=np.float64)
     for _ in range(L):
         eta = eta + (eps / 2.0) * g          # Eq. hmc1
         beta = beta + eps * eta              # theta update between hmc1 and hmc3
-        g = model.grad_log_kernel(X, y, beta, kind, scale)
+        g = grad(beta)
         eta = eta + (eps / 2.0) * g          # Eq. hmc3
-    return beta, eta, model.log_kernel(X, y, beta, kind, scale), g
+    return beta, eta, model.log_kernel_layout(X, y, beta, kind, scale, layout), g
 
 
 def hamiltonian(logk, eta):
@@ -58,30 +63,38 @@ def annealing_temperatures(burn_in, t0=1.0e3, r=0.9):
 
 
 def sample(X, y, K, kind, scale, chains, L, eps, iters, seed,
-           beta0=None, iter0=0, temps=None, chain0=0):
+           beta0=None, iter0=0, temps=None, chain0=0, layout="free"):
     """Run `chains` independent HMC chains for `iters` iterations.
 
     eps   : scalar or per-iteration array of step sizes.
-    beta0 : (chains, K-1, p) start, zeros if None.
+    beta0 : (chains, R, p) start, zeros if None (R = K-1, or K for the
+            "masked" and "unconstrained" layouts).
     iter0 : RNG iteration index of the first iteration (counter word 1).
     temps : per-iteration acceptance temperatures (None -> all 1).
     chain0: RNG chain word of chain 0 (counter word 2 is chain0 + c).
 
-    Returns a dict with samples (iters, chains, K-1, p), accept (iters, chains),
+    The momentum is drawn for the free coefficients only: (K-1) p normals,
+    with the row of beta_K held at 0 in the masked layout (the Appendix sets
+    its momentum to 0), and K p normals in the unconstrained layout.
+
+    Returns a dict with samples (iters, chains, R, p), accept (iters, chains),
     dH = H1 - H0, logk (log K of the state kept), diverged, and the final
     state (beta, grad, logk).
     """
     X = np.asarray(X, dtype=np.float64)
     p = X.shape[1]
-    km1 = K - 1
+    km1 = K - 1 if layout == "free" else K
+    nfree = K * p if layout == "unconstrained" else (K - 1) * p
     eps_t = np.broadcast_to(np.asarray(eps, dtype=np.float64), (iters,))
     temp_t = np.ones(iters) if temps is None else np.asarray(temps, dtype=np.float64)
     if beta0 is None:
         beta = np.zeros((chains, km1, p))
     else:
         beta = np.array(beta0, dtype=np.float64).reshape(chains, km1, p).copy()
-    logk = np.array([model.log_kernel(X, y, beta[c], kind, scale) for c in range(chains)])
-    grad = np.stack([model.grad_log_kernel(X, y, beta[c], kind, scale) for c in range(chains)])
+    if layout == "masked":
+        beta[:, -1] = 0.0
+    logk = np.array([model.log_kernel_layout(X, y, beta[c], kind, scale, layout) for c in range(chains)])
+    grad = np.stack([model.grad_log_kernel_layout(X, y, beta[c], kind, scale, layout) for c in range(chains)])
 
     out_samples = np.empty((iters, chains, km1, p))
     out_acc = np.zeros((iters, chains), dtype=bool)
@@ -91,9 +104,10 @@ def sample(X, y, K, kind, scale, chains, L, eps, iters, seed,
     for t in range(iters):
         it = iter0 + t
         for c in range(chains):
-            eta0 = philox.momentum_normals(seed, it, chain0 + c, km1 * p).reshape(km1, p)
+            eta0 = np.zeros((km1, p))
+            eta0.reshape(-1)[:nfree] = philox.momentum_normals(seed, it, chain0 + c, nfree)
             h0 = hamiltonian(logk[c], eta0)
-            b1, e1, lk1, g1 = leapfrog(X, y, beta[c], eta0, eps_t[t], L, kind, scale, grad0=grad[c])
+            b1, e1, lk1, g1 = leapfrog(X, y, beta[c], eta0, eps_t[t], L, kind, scale, grad0=grad[c], layout=layout)
             h1 = hamiltonian(lk1, e1)
             u = philox.accept_uniform(seed, it, chain0 + c)
             finite = np.isfinite(h1)

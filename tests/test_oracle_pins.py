@@ -384,3 +384,17 @@ def test_tempered_acceptance_reading():
     warm = hmc.sample(*args, temps=np.full(5, 3.0))
     assert np.all(warm["accept"][0] >= plain["accept"][0])
     assert np.array_equal(warm["dH"][0], plain["dH"][0])
+
+
+# --- row-blocked evaluation (for X too large to hold in FP64 at once) ---------
+
+def test_row_blocks_equal_the_whole_problem():
+    X, y, _ = _small(n=53, p=7, K=4)
+    rng = np.random.default_rng(12)
+    betas = [0.4 * rng.standard_normal((3, 7)) for _ in range(2)]
+    blocks = [(X[a:a + 20], y[a:a + 20]) for a in range(0, 53, 20)]
+    lk, g, Z = model.log_kernel_and_grad_by_rows(blocks, betas, "cauchy", 1.5)
+    for c, b in enumerate(betas):
+        assert abs(lk[c] - model.log_kernel(X, y, b, "cauchy", 1.5)) < 1e-11
+        assert np.allclose(g[c], model.grad_log_kernel(X, y, b, "cauchy", 1.5), rtol=1e-12, atol=1e-12)
+        assert np.allclose(Z[c], model.full_logits(X, b), rtol=0, atol=1e-13)
