@@ -22,11 +22,13 @@
  *    stated otherwise; results are valid after that stream is synchronised.
  *  - A handle is not thread safe: one thread at a time per handle.
  *  - Coefficient layout ("beta layout"): for `chains` chains of a problem
- *    with p features and K classes, a dense array [chains][K-1][p] of the
- *    handle's state type (double for HMC_F64, float for HMC_F32).  Row k of
- *    chain c is beta_{k+1} of that chain; beta_K = 0 is implied (Sec. 2.1,
- *    identifiability) and never stored.  For a batch handle the problems'
- *    blocks follow one another in problem order.
+ *    with p features and K classes, a dense array [chains][R][p] of the
+ *    handle's state type (double for HMC_F64, float for HMC_F32), where R is
+ *    the number of coefficient rows per chain of opts.layout (hmc_layout):
+ *    R = K-1 for HMC_LAYOUT_FREE (row k of chain c is beta_{k+1}; beta_K = 0
+ *    is implied by the identifiability constraint of Sec. 2.1 and never
+ *    stored), R = K for HMC_LAYOUT_MASKED and HMC_LAYOUT_UNCONSTRAINED.  For a
+ *    batch handle the problems' blocks follow one another in problem order.
  *  - Every device-side wait is bounded (opts.spin_limit); when a bound runs
  *    out the kernel stops, the call returns HMC_ETIMEOUT and the handle stays
  *    usable.
@@ -58,6 +60,23 @@ typedef enum {
  * kernel -b^2/(2 s^2).  No normalising constants (Sec. 1.1). */
 typedef enum { HMC_PRIOR_GAUSSIAN = 0, HMC_PRIOR_CAUCHY = 1 } hmc_prior_kind;
 
+/* Coefficient layout and identifiability (Sec. 2.1; Appendix, the mask M
+ * after Eq. fullgrad).
+ *  HMC_LAYOUT_FREE          K-1 free coefficient rows per chain, beta_K = 0
+ *                           implied (the default).
+ *  HMC_LAYOUT_MASKED        K rows per chain in the p x K form of Eq. fullgrad;
+ *                           row K is held at zero: the gradient and momentum of
+ *                           beta_K are masked to zero, as the elementwise mask M
+ *                           of the Appendix does, so values, gradients and
+ *                           chains equal those of HMC_LAYOUT_FREE with a zero
+ *                           row appended.  Row K of any input is ignored (read
+ *                           as zero); row K of every output is zero.
+ *  HMC_LAYOUT_UNCONSTRAINED K free rows per chain: identifiability is not
+ *                           enforced (the prediction-only variant whose timings
+ *                           are Figs 3-4); the softmax runs over K free logits
+ *                           and the prior covers all p K coefficients. */
+typedef enum { HMC_LAYOUT_FREE = 0, HMC_LAYOUT_MASKED = 1, HMC_LAYOUT_UNCONSTRAINED = 2 } hmc_layout;
+
 /* Element types.  X may be stored as HMC_F64, HMC_F32, HMC_BF16 (round to
  * nearest even) or HMC_FP8E4M3 (per-column scale s_j = max_i|x_ij|/448,
  * x_ij/s_j rounded to nearest even, saturating).  The chain state (beta,
@@ -81,6 +100,9 @@ typedef struct {
                              launches no more than one cluster per S SMs unless each still gets
                              about four 16-row tiles; the chosen tensor-core tile takes the most
                              chains TMEM holds, spread evenly over the launches a call needs */
+  int32_t layout;         /* hmc_layout of every coefficient buffer (default HMC_LAYOUT_FREE); the
+                             kernels see K-1 free rows (K for HMC_LAYOUT_UNCONSTRAINED), which must
+                             fit their class bounds */
 } hmc_opts;
 
 /* Per-chain counters of hmc_sample (host memory, one entry per chain). */
@@ -132,7 +154,8 @@ hmc_status hmc_create_batch(int32_t nprob, const void* const* X, hmc_dtype x_dty
 /* Release every resource of the handle (NULL is accepted).  Synchronous. */
 hmc_status hmc_destroy(hmc_handle h);
 
-/* Total free coefficients of one chain (sum over problems of (K_b-1) p_b). */
+/* Coefficients of one chain in the beta layout (sum over problems of R_b p_b,
+ * R_b the rows per chain of opts.layout). */
 int64_t hmc_chain_size(hmc_handle h);
 
 /*
@@ -189,6 +212,38 @@ hmc_status hmc_sample_tempered(hmc_handle h, int32_t chains, int32_t L, double e
                                hmc_chain_stats* stats, const double* temps);
 
 /*
+ * hmc_predict -- posterior predictive class probabilities and classes
+ * (Sec. 3.2: predict the class with the highest average softmax value over the
+ * posterior samples).  For every row x_i of Xnew: prob[i][k] = the mean over
+ * the draws d of psi_k(x_i B_d) (Eq. softmax, all K classes, the implied zero
+ * logit of class K included in the identifiable layouts), summed in draw order
+ * in FP64; cls[i] = argmax_k prob[i][k], the lowest class on a tie.  Logits and
+ * softmax are formed in the handle's state type from Xnew as given.
+ *   b        problem index (0 for a single-problem handle).
+ *   draws    host or device [ndraws][R][p_b] of the state type: coefficient
+ *            states of problem b in the beta layout of one chain, e.g. the
+ *            samples of hmc_sample on a single-problem handle read as
+ *            (iters / thin) * chains draws.  ndraws >= 1.
+ *   Xnew     host or device, row-major n_new x p_b of x_dtype (HMC_F64 or
+ *            HMC_F32).  n_new >= 0.
+ *   prob     host or device double[n_new][K], or NULL.
+ *   cls      host or device int32[n_new], or NULL.
+ * At most 32 classes (HMC_EUNSUPPORTED above).  Synchronous.
+ */
+hmc_status hmc_predict(hmc_handle h, int32_t b, const void* draws, int64_t ndraws, const void* Xnew,
+                       hmc_dtype x_dtype, int64_t n_new, double* prob, int32_t* cls);
+
+/*
+ * hmc_annealing_schedule -- the acceptance temperatures of the annealed
+ * burn-in of Sec. 3.2 for `iters` iterations: T_t = max(1, r T_{t-1}) with
+ * T_0 = t0, iteration t = 1..iters accepting at T_t (once T reaches 1 it stays
+ * there).  temps: host double[iters] (output), to be passed to
+ * hmc_sample_tempered.  Requires t0 >= 1, 0 < r <= 1, iters >= 0 (else
+ * HMC_EINVAL).  Host computation only; no handle, no device work.
+ */
+hmc_status hmc_annealing_schedule(double t0, double r, int64_t iters, double* temps);
+
+/*
  * hmc_get_state -- copy the handle's chain state: beta and grad (beta layout,
  * host or device, or NULL), logpost (double[nprob * chains], host or device,
  * or NULL) and the next iteration index (host, or NULL).  Synchronous.
@@ -201,14 +256,21 @@ hmc_status hmc_get_state(hmc_handle h, int32_t chains, void* beta, void* grad, d
  * that hmc_sample continues from: beta, grad and log K of the handle's chains
  * (every problem) and the next global iteration index, which numbers the
  * counter-based momentum and accept draws (Sec. 1.1 proposals).  The file at
- * `path` (host path, overwritten by save) records the state type and every
- * problem's (n, p, K); load requires a handle with the same problems, state
- * type and max_chains >= the saved chain count, and replaces its chain state,
- * so hmc_sample with beta0 = NULL, the saved chain count and the same seed then
- * continues the saved chains exactly (bitwise, on the same device and tile
- * configuration; another chain count starts over from zero).  Save
- * needs a chain state (HMC_EINVAL before the first hmc_sample); a missing,
- * truncated or mismatched file is HMC_EINVAL.  Synchronous.
+ * `path` (host path, overwritten by save) records the state type, the storage
+ * type of X, the prior (kind and scale), the coefficient layout and every
+ * problem's (n, p, K).  Load requires a handle that matches all of them and has
+ * max_chains >= the saved chain count, and it evaluates log K and the gradient
+ * at the saved coefficients: if they differ from the saved ones by more than
+ * rounding (relative 1e-4; 1e-9 for HMC_F64), the checkpoint belongs to another
+ * posterior (other X or labels) and is rejected.  On success the handle's chain
+ * state is replaced, so hmc_sample with beta0 = NULL, the saved chain count and
+ * the same seed continues the saved chains; the continuation is bitwise
+ * identical to an uninterrupted run when the device and the tile configuration
+ * are the same (pass opts.tile explicitly: a measured tile choice may differ
+ * between runs), otherwise equal to rounding.  Another chain count starts over
+ * from zero.  Save needs a chain state (HMC_EINVAL before the first
+ * hmc_sample); a missing, truncated or mismatched file is HMC_EINVAL.
+ * Synchronous.
  */
 hmc_status hmc_state_save(hmc_handle h, const char* path);
 hmc_status hmc_state_load(hmc_handle h, const char* path);
@@ -251,15 +313,20 @@ hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launch
  * must not pay cudaMalloc's implicit device synchronisation.  No handle is
  * used; the caller owns every buffer below (all device memory):
  *   X        FP32, row-major n x ldx; columns [p, ldx) must be zero.
- *            ldx >= p and a multiple of 16; a multiple of 256 (up to
- *            20480) always finds a tile.
- *   y        int32[n], labels in [0, K) (not validated).
+ *            ldx >= p and a multiple of 16; a multiple of 256 finds a tile up
+ *            to 10240 for any C = chains (K-1) <= 20, up to 16384 for C <= 12
+ *            and up to 20480 for C <= 6 (the coefficient slice and the ring of
+ *            one cluster CTA share its shared memory).
+ *   y        int32[n], labels in [0, K); the fused pass flags any other
+ *            value and the call then returns HMC_ENONFINITE (outputs invalid).
  *   beta     FP32 [chains][K-1][p]; chains * (K-1) <= 20.
  *   logpost  double[chains]; grad FP32 [chains][K-1][p].
  *   stream   cudaStream_t (NULL: legacy default stream).
  * The library's intermediates live in a 16 MiB static device array that
  * every GPU loading the library holds until the process exits.  Problems
- * whose intermediates do not fit are rejected with HMC_EINVAL and a message.
+ * whose intermediates do not fit are rejected with HMC_EINVAL and a message;
+ * the array also bounds the clusters of the fused pass (one partial gradient
+ * slice each), so the widest problems run on fewer SMs than through a handle.
  * The first call on a device takes that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call
  * before any stream capture.  All calls share the array: calls whose GPU

@@ -64,7 +64,10 @@ struct StateSet {
 
 struct Problem {
   int64_t n = 0;
-  int32_t p = 0, p_pad = 0, K = 0, Km1 = 0;
+  int32_t p = 0, p_pad = 0, K = 0;
+  int32_t Km1 = 0;     // free coefficient rows per chain the kernels see (K - 1, or K unconstrained)
+  int32_t ku = 0;      // rows per chain of the user's beta layout (Km1, or K with the masked row)
+  int32_t zlogit = 1;  // class K is the implied zero logit (identifiable layouts)
   void* X = nullptr;
   int32_t* y = nullptr;
   float* xscale = nullptr;
@@ -100,7 +103,7 @@ struct FusedTimer {
 }  // namespace
 
 struct hmc_ctx {
-  int xt = HMC_F32, st = HMC_F32, prior_kind = 0;
+  int xt = HMC_F32, st = HMC_F32, prior_kind = 0, layout = HMC_LAYOUT_FREE;
   double prior_scale = 1.0;
   int max_chains = 1, engine = 0;
   long long spin_limit = 1ll << 22;
@@ -217,6 +220,7 @@ int balanced_group(int chains, int gmax) {
 // then the cluster size that keeps the most SMs busy.
 hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
   *ok = false;
+  if (P.Km1 > 32) return HMC_OK;   // the softmax maps one (row, chain) task to a warp, class <-> lane
   int dev = 0, smem_max = 0;
   HMC_CUDA(cudaGetDevice(&dev));
   HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -313,7 +317,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   if (!tc_ok) {
     const int maxct = simt_max_ct(h->xt);
     if (P.Km1 > maxct)
-      return fail(HMC_EUNSUPPORTED, "K-1 = " + std::to_string(P.Km1) + " exceeds the CUDA-core kernel's class bound " +
+      return fail(HMC_EUNSUPPORTED, "free classes per chain " + std::to_string(P.Km1) + " exceed the CUDA-core kernel's class bound " +
                                         std::to_string(maxct));
     P.group_chains = balanced_group(h->max_chains, std::max(1, std::min(h->max_chains, maxct / P.Km1)));
     P.ct_launch = P.group_chains * P.Km1;
@@ -489,6 +493,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       L.err = h->err_d;
       L.spin_limit = h->spin_limit;
       L.inject_timeout = inject ? 1 : 0;
+      L.zlogit = P.zlogit;
       le = tc_launch(P.tp, L, P.smem, stream);
     } else {
       LpgArgs a{};
@@ -506,6 +511,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       a.PC = P.PC;
       a.C = C;
       a.Km1 = P.Km1;
+      a.zlogit = P.zlogit;
       a.chains = c1 - c0;
       a.BM = P.BM;
       a.CR = P.CR;
@@ -548,6 +554,7 @@ LpgArgs batched_args(hmc_ctx* h, Problem& P, StateSet& S) {
   a.PC = P.PC;
   a.C = h->max_chains * P.Km1;
   a.Km1 = P.Km1;
+  a.zlogit = P.zlogit;
   a.chains = h->max_chains;
   a.BM = P.BM;
   a.CR = P.CR;
@@ -686,6 +693,7 @@ hmc_status setup_batched_tc(hmc_ctx* h) {
     L.err = h->err_d;
     L.spin_limit = h->spin_limit;
     L.inject_timeout = 0;
+    L.zlogit = P.zlogit;
     for (int w = 0; w < 2; ++w)
       boxes[w * m + b] = TcBetaBox{static_cast<const float*>(w == 0 ? P.cs.beta : P.us.beta), P.xscale, P.bbf, P.Km1,
                                    P.tp.N, P.p_pad};
@@ -769,6 +777,7 @@ UpdateArgs make_update(hmc_ctx* h, Problem& P, StateSet& S, int which_logk, int 
   u.p = P.p;
   u.p_pad = P.p_pad;
   u.Km1 = P.Km1;
+  u.ku = P.ku;
   u.chains = chains;
   u.nblk = P.nblk;
   u.prior_kind = h->prior_kind;
@@ -794,12 +803,15 @@ hmc_status validate_opts(const hmc_opts* o) {
   if (t[2] < 0 || t[2] > kTcMaxDepth)
     return fail(HMC_EINVAL, "opts.tile[2] (tensor-core sweep lookahead) must be in [0, " + std::to_string(kTcMaxDepth) + "]");
   if (t[3] != 0 && (t[3] < 2 || t[3] > 6)) return fail(HMC_EINVAL, "opts.tile[3] (ring chunks) must be 0 or in [2, 6]");
+  if (o->layout < HMC_LAYOUT_FREE || o->layout > HMC_LAYOUT_UNCONSTRAINED)
+    return fail(HMC_EINVAL, "opts.layout must be HMC_LAYOUT_FREE, HMC_LAYOUT_MASKED or HMC_LAYOUT_UNCONSTRAINED");
   return HMC_OK;
 }
 
 void build_description(hmc_ctx* h) {
   std::string s = "{\"engine\": \"" + std::string(h->probs.empty() || h->probs[0].engine == 1 ? "simt" : "tcgen05") +
                   "\", \"batched_launch\": " + std::string(h->batched || h->tc_batched ? "true" : "false") +
+                  ", \"layout\": " + std::to_string(h->layout) +
                   ", \"x_storage\": " + std::to_string(h->xt) +
                   ", \"state\": " + std::to_string(h->st) + ", \"max_chains\": " + std::to_string(h->max_chains) +
                   ", \"problems\": [";
@@ -847,6 +859,7 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
   h->prior_scale = prior_scale;
   h->max_chains = o.max_chains;
   h->engine = o.engine;
+  h->layout = o.layout;
   h->spin_limit = o.spin_limit > 0 ? o.spin_limit : (1ll << 22);
   h->stream = static_cast<cudaStream_t>(o.stream);
   for (int i = 0; i < 4; ++i) h->tile[i] = o.tile[i];
@@ -869,7 +882,9 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
     P.n = n[b];
     P.p = int32_t(p[b]);
     P.K = K[b];
-    P.Km1 = K[b] - 1;
+    P.Km1 = (h->layout == HMC_LAYOUT_UNCONSTRAINED) ? K[b] : K[b] - 1;
+    P.ku = (h->layout == HMC_LAYOUT_FREE) ? K[b] - 1 : K[b];
+    P.zlogit = (h->layout == HMC_LAYOUT_UNCONSTRAINED) ? 0 : 1;
   }
   // A batch on the CUDA-core engine shares one cluster size (the largest any
   // problem needs) so that one fused launch can serve every problem.
@@ -914,7 +929,7 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
     Problem& P = h->probs[b];
     hmc_status s = setup_problem(h, P, X[b], x_dtype, y[b]);
     if (s != HMC_OK) return cleanup(s);
-    h->chain_size += int64_t(P.Km1) * P.p;
+    h->chain_size += int64_t(P.ku) * P.p;
   }
   if (want_batch) {
     h->tile[0] = 0;
@@ -933,7 +948,7 @@ hmc_status create_common(int32_t nprob, const void* const* X, hmc_dtype x_dtype,
 
 int64_t block_offset(const hmc_ctx* h, int b, int chains) {
   int64_t off = 0;
-  for (int q = 0; q < b; ++q) off += int64_t(chains) * h->probs[q].Km1 * h->probs[q].p;
+  for (int q = 0; q < b; ++q) off += int64_t(chains) * h->probs[q].ku * h->probs[q].p;
   return off;
 }
 
@@ -944,7 +959,7 @@ hmc_status pack_all(hmc_ctx* h, const void* user_dev, int chains, bool chain_sta
     Problem& P = h->probs[b];
     StateSet& S = chain_state ? P.cs : P.us;
     const char* src = static_cast<const char*>(user_dev) + size_t(block_offset(h, int(b), chains)) * sb;
-    HMC_CUDA(launch_pack(h->st, src, S.*field, int64_t(chains) * P.Km1, P.p, P.p_pad, h->stream));
+    HMC_CUDA(launch_pack(h->st, src, S.*field, chains, P.ku, P.Km1, P.p, P.p_pad, h->stream));
   }
   return HMC_OK;
 }
@@ -955,7 +970,7 @@ hmc_status unpack_all(hmc_ctx* h, void* user_dev, int chains, bool chain_state, 
     Problem& P = h->probs[b];
     StateSet& S = chain_state ? P.cs : P.us;
     char* dst = static_cast<char*>(user_dev) + size_t(block_offset(h, int(b), chains)) * sb;
-    HMC_CUDA(launch_unpack(h->st, S.*field, dst, int64_t(chains) * P.Km1, P.p, P.p_pad, h->stream));
+    HMC_CUDA(launch_unpack(h->st, S.*field, dst, chains, P.ku, P.Km1, P.p, P.p_pad, h->stream));
   }
   return HMC_OK;
 }
@@ -1277,6 +1292,50 @@ hmc_status hmc_sample(hmc_handle h, int32_t chains, int32_t L, double eps, int64
   return hmc_sample_tempered(h, chains, L, eps, iters, seed, beta0, samples, thin, stats, nullptr);
 }
 
+hmc_status hmc_predict(hmc_handle h, int32_t b, const void* draws, int64_t ndraws, const void* Xnew,
+                       hmc_dtype x_dtype, int64_t n_new, double* prob, int32_t* cls) {
+  g_last_error.clear();
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  if (b < 0 || b >= int(h->probs.size())) return fail(HMC_EINVAL, "problem index out of range");
+  if (!draws || ndraws < 1) return fail(HMC_EINVAL, "need ndraws >= 1 coefficient draws");
+  if (n_new < 0) return fail(HMC_EINVAL, "n_new must be >= 0");
+  if (n_new > 0 && !Xnew) return fail(HMC_EINVAL, "Xnew is NULL");
+  if (x_dtype != HMC_F64 && x_dtype != HMC_F32) return fail(HMC_EINVAL, "x_dtype must be HMC_F64 or HMC_F32");
+  Problem& P = h->probs[b];
+  if (P.K > predict_max_classes())
+    return fail(HMC_EUNSUPPORTED, "prediction handles at most " + std::to_string(predict_max_classes()) + " classes");
+  if (n_new == 0 || (!prob && !cls)) return HMC_OK;
+  const size_t db = size_t(ndraws) * P.ku * P.p * state_bytes(h);
+  const size_t xb = size_t(n_new) * P.p * (x_dtype == HMC_F64 ? 8 : 4);
+  const void *dd = nullptr, *xd = nullptr;
+  HMC_TRY(dev_in(h, 0, draws, db, &dd));
+  HMC_TRY(dev_in(h, 1, Xnew, xb, &xd));
+  bool ph = false, chh = false;
+  void *pd = nullptr, *cd = nullptr;
+  HMC_TRY(dev_out(h, 2, prob, size_t(n_new) * P.K * sizeof(double), &pd, &ph));
+  HMC_TRY(dev_out(h, 3, cls, size_t(n_new) * sizeof(int32_t), &cd, &chh));
+  HMC_CUDA(launch_predict(h->st, x_dtype, xd, n_new, P.p, dd, ndraws, P.ku, P.zlogit ? P.K - 1 : P.K, P.zlogit, P.K,
+                          static_cast<double*>(pd), static_cast<int32_t*>(cd), h->stream));
+  if (ph) HMC_CUDA(cudaMemcpyAsync(prob, pd, size_t(n_new) * P.K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (chh) HMC_CUDA(cudaMemcpyAsync(cls, cd, size_t(n_new) * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  HMC_CUDA(cudaStreamSynchronize(h->stream));
+  return HMC_OK;
+}
+
+hmc_status hmc_annealing_schedule(double t0, double r, int64_t iters, double* temps) {
+  g_last_error.clear();
+  if (!(t0 >= 1.0) || !std::isfinite(t0)) return fail(HMC_EINVAL, "t0 must be finite and >= 1");
+  if (!(r > 0.0 && r <= 1.0)) return fail(HMC_EINVAL, "r must be in (0, 1]");
+  if (iters < 0) return fail(HMC_EINVAL, "iters must be >= 0");
+  if (iters > 0 && !temps) return fail(HMC_EINVAL, "temps is NULL");
+  double t = t0;
+  for (int64_t i = 0; i < iters; ++i) {
+    t = std::max(1.0, r * t);
+    temps[i] = t;
+  }
+  return HMC_OK;
+}
+
 hmc_status hmc_get_state(hmc_handle h, int32_t chains, void* beta, void* grad, double* logpost,
                          int64_t* next_iteration) {
   g_last_error.clear();
@@ -1301,18 +1360,50 @@ hmc_status hmc_get_state(hmc_handle h, int32_t chains, void* beta, void* grad, d
 }
 
 // ------------------------------------------------------------- checkpoints
-// File layout (host byte order): the 8 bytes "HMCCKPT1"; int32 state type,
-// number of problems, chains, 0; per problem int64 n, int32 p, int32 K, int64
-// next global iteration; then beta and grad of every chain in the beta layout
-// of hmc_logpost_grad (state type), and log K as double[nprob * chains].
+// File layout (host byte order): the 8 bytes "HMCCKPT2"; int32 state type,
+// number of problems, chains, X storage type, prior kind, coefficient layout;
+// double prior scale; per problem int64 n, int32 p, int32 K, int64 next global
+// iteration; then beta and grad of every chain in the beta layout of
+// hmc_logpost_grad (state type), and log K as double[nprob * chains].
 namespace {
-constexpr char kCkptMagic[8] = {'H', 'M', 'C', 'C', 'K', 'P', 'T', '1'};
+constexpr char kCkptMagic[8] = {'H', 'M', 'C', 'C', 'K', 'P', 'T', '2'};
 struct FileCloser {
   FILE* f = nullptr;
   ~FileCloser() {
     if (f) std::fclose(f);
   }
 };
+
+// Largest |a - b| / max(1, |b|) over n doubles, and the relative 2-norm error
+// ||a - b|| / ||b|| over n values of the state type (bytes per value sb).
+double logk_mismatch(const double* a, const double* b, size_t n) {
+  double m = 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    const double d = std::fabs(a[i] - b[i]) / std::max(1.0, std::fabs(b[i]));
+    m = std::max(m, std::isfinite(d) ? d : 1e300);
+  }
+  return m;
+}
+double grad_mismatch(const char* a, const char* b, size_t n, size_t sb) {
+  double num = 0.0, den = 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    double x, y;
+    if (sb == 8) {
+      std::memcpy(&x, a + i * 8, 8);
+      std::memcpy(&y, b + i * 8, 8);
+    } else {
+      float xf, yf;
+      std::memcpy(&xf, a + i * 4, 4);
+      std::memcpy(&yf, b + i * 4, 4);
+      x = xf;
+      y = yf;
+    }
+    num += (x - y) * (x - y);
+    den += y * y;
+  }
+  const double r = std::sqrt(num) / std::max(std::sqrt(den), 1e-300);
+  return std::isfinite(r) ? r : 1e300;
+}
 }  // namespace
 
 hmc_status hmc_state_save(hmc_handle h, const char* path) {
@@ -1342,8 +1433,10 @@ hmc_status hmc_state_save(hmc_handle h, const char* path) {
   FileCloser fc;
   fc.f = std::fopen(path, "wb");
   if (!fc.f) return fail(HMC_EINVAL, std::string("cannot open ") + path + " for writing");
-  const int32_t hdr[4] = {int32_t(h->st), int32_t(nprob), int32_t(chains), 0};
-  bool ok = std::fwrite(kCkptMagic, 1, 8, fc.f) == 8 && std::fwrite(hdr, sizeof(int32_t), 4, fc.f) == 4;
+  const int32_t hdr[6] = {int32_t(h->st), int32_t(nprob), int32_t(chains), int32_t(h->xt), int32_t(h->prior_kind),
+                          int32_t(h->layout)};
+  bool ok = std::fwrite(kCkptMagic, 1, 8, fc.f) == 8 && std::fwrite(hdr, sizeof(int32_t), 6, fc.f) == 6 &&
+            std::fwrite(&h->prior_scale, sizeof(double), 1, fc.f) == 1;
   for (int b = 0; b < nprob && ok; ++b) {
     const Problem& P = h->probs[b];
     const int64_t n = P.n;
@@ -1367,13 +1460,18 @@ hmc_status hmc_state_load(hmc_handle h, const char* path) {
   fc.f = std::fopen(path, "rb");
   if (!fc.f) return fail(HMC_EINVAL, std::string("cannot open ") + path);
   char magic[8];
-  int32_t hdr[4];
+  int32_t hdr[6];
+  double pscale = 0.0;
   if (std::fread(magic, 1, 8, fc.f) != 8 || std::memcmp(magic, kCkptMagic, 8) != 0 ||
-      std::fread(hdr, sizeof(int32_t), 4, fc.f) != 4)
+      std::fread(hdr, sizeof(int32_t), 6, fc.f) != 6 || std::fread(&pscale, sizeof(double), 1, fc.f) != 1)
     return fail(HMC_EINVAL, std::string(path) + " is not a chain-state checkpoint");
   const int nprob = int(h->probs.size());
   if (hdr[0] != h->st) return fail(HMC_EINVAL, "the checkpoint's state type differs from the handle's");
   if (hdr[1] != nprob) return fail(HMC_EINVAL, "the checkpoint holds a different number of problems");
+  if (hdr[3] != h->xt) return fail(HMC_EINVAL, "the checkpoint was taken with another storage type of X");
+  if (hdr[4] != h->prior_kind || pscale != h->prior_scale)
+    return fail(HMC_EINVAL, "the checkpoint was taken under another prior (kind or scale)");
+  if (hdr[5] != h->layout) return fail(HMC_EINVAL, "the checkpoint uses another coefficient layout");
   const int chains = hdr[2];
   if (chains < 1 || chains > h->max_chains)
     return fail(HMC_EINVAL, "the checkpoint's chain count is outside [1, max_chains]");
@@ -1389,14 +1487,39 @@ hmc_status hmc_state_load(hmc_handle h, const char* path) {
       return fail(HMC_EINVAL, "problem " + std::to_string(b) + " of the checkpoint has another shape (n, p, K)");
     if (it[b] < 0) return fail(HMC_EINVAL, "negative iteration index in the checkpoint");
   }
-  const size_t bytes = size_t(chains) * h->chain_size * state_bytes(h);
-  std::vector<char> hb(bytes), hg(bytes);
-  std::vector<double> hl(size_t(nprob) * chains);
+  const size_t sb = state_bytes(h);
+  const size_t bytes = size_t(chains) * h->chain_size * sb;
+  std::vector<char> hb(bytes), hg(bytes), rg(bytes);
+  std::vector<double> hl(size_t(nprob) * chains), rl(hl.size());
   if (std::fread(hb.data(), 1, bytes, fc.f) != bytes || std::fread(hg.data(), 1, bytes, fc.f) != bytes ||
       std::fread(hl.data(), sizeof(double), hl.size(), fc.f) != hl.size())
     return fail(HMC_EINVAL, std::string(path) + " is truncated");
+  // The saved gradient and log K are reused as the state of the next
+  // trajectory's first half step and accept test, so they must belong to this
+  // handle's posterior: evaluate both at the saved coefficients (user scratch
+  // state, the chain state is untouched) and compare.  The same X, labels and
+  // prior agree to rounding order; another posterior does not.
   void* d = nullptr;
   HMC_TRY(grow_staging(h, 0, bytes, &d));
+  HMC_CUDA(cudaMemcpyAsync(d, hb.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+  HMC_TRY(pack_all(h, d, chains, false, &StateSet::beta));
+  HMC_TRY(eval_state(h, false, chains));
+  HMC_TRY(unpack_all(h, d, chains, false, &StateSet::grad));
+  HMC_CUDA(cudaMemcpyAsync(rg.data(), d, bytes, cudaMemcpyDeviceToHost, h->stream));
+  for (int b = 0; b < nprob; ++b)
+    HMC_CUDA(cudaMemcpyAsync(rl.data() + size_t(b) * chains, h->probs[b].logk + h->max_chains,
+                             size_t(chains) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  HMC_TRY(check_device_error(h));
+  const double el = logk_mismatch(hl.data(), rl.data(), hl.size());
+  const double eg = grad_mismatch(hg.data(), rg.data(), bytes / sb, sb);
+  const double tol = h->xt == HMC_F64 ? 1e-9 : 1e-4;
+  if (el > tol || eg > tol) {
+    char buf[200];
+    std::snprintf(buf, sizeof(buf),
+                  "the checkpoint does not belong to this handle's posterior (log K mismatch %.3g, gradient "
+                  "mismatch %.3g at the saved coefficients; tolerance %.0e)", el, eg, tol);
+    return fail(HMC_EINVAL, buf);
+  }
   HMC_CUDA(cudaMemcpyAsync(d, hb.data(), bytes, cudaMemcpyHostToDevice, h->stream));
   HMC_TRY(pack_all(h, d, chains, true, &StateSet::beta));
   HMC_CUDA(cudaMemcpyAsync(d, hg.data(), bytes, cudaMemcpyHostToDevice, h->stream));   // after the pack, in stream order

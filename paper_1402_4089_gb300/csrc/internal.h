@@ -27,7 +27,8 @@ struct LpgArgs {
   int32_t p_pad;            // padded columns (= S * PC)
   int32_t PC;               // columns per CTA
   int32_t C;                // coefficient columns of this launch (chains * Km1)
-  int32_t Km1;              // K - 1
+  int32_t Km1;              // free coefficient rows per chain (K - 1, or K when unconstrained)
+  int32_t zlogit;           // 1: class K is the implied zero logit (valid labels 0..Km1); 0: none (0..Km1-1)
   int32_t chains;           // chains of this launch
   int32_t BM;               // rows per super-tile (8 on the CUDA-core engine)
   int32_t CR;               // unused by the CUDA-core engine (kept equal to BM)
@@ -98,6 +99,7 @@ struct TcLaunch {
   int* err;
   long long spin_limit;
   int32_t inject_timeout;
+  int32_t zlogit;           // 1: class K is the implied zero logit; 0: all Km1 classes free
 };
 bool tc_plan(int64_t p, int C, int S, TcPlan* out);
 size_t tc_smem_bytes(const TcPlan& pl, int NST, int chains, bool fp8);
@@ -149,6 +151,7 @@ struct UpdateArgs {
   int32_t chains_word_hi;  // problem index (high half of the RNG chain word)
   int* err;
   int32_t p, p_pad, Km1, chains, nblk;
+  int32_t ku;       // rows per chain of the user layout (samples): Km1, or Km1 + 1 with a zero masked row
   int32_t prior_kind; double prior_scale;
   double eps;
   const uint64_t* seed;  // device: generator key of the current hmc_sample call
@@ -168,10 +171,13 @@ cudaError_t launch_select(int st, const UpdateArgs& a, unsigned int* ticket_all,
 int update_blocks_per_chain(int64_t per_chain);
 cudaError_t launch_leap_start(int st, const UpdateArgs& a, cudaStream_t s);
 
-// Layout conversion between the user layout [chains][Km1][p] (state type)
-// and the padded device layout [chains][Km1][p_pad].
-cudaError_t launch_pack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s);
-cudaError_t launch_unpack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s);
+// Layout conversion between the user layout [chains][ku][p] (state type)
+// and the padded device layout [chains][km1][p_pad] (ku >= km1): pack drops
+// rows km1..ku-1 of each chain (a masked row), unpack writes them as zero.
+cudaError_t launch_pack(int st, const void* src, void* dst, int64_t chains, int32_t ku, int32_t km1, int32_t p,
+                        int32_t p_pad, cudaStream_t s);
+cudaError_t launch_unpack(int st, const void* src, void* dst, int64_t chains, int32_t ku, int32_t km1, int32_t p,
+                          int32_t p_pad, cudaStream_t s);
 
 // X upload: convert float/double rows into the storage type with padding.
 cudaError_t launch_convert_x(int in_dtype, const void* src, int xt, void* dst, const float* scales, int64_t n, int32_t p,
@@ -180,6 +186,14 @@ cudaError_t launch_fp8_scales(int in_dtype, const void* src, float* scales, int6
                               cudaStream_t s);
 cudaError_t launch_check_labels(const int32_t* y, int64_t n, int32_t K, int* err, cudaStream_t s);
 cudaError_t launch_init_stats(void* stats, int chains, cudaStream_t s);
+
+// Posterior predictive (predict.cu): mean softmax over `ndraws` coefficient
+// draws [ndraws][ku][p] (state type) for the rows of X (n x p, in_dtype), and
+// its argmax.  K <= predict_max_classes().
+int predict_max_classes();
+cudaError_t launch_predict(int st, int in_dtype, const void* X, int64_t n, int32_t p, const void* draws, int64_t ndraws,
+                           int32_t ku, int32_t km1, int32_t zlogit, int32_t K, double* prob, int32_t* cls,
+                           cudaStream_t s);
 
 // Message returned by hmc_last_error() for the calling thread.
 void set_last_error(const std::string& msg);

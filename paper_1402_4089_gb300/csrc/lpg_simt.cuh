@@ -411,7 +411,14 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
       // Labels of this tile: loaded now, stored with the exchange (the load's
       // latency overlaps the sweep).
       int ylv = 0;
-      if (tid < BM && tid < rv) ylv = __ldg(A.y + row0_of(t) + tid);
+      if (tid < BM && tid < rv) {
+        ylv = __ldg(A.y + row0_of(t) + tid);
+        // A label outside the classes is reported, not used as a lane index.
+        if (ylv < 0 || ylv >= A.Km1 + A.zlogit) {
+          err |= ERR_BAD_LABEL;
+          ylv = 0;
+        }
+      }
       if (!mbar_wait_cta(&full[slot], uint32_t((t / NSTAGE) & 1), lim)) {
         err |= ERR_TIMEOUT_STAGE;
         lim = 0;
@@ -580,6 +587,7 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
     }
     double lacc = 0.0;
     const int Km1 = A.Km1, chains = A.chains;
+    const bool zl = A.zlogit != 0;
     int W = 1;
     while (W < Km1) W <<= 1;
     const int RPW = 32 / W, sl = lane % W;
@@ -627,12 +635,14 @@ __device__ __forceinline__ void lpg_body(const LpgArgs& A, const int cl) {
           for (int r = 0; r < 16; ++r)
             if (r < S) z += zr[r];
         }
-        AT mx = cls ? max(z, AT(0)) : AT(0);
+        // With the zero logit of class K the row maximum includes 0 and the sum
+        // e^{-m}; without it (unconstrained layout) only the Km1 free logits count.
+        AT mx = cls ? (zl ? max(z, AT(0)) : z) : (zl ? AT(0) : AT(-INFINITY));
         for (int o = W / 2; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o, W));
         const AT e = cls ? ex<AT>(z - mx) : AT(0);
         AT se = e;
         for (int o = W / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o, W);
-        se += ex<AT>(-mx);
+        if (zl) se += ex<AT>(-mx);
         const int yi = valid ? ylab[buf * BM + i] : 0;
         const AT zy = __shfl_sync(0xffffffffu, z, yi < Km1 ? yi : 0, W);
         if (cls) rsb[size_t(i) * CTP + cb + sl] = valid ? (sl == yi ? AT(1) : AT(0)) - e / se : AT(0);

@@ -77,6 +77,7 @@ struct TcArgs {
   long long spin_limit;
   int32_t inject_timeout;
   int32_t fp8;
+  int32_t zlogit;           // 1: class K is the implied zero logit; 0: all Km1 classes free
   // Pipeline depths (host-chosen from the TMEM and shared-memory budgets):
   int32_t nz;      // logit accumulators in TMEM (sweep 1 of the next tiles runs while one drains)
   int32_t slots;   // partial-logit receive slots (reuse gated by a cluster 'consumed' barrier)
@@ -163,6 +164,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
   const uint32_t rank = (S > 1) ? cluster_rank() : 0u;
   const int RS = kRows / S;                        // rows this CTA owns in the exchange
   const int chains = A.chains, C = A.C, Km1 = A.Km1;
+  const bool zl = A.zlogit != 0;
   const int C8 = (C + 7) / 8;                      // 16-byte chunks of one R row
   constexpr bool fp8 = kFP8;
   const int NZ = A.nz, SLOTS = A.slots, RBUFS = A.rbufs, LA = A.la;
@@ -555,8 +557,10 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
                 asm volatile("ld.shared.f32 %0, [%1];" : "=f"(t) : "r"(zsl_s + uint32_t(((pr * RS + il[g]) * N + cb[g] + lane) * 4)));
                 z[g] += t;
               }
+        // With the zero logit of class K the row maximum includes 0 and the sum
+        // e^{-m}; without it (unconstrained layout) only the Km1 free logits count.
 #pragma unroll
-        for (int g = 0; g < kG; ++g) mx[g] = (lane < Km1) ? fmaxf(z[g], 0.f) : 0.f;
+        for (int g = 0; g < kG; ++g) mx[g] = (lane < Km1) ? (zl ? fmaxf(z[g], 0.f) : z[g]) : (zl ? 0.f : -INFINITY);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -572,7 +576,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& A, const int cl) {
           for (int g = 0; g < kG; ++g) se[g] += __shfl_xor_sync(0xffffffffu, se[g], o);
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
-          se[g] += expf(-mx[g]);
+          if (zl) se[g] += expf(-mx[g]);
           const bool valid = yi[g] >= 0;
           zy[g] = __shfl_sync(0xffffffffu, z[g], (valid && yi[g] < Km1) ? yi[g] : 0);
           if (act[g] && lane < Km1)
@@ -916,6 +920,7 @@ static tc::TcArgs make_args(const TcPlan& pl, const TcLaunch& L) {
   a.err = L.err;
   a.spin_limit = L.spin_limit;
   a.inject_timeout = L.inject_timeout;
+  a.zlogit = L.zlogit;
   a.nz = pl.nz;
   a.slots = pl.slots;
   a.rbufs = pl.rbufs;

@@ -111,12 +111,20 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
   const size_t o_beta = off;    off = al256(off + elems * sizeof(float));
   const size_t o_grad = off;    off = al256(off + elems * sizeof(float));
   const size_t fixed = off;
+  // Every cluster of the fused pass writes one partial gradient slice (C x ldx
+  // floats), so the array also caps the clusters launched, at about
+  // 16 MiB / (4 C ldx) - 2.  Within the tile limits (C <= 12 columns up to
+  // ldx = 20480, C <= 20 up to 10240) that is at least 15 slices, more than the
+  // 7-9 clusters that fit the GPU at the widest tiles; it can bind only for
+  // narrower problems with many row tiles and many resident clusters, which
+  // then run on fewer clusters than the occupancy limit allows.
   const size_t per_cluster = al256(elems * sizeof(float)) + al256(size_t(chains) * sizeof(double));
-  if (fixed + per_cluster > kScratchBytes)
+  const int64_t nclu_cap = fixed < kScratchBytes ? int64_t((kScratchBytes - fixed) / per_cluster) : 0;
+  if (nclu_cap < 1)
     return nfail(HMC_EINVAL, "problem needs " + std::to_string(fixed + per_cluster) +
                                  " bytes of scratch; the static maximum is " + std::to_string(kScratchBytes));
   int64_t nclu = std::min<int64_t>(maxclu, std::max<int64_t>(ntiles, 1));
-  nclu = std::min<int64_t>(nclu, int64_t((kScratchBytes - fixed) / per_cluster));
+  nclu = std::min<int64_t>(nclu, nclu_cap);
   const size_t o_gpart = off;   off = al256(off + size_t(nclu) * elems * sizeof(float));
   const size_t o_lpart = off;   off = al256(off + size_t(nclu) * chains * sizeof(double));
   if (off > kScratchBytes) return nfail(HMC_EINVAL, "scratch layout exceeds the static maximum");
@@ -137,7 +145,7 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
   double* lpart = reinterpret_cast<double*>(sc + o_lpart);
 
   NA_CUDA(cudaMemsetAsync(sc, 0, o_logk, stream));  // error word and tickets start at zero
-  NA_CUDA(launch_pack(HMC_F32, beta, bpad, int64_t(C), int32_t(p), int32_t(ldx), stream));
+  NA_CUDA(launch_pack(HMC_F32, beta, bpad, chains, Km1, Km1, int32_t(p), int32_t(ldx), stream));
   if (n > 0) {
     LpgArgs a{};
     a.X = X;
@@ -154,6 +162,7 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
     a.PC = PC;
     a.C = C;
     a.Km1 = Km1;
+    a.zlogit = 1;
     a.chains = chains;
     a.BM = kSimtRows;
     a.CR = kSimtRows;
@@ -184,16 +193,19 @@ extern "C" hmc_status hmc_logpost_grad_noalloc(const float* X, int64_t ldx, cons
   u.p = int32_t(p);
   u.p_pad = int32_t(ldx);
   u.Km1 = Km1;
+  u.ku = Km1;
   u.chains = chains;
   u.nblk = nblk;
   u.prior_kind = prior;
   u.prior_scale = prior_scale;
   NA_CUDA(launch_reduce_update(HMC_F32, u, UPD_SCALARS, stream));
-  NA_CUDA(launch_unpack(HMC_F32, gpad, grad, int64_t(C), int32_t(p), int32_t(ldx), stream));
+  NA_CUDA(launch_unpack(HMC_F32, gpad, grad, chains, Km1, Km1, int32_t(p), int32_t(ldx), stream));
   NA_CUDA(cudaMemcpyAsync(logpost, logk, size_t(chains) * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   int herr = 0;
   NA_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream));
   NA_CUDA(cudaStreamSynchronize(stream));
+  if (herr & ERR_BAD_LABEL)
+    return nfail(HMC_ENONFINITE, "a label outside [0, K) (error bits " + std::to_string(herr) + "); outputs are invalid");
   if (herr) return nfail(HMC_ETIMEOUT, "a bounded device wait ran out (error bits " + std::to_string(herr) + ")");
   return HMC_OK;
 }

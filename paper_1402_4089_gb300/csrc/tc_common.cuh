@@ -1,9 +1,7 @@
 // Blackwell (sm_103a) tensor-core building blocks: tcgen05 MMA with TMEM
-// accumulators, shared-memory matrix descriptors, TMEM allocation / loads,
-// and TMA tiled loads.  All inline PTX.
+// accumulators, shared-memory matrix descriptors, TMEM allocation and loads.
+// All inline PTX.
 #pragma once
-#include <cuda.h>
-
 #include "device_common.cuh"
 
 namespace hmc {
@@ -87,21 +85,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-// TMA: 2-D tiled load of the box at (c0 inner, c1 outer) into shared memory.
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-      "[%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* tm) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 }  // namespace tc
 }  // namespace hmc

@@ -212,7 +212,11 @@ __global__ void __launch_bounds__(kThreads) select_kernel(const UpdateArgs A, un
   ST* out = nullptr;
   if (A.samples && ((li + 1) % A.thin) == 0) {
     const int64_t slot = (li + 1) / A.thin - 1;
-    out = static_cast<ST*>(A.samples) + size_t(slot) * A.sample_slot_stride + size_t(c) * A.Km1 * A.p;
+    out = static_cast<ST*>(A.samples) + size_t(slot) * A.sample_slot_stride + size_t(c) * A.ku * A.p;
+    // Rows past the free ones (the masked row K) are zero in every sample.
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < int64_t(A.ku - A.Km1) * A.p;
+         e += int64_t(gridDim.x) * blockDim.x)
+      out[size_t(A.Km1) * A.p + size_t(e)] = ST(0);
   }
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < per_chain;
        e += int64_t(gridDim.x) * blockDim.x) {
@@ -254,21 +258,27 @@ __global__ void leap_start_kernel(const UpdateArgs A, int64_t total) {
   }
 }
 
+// [chains][ku][p] -> [chains][km1][p_pad]: rows past km1 of a chain are dropped,
+// padding columns are zero.
 template <typename T>
-__global__ void pack_kernel(const T* src, T* dst, int64_t rows, int32_t p, int32_t p_pad) {
-  const int64_t total = rows * p_pad;
+__global__ void pack_kernel(const T* src, T* dst, int64_t chains, int32_t ku, int32_t km1, int32_t p, int32_t p_pad) {
+  const int64_t total = chains * km1 * p_pad;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = i / p_pad, j = i - r * p_pad;
-    dst[i] = (j < p) ? src[r * p + j] : T(0);
+    const int64_t c = r / km1, k = r - c * km1;
+    dst[i] = (j < p) ? src[(c * ku + k) * p + j] : T(0);
   }
 }
 
+// [chains][km1][p_pad] -> [chains][ku][p]: rows past km1 of a chain are zero.
 template <typename T>
-__global__ void unpack_kernel(const T* src, T* dst, int64_t rows, int32_t p, int32_t p_pad) {
-  const int64_t total = rows * p;
+__global__ void unpack_kernel(const T* src, T* dst, int64_t chains, int32_t ku, int32_t km1, int32_t p,
+                              int32_t p_pad) {
+  const int64_t total = chains * ku * p;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = i / p, j = i - r * p;
-    dst[i] = src[r * p_pad + j];
+    const int64_t c = r / ku, k = r - c * ku;
+    dst[i] = (k < km1) ? src[(c * km1 + k) * p_pad + j] : T(0);
   }
 }
 
@@ -384,21 +394,27 @@ cudaError_t launch_leap_start(int st, const UpdateArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s) {
-  const int g = grid_for(rows * p_pad);
+cudaError_t launch_pack(int st, const void* src, void* dst, int64_t chains, int32_t ku, int32_t km1, int32_t p,
+                        int32_t p_pad, cudaStream_t s) {
+  const int g = grid_for(chains * km1 * p_pad);
   if (st == HMC_F64)
-    pack_kernel<double><<<g, kThreads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), rows, p, p_pad);
+    pack_kernel<double><<<g, kThreads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), chains, ku,
+                                               km1, p, p_pad);
   else
-    pack_kernel<float><<<g, kThreads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), rows, p, p_pad);
+    pack_kernel<float><<<g, kThreads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), chains, ku, km1,
+                                              p, p_pad);
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(int st, const void* src, void* dst, int64_t rows, int32_t p, int32_t p_pad, cudaStream_t s) {
-  const int g = grid_for(rows * p);
+cudaError_t launch_unpack(int st, const void* src, void* dst, int64_t chains, int32_t ku, int32_t km1, int32_t p,
+                          int32_t p_pad, cudaStream_t s) {
+  const int g = grid_for(chains * ku * p);
   if (st == HMC_F64)
-    unpack_kernel<double><<<g, kThreads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), rows, p, p_pad);
+    unpack_kernel<double><<<g, kThreads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), chains, ku,
+                                                 km1, p, p_pad);
   else
-    unpack_kernel<float><<<g, kThreads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), rows, p, p_pad);
+    unpack_kernel<float><<<g, kThreads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), chains, ku,
+                                                km1, p, p_pad);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ STATUS_NAMES = ["HMC_OK", "HMC_EINVAL", "HMC_ENOMEM", "HMC_ECUDA", "HMC_ETIMEOUT
 F64, F32, BF16, FP8E4M3 = range(4)
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, "fp8": FP8E4M3}
 PRIORS = {"gaussian": 0, "cauchy": 1}
+LAYOUTS = {"free": 0, "masked": 1, "unconstrained": 2}
 
 
 class HmcError(RuntimeError):
@@ -34,7 +35,7 @@ class HmcError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("x_storage", ctypes.c_int), ("state", ctypes.c_int), ("max_chains", ctypes.c_int32),
                 ("engine", ctypes.c_int32), ("spin_limit", ctypes.c_int64), ("stream", ctypes.c_void_p),
-                ("tile", ctypes.c_int32 * 4)]
+                ("tile", ctypes.c_int32 * 4), ("layout", ctypes.c_int32)]
 
 
 class ChainStats(ctypes.Structure):
@@ -71,6 +72,8 @@ def lib():
         "hmc_sample": (st, [P, I32, I32, D, I64, U64, P, P, I32, P]),
         "hmc_sample_tempered": (st, [P, I32, I32, D, I64, U64, P, P, I32, P, P]),
         "hmc_get_state": (st, [P, I32, P, P, P, P]),
+        "hmc_annealing_schedule": (st, [D, D, I64, P]),
+        "hmc_predict": (st, [P, I32, P, I64, P, ctypes.c_int, I64, P, P]),
         "hmc_get_x": (st, [P, I32, P, P]),
         "hmc_state_save": (st, [P, ctypes.c_char_p]),
         "hmc_state_load": (st, [P, ctypes.c_char_p]),
@@ -121,8 +124,9 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
-def _make_opts(x_storage, state, max_chains, engine, spin_limit, stream, tile):
+def _make_opts(x_storage, state, max_chains, engine, spin_limit, stream, tile, layout="free"):
     o = default_opts()
+    o.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
     o.x_storage = DTYPES[x_storage] if isinstance(x_storage, str) else int(x_storage)
     o.state = DTYPES[state] if isinstance(state, str) else int(state)
     o.max_chains = int(max_chains)
@@ -147,12 +151,18 @@ def _x_in_dtype(X):
 class Handle:
     """One uploaded problem (or batch of problems) and its persistent chain state."""
 
-    def __init__(self, ptr, keep, shapes, state, max_chains):
+    def __init__(self, ptr, keep, shapes, state, max_chains, layout=0):
         self._h = ctypes.c_void_p(ptr)
         self._keep = keep
         self.shapes = shapes            # [(n, p, K)]
         self.state = state
         self.max_chains = max_chains
+        self.layout = layout
+
+    def rows(self, b=0):
+        """Coefficient rows per chain of problem b in the beta layout (K-1, or K for the
+        masked and unconstrained layouts)."""
+        return self.shapes[b][2] - (1 if self.layout == LAYOUTS["free"] else 0)
 
     # -- plumbing
     def close(self):
@@ -226,6 +236,26 @@ class Handle:
         return [dict(iterations=s.iterations, accepted=s.accepted, diverged=s.diverged, sum_abs_dH=s.sum_abs_dH,
                      logpost=s.logpost) for s in stats]
 
+    def predict(self, draws, Xnew, b=0, prob=None, cls=None):
+        """Posterior predictive (hmc_predict): mean softmax over the coefficient draws
+        ([ndraws][rows][p] of the state type) for the rows of Xnew, and its argmax.
+        Outputs are allocated like Xnew (numpy or the same device) unless given."""
+        n, p, K = self.shapes[b]
+        ndraws, r = divmod(draws.numel() if hasattr(draws, "numel") else draws.size, self.rows(b) * p)
+        if r or ndraws < 1:
+            raise ValueError("draws must hold whole coefficient states of problem b")
+        n_new = int(Xnew.shape[0])
+        if prob is None and cls is None:
+            if isinstance(Xnew, np.ndarray):
+                prob, cls = np.empty((n_new, K), np.float64), np.empty(n_new, np.int32)
+            else:
+                import torch
+                prob = torch.empty((n_new, K), dtype=torch.float64, device=Xnew.device)
+                cls = torch.empty(n_new, dtype=torch.int32, device=Xnew.device)
+        _check(lib().hmc_predict(self._h, int(b), _ptr(draws), int(ndraws), _ptr(Xnew), _x_in_dtype(Xnew), n_new,
+                                 _ptr(prob), _ptr(cls)))
+        return prob, cls
+
     def get_state(self, chains, beta=None, grad=None, logpost=None):
         nxt = ctypes.c_int64(0)
         _check(lib().hmc_get_state(self._h, chains, _ptr(beta), _ptr(grad), _ptr(logpost), ctypes.byref(nxt)))
@@ -285,22 +315,24 @@ class Handle:
 
 
 def create(X, y, K, prior="gaussian", prior_scale=1.0, x_storage="f32", state="f32", max_chains=1, engine=0,
-           spin_limit=0, stream=None, tile=None):
-    """Upload one problem (X: float32/float64 n x p, host numpy or device tensor; y: int32)."""
-    o = _make_opts(x_storage, state, max_chains, engine, spin_limit, stream, tile)
+           spin_limit=0, stream=None, tile=None, layout="free"):
+    """Upload one problem (X: float32/float64 n x p, host numpy or device tensor; y: int32).
+    ``layout``: "free" (K-1 rows per chain), "masked" (K rows, row K held at zero) or
+    "unconstrained" (K free rows)."""
+    o = _make_opts(x_storage, state, max_chains, engine, spin_limit, stream, tile, layout)
     n, p = int(X.shape[0]), int(X.shape[1])
     h = ctypes.c_void_p()
     _check(lib().hmc_create(_ptr(X), _x_in_dtype(X), _ptr(y), n, p, int(K), PRIORS[prior], float(prior_scale),
                             ctypes.byref(o), ctypes.byref(h)))
-    hd = Handle(h.value, None, [(n, p, int(K))], o.state, int(max_chains))
+    hd = Handle(h.value, None, [(n, p, int(K))], o.state, int(max_chains), o.layout)
     hd._x_storage = o.x_storage
     return hd
 
 
 def create_batch(Xs, ys, Ks, prior="gaussian", prior_scale=1.0, x_storage="f32", state="f32", max_chains=1,
-                 engine=0, spin_limit=0, stream=None, tile=None):
+                 engine=0, spin_limit=0, stream=None, tile=None, layout="free"):
     """Upload several independent problems into one handle."""
-    o = _make_opts(x_storage, state, max_chains, engine, spin_limit, stream, tile)
+    o = _make_opts(x_storage, state, max_chains, engine, spin_limit, stream, tile, layout)
     m = len(Xs)
     xin = {_x_in_dtype(X) for X in Xs}
     if len(xin) != 1:
@@ -314,21 +346,17 @@ def create_batch(Xs, ys, Ks, prior="gaussian", prior_scale=1.0, x_storage="f32",
     _check(lib().hmc_create_batch(m, Xp, xin.pop(), yp, ns, ps, ks, PRIORS[prior], float(prior_scale),
                                   ctypes.byref(o), ctypes.byref(h)))
     hd = Handle(h.value, None, [(int(X.shape[0]), int(X.shape[1]), int(k)) for X, k in zip(Xs, Ks)], o.state,
-                int(max_chains))
+                int(max_chains), o.layout)
     hd._x_storage = o.x_storage
     return hd
 
 
 def annealing_temperatures(iters, t0=1.0e3, r=0.9):
     """Acceptance temperatures of the annealed burn-in of Sec. 3.2 for `iters`
-    iterations: T_t = max(1, r T_{t-1}) with T_0 = t0, iteration t (1-based)
-    accepting at T_t; once T reaches 1 it stays there.  Pass the result as
-    ``temps`` to ``Handle.sample``."""
+    iterations (hmc_annealing_schedule); pass the result as ``temps`` to
+    ``Handle.sample``."""
     out = np.empty(int(iters), dtype=np.float64)
-    t = float(t0)
-    for i in range(out.size):
-        t = max(1.0, r * t)
-        out[i] = t
+    _check(lib().hmc_annealing_schedule(float(t0), float(r), int(iters), out.ctypes.data if out.size else None))
     return out
 
 

@@ -73,3 +73,28 @@ def test_checkpoint_errors(cuda, tmp_path):
         with pytest.raises(hmc.HmcError) as e:
             h5.load_state(path)                                # truncated
         assert e.value.status == hmc.EINVAL
+
+
+def test_checkpoint_of_another_posterior_is_rejected(cuda, tmp_path):
+    """A checkpoint loads only into a handle of the same posterior: the prior,
+    the storage of X and the layout are in its header, and the saved gradient and
+    log K must agree with the handle's own at the saved coefficients (another X or
+    other labels of the same shape do not)."""
+    X, y, _ = synthetic.make_problem(300, 40, 3, seed=5)
+    path = str(tmp_path / "c.ckpt")
+    with hmc.create(X, y, 3, "gaussian", 10.0, max_chains=2) as h:
+        h.sample(2, 3, 0.01, 2, 1)
+        h.save_state(path)
+    X2, y2, _ = synthetic.make_problem(300, 40, 3, seed=6)           # same shape, other data
+    cases = [dict(X=X, y=y, prior=("gaussian", 5.0)), dict(X=X, y=y, prior=("cauchy", 10.0)),
+             dict(X=X, y=y, prior=("gaussian", 10.0), x_storage="bf16"),
+             dict(X=X, y=y, prior=("gaussian", 10.0), layout="masked"),
+             dict(X=X2, y=y2, prior=("gaussian", 10.0)), dict(X=X, y=y2, prior=("gaussian", 10.0))]
+    for kw in cases:
+        extra = {k: v for k, v in kw.items() if k in ("x_storage", "layout")}
+        with hmc.create(kw["X"], kw["y"], 3, kw["prior"][0], kw["prior"][1], max_chains=2, **extra) as h2:
+            with pytest.raises(hmc.HmcError) as e:
+                h2.load_state(path)
+            assert e.value.status == hmc.EINVAL, kw
+    with hmc.create(X, y, 3, "gaussian", 10.0, max_chains=2, tile=(2, 0, 0, 3)) as h3:
+        h3.load_state(path)          # the same posterior on another tile loads (not bitwise-continuing)
