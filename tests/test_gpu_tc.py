@@ -1,22 +1,25 @@
 """Tensor-core engine (tcgen05, BF16 or per-column-scaled FP8 X) against the
 FP64 oracle on the same stored values (FP8: the dequantised codes x_q s_j).
-The MMA operands are BF16 (coefficients, with FP8 column scales folded in,
-and the residual are rounded to BF16 before the contractions; accumulation is
-FP32 in TMEM), so the tolerance is the BF16 bar: gradient relative error
-<= 1e-2 and log K relative error <= 1e-3."""
+
+The MMA operands are BF16: the coefficients enter as two BF16 terms (hi + lo,
+about 16 bits), the residual R = Y - P as one BF16 term (relative rounding
+error <= 2^-9 per entry), accumulation is FP32 in TMEM.  The gradient's
+arithmetic error against the oracle on the stored X is therefore dominated by
+the rounding of R: about 2^-9 / sqrt(3) ~ 1.1e-3 relative for independent
+roundings, so the gate is 3e-3 (relative norm and element-wise), log K 1e-4.
+The total error against the original X (BF16 storage adds a 2^-9 relative
+rounding of every x_ij) is held to the BF16 bar of 1e-2."""
 import numpy as np
 import pytest
 
 from oracle import model, quant
 from paper_1402_4089_gb300 import hmc, synthetic
+from parity_util import grad_errs, lk_err
 
 pytestmark = pytest.mark.gpu
 
-TOL_G, TOL_L = 1e-2, 1e-3
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+TOL_G, TOL_L = 3e-3, 1e-4
+TOL_TOTAL_BF16 = 1e-2
 
 
 def _run(cuda, n, p, K, chains, seed, bscale=0.05, tile=None, prior=("gaussian", 10.0), storage="bf16"):
@@ -42,16 +45,18 @@ def _run(cuda, n, p, K, chains, seed, bscale=0.05, tile=None, prior=("gaussian",
     for c in range(chains):
         lk_o = model.log_kernel(Xq, y, beta[c], prior[0], prior[1])
         g_o = model.grad_log_kernel(Xq, y, beta[c], prior[0], prior[1])
-        errs.append((abs(lp[c] - lk_o) / max(1.0, abs(lk_o)), _rel(g[c], g_o)))
+        g_t = model.grad_log_kernel(X.astype(np.float64), y, beta[c], prior[0], prior[1])   # original X
+        errs.append((lk_err(lp[c], lk_o),) + grad_errs(g[c], g_o) + (max(grad_errs(g[c], g_t)),))
     return d, errs
 
 
 @pytest.mark.parametrize("n,p,K,chains,S", [(1000, 700, 6, 2, 0), (333, 129, 3, 1, 1), (2049, 1000, 20, 4, 0),
-                                            (128, 64, 2, 3, 2), (5000, 2000, 10, 7, 4)])
+                                            (128, 64, 2, 3, 2), (5000, 2000, 10, 7, 4), (130, 4100, 5, 1, 16)])
 def test_tc_matches_oracle(cuda, n, p, K, chains, S):
     d, errs = _run(cuda, n, p, K, chains, seed=n + p, tile=(S, 0, 0, 0))
-    for c, (el, eg) in enumerate(errs):
-        assert el <= TOL_L and eg <= TOL_G, (d["problems"][0], c, el, eg)
+    for c, (el, eg, ee, et) in enumerate(errs):
+        assert el <= TOL_L and eg <= TOL_G and ee <= TOL_G, (d["problems"][0], c, el, eg, ee)
+        assert et <= TOL_TOTAL_BF16, (d["problems"][0], c, "total error vs original X", et)
 
 
 def test_tc_deterministic(cuda):
@@ -68,8 +73,11 @@ def test_tc_deterministic(cuda):
                                             (5000, 2000, 10, 7, 4)])
 def test_tc_fp8_matches_oracle(cuda, n, p, K, chains, S):
     d, errs = _run(cuda, n, p, K, chains, seed=n + 3 * p, tile=(S, 0, 0, 0), storage="fp8")
-    for c, (el, eg) in enumerate(errs):
-        assert el <= TOL_L and eg <= TOL_G, (d["problems"][0], c, el, eg)
+    for c, (el, eg, ee, et) in enumerate(errs):
+        assert el <= TOL_L and eg <= TOL_G and ee <= TOL_G, (d["problems"][0], c, el, eg, ee)
+        # total error of E4M3 storage (3 mantissa bits) against the original X: reported, aim <= 3e-2
+        print(f"fp8 total error n={n} p={p} K={K} chain {c}: {et:.3e}")
+        assert et <= 0.1, et
 
 
 def test_tc_fp8_deterministic(cuda):
@@ -112,8 +120,8 @@ def test_tc_batch_of_uneven_problems_one_launch(cuda, storage):
         for c in range(chains):
             lk_o = model.log_kernel(Xq, y, betas[b][c], "gaussian", 10.0)
             g_o = model.grad_log_kernel(Xq, y, betas[b][c], "gaussian", 10.0)
-            assert abs(lp[b * chains + c] - lk_o) / max(1.0, abs(lk_o)) <= TOL_L, (b, c)
-            assert _rel(gb[c], g_o) <= TOL_G, (b, c, _rel(gb[c], g_o))
+            assert lk_err(lp[b * chains + c], lk_o) <= TOL_L, (b, c)
+            assert max(grad_errs(gb[c], g_o)) <= TOL_G, (b, c, grad_errs(gb[c], g_o))
 
 
 def test_tc_chain_groups_are_even(cuda):
@@ -138,4 +146,4 @@ def test_tc_chain_groups_are_even(cuda):
     for c in (0, 7, 8, 15):
         lk_o = model.log_kernel(Xq, y, beta[c], "gaussian", 10.0)
         g_o = model.grad_log_kernel(Xq, y, beta[c], "gaussian", 10.0)
-        assert abs(lp[c] - lk_o) / max(1.0, abs(lk_o)) <= TOL_L and _rel(g[c], g_o) <= TOL_G, c
+        assert lk_err(lp[c], lk_o) <= TOL_L and max(grad_errs(g[c], g_o)) <= TOL_G, (c, grad_errs(g[c], g_o))
