@@ -58,21 +58,22 @@ def _store(d):
         pass
 
 
-def time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, engine, tile, stream=None, reps=5, warmup=2):
+def time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, engine, tile, stream=None, reps=5, warmup=2,
+              layout="free"):
     """Median time (us) of the fused launches of one log-posterior + gradient call for all
     `chains` (a tile may split the chains into several launches), or None if the library
     rejects the tile."""
     import torch
     try:
         h = hmc.create(X, y, K, prior, prior_scale, x_storage=x_storage, state=state, max_chains=chains,
-                       engine=engine, stream=stream, tile=tile)
+                       engine=engine, stream=stream, tile=tile, layout=layout)
     except hmc.HmcError:
         return None, None
     try:
         d = h.describe()
         dev = torch.device("cuda", torch.cuda.current_device())
         p = int(X.shape[1])
-        beta = torch.zeros((chains, K - 1, p), dtype=h.torch_dtype(), device=dev)
+        beta = torch.zeros((chains, h.rows(), p), dtype=h.torch_dtype(), device=dev)
         for _ in range(warmup):
             h.logpost_grad(beta)
         times = []
@@ -89,7 +90,7 @@ def time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, engine, til
 
 
 def autotune(X, y, K, prior="gaussian", prior_scale=1.0, x_storage="f32", state="f32", chains=1, engine=0,
-             stream=None, reps=5, use_cache=True, verbose=False):
+             stream=None, reps=5, use_cache=True, verbose=False, layout="free"):
     """Fastest (engine, tile) for this problem: returns (engine, tile tuple for hmc.create, table of
     measurements); (engine, None, table) when no explicit tile runs."""
     import torch
@@ -98,7 +99,8 @@ def autotune(X, y, K, prior="gaussian", prior_scale=1.0, x_storage="f32", state=
         engines = (engine,)
     else:
         engines = (2, 1) if x_storage in ("bf16", "fp8") else (1,)
-    key = _key(torch.cuda.get_device_name(), n, p, K, x_storage, state, chains, engine)
+    key = _key(torch.cuda.get_device_name(), n, p, K, x_storage, state, chains, engine) + \
+        ("" if layout == "free" else f"|layout={layout}")
     cache = _load() if use_cache else {}
     if key in cache:
         e = cache[key]
@@ -108,7 +110,7 @@ def autotune(X, y, K, prior="gaussian", prior_scale=1.0, x_storage="f32", state=
         for S in (TC_S if eng == 2 else SIMT_S):
             for ns in RING:
                 us, d = time_tile(X, y, K, prior, prior_scale, x_storage, state, chains, eng, (S, 0, 0, ns),
-                                  stream=stream, reps=reps)
+                                  stream=stream, reps=reps, layout=layout)
                 if us is None:
                     continue
                 pr = d["problems"][0]
