@@ -39,6 +39,8 @@ KERNEL_SOURCES = {
     "simt": ["paper_1402_4089_gb300/csrc/lpg_simt.cuh", "paper_1402_4089_gb300/csrc/device_common.cuh"],
     "tcgen05": ["paper_1402_4089_gb300/csrc/lpg_tc.cu", "paper_1402_4089_gb300/csrc/tc_common.cuh",
                 "paper_1402_4089_gb300/csrc/device_common.cuh"],
+    "tcgen05_2pass": ["paper_1402_4089_gb300/csrc/lpg_tc2.cu", "paper_1402_4089_gb300/csrc/tc_common.cuh",
+                      "paper_1402_4089_gb300/csrc/device_common.cuh"],
 }
 
 

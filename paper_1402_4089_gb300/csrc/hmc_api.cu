@@ -88,9 +88,11 @@ struct Problem {
   int64_t* iter = nullptr;  // [3]: global iteration, local iteration, generator seed
   int nblk = 1;
   int64_t state_elems = 0;  // max_chains * Km1 * p_pad
-  // tensor-core engine
-  int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel
+  // tensor-core engines
+  int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel, 3 tensor-core two-pass
   TcPlan tp{};
+  Tc2Plan tp2{};            // engine 3
+  void* rbuf = nullptr;     // engine 3: residual boxes written by pass A, read by pass B
   void* bbf = nullptr;      // BF16 coefficient operand boxes [p_pad / 64][2N x 128 B] (hi, lo terms)
   int nlparts = 0;          // log-likelihood partials reduced per chain
 };
@@ -310,10 +312,44 @@ hmc_status choose_tc(hmc_ctx* h, Problem& P, bool* ok) {
 hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, const int32_t* y) {
   const int xb = dtype_bytes(h->xt);
   bool tc_ok = false;
-  if ((h->xt == HMC_BF16 || h->xt == HMC_FP8E4M3) && h->engine != 1 && P.n > 0) HMC_TRY(choose_tc(h, P, &tc_ok));
+  if ((h->xt == HMC_BF16 || h->xt == HMC_FP8E4M3) && (h->engine == 0 || h->engine == 2) && P.n > 0)
+    HMC_TRY(choose_tc(h, P, &tc_ok));
   if (h->engine == 2 && !tc_ok)
     return fail(HMC_EUNSUPPORTED, "the tensor-core engine needs BF16 or FP8 storage of X, n > 0 and chains * (K-1) "
                                   "columns that fit TMEM next to the cluster's gradient slice");
+  // Two-pass tensor-core engine: on request, or by default (BF16 X) when the
+  // fused engine cannot take every chain in one launch (each launch would
+  // stream X again) or cannot run the problem at all.
+  const bool want2 = h->xt == HMC_BF16 && P.n > 0 && P.Km1 <= 32 &&
+                     (h->engine == 3 || (h->engine == 0 && !h->tile[0] && (!tc_ok || P.group_chains < h->max_chains)));
+  if (want2) {
+    int dev = 0, nsm = 0, smem_max = 0;
+    HMC_CUDA(cudaGetDevice(&dev));
+    HMC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    Tc2Plan p2;
+    if (tc2_plan(P.n, P.p, P.Km1, h->max_chains, nsm, smem_max, &p2)) {
+      HMC_CUDA(tc2_prepare());
+      P.engine = 3;
+      P.tp2 = p2;
+      P.group_chains = h->max_chains;
+      P.ct_launch = h->max_chains * P.Km1;
+      P.S = 1;
+      P.PC = p2.p_pad;
+      P.p_pad = p2.p_pad;
+      P.BM = 128;
+      P.CR = 128;
+      P.NT = tc2_threads();
+      P.NSTAGE = p2.nstA;
+      P.smem = p2.smemA;
+      P.ntiles = (P.n + 127) / 128;
+      P.nclusters = p2.Q;           // partial gradient slices reduced per gradient
+      tc_ok = true;
+    }
+  }
+  if (h->engine == 3 && P.engine != 3)
+    return fail(HMC_EUNSUPPORTED, "the two-pass tensor-core engine needs BF16 storage of X, n > 0 and at most 32 free "
+                                  "classes per chain");
   if (!tc_ok) {
     const int maxct = simt_max_ct(h->xt);
     if (P.Km1 > maxct)
@@ -358,7 +394,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(cudaMemcpyAsync(tmp, X, in_bytes, cudaMemcpyHostToDevice, h->stream));
     Xd = tmp;
   }
-  const int64_t n_alloc = P.engine == 2 ? (P.n + 127) / 128 * 128 : P.n;
+  const int64_t n_alloc = P.engine >= 2 ? (P.n + 127) / 128 * 128 : P.n;
   HMC_CUDA(cudaMalloc(&P.X, std::max<size_t>(16, size_t(n_alloc) * P.p_pad * xb)));
   if (h->xt == HMC_FP8E4M3) {
     HMC_CUDA(cudaMalloc(&P.xscale, size_t(P.p_pad) * sizeof(float)));
@@ -367,7 +403,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   if (P.n > 0) {
     if (P.engine == 2 && h->xt == HMC_FP8E4M3)
       HMC_CUDA(tc_x_to_tiles_fp8(x_dtype, Xd, P.xscale, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
-    else if (P.engine == 2)
+    else if (P.engine >= 2)
       HMC_CUDA(tc_x_to_tiles(x_dtype, Xd, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
     else
       HMC_CUDA(launch_convert_x(x_dtype, Xd, h->xt, P.X, P.xscale, P.n, P.p, P.p_pad, h->err_d, h->stream));
@@ -384,8 +420,16 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   const size_t sb = state_bytes(h);
   P.state_elems = int64_t(h->max_chains) * P.Km1 * P.p_pad;
   HMC_CUDA(cudaMalloc(&P.gpart, size_t(P.nclusters) * P.state_elems * sb));
-  P.nlparts = P.engine == 2 ? P.nclusters * P.S : P.nclusters;
+  P.nlparts = P.engine == 2 ? P.nclusters * P.S : P.engine == 3 ? P.tp2.gridA : P.nclusters;
   HMC_CUDA(cudaMalloc(&P.lpart, size_t(P.nlparts) * h->max_chains * sizeof(double)));
+  if (P.engine == 3) {
+    const Tc2Plan& t2 = P.tp2;
+    const int64_t ngroups = (h->max_chains + t2.gc - 1) / t2.gc;
+    const size_t bbytes = size_t(ngroups) * (t2.p_pad / 64) * 2 * t2.N * 128;
+    HMC_CUDA(cudaMalloc(&P.bbf, bbytes));
+    HMC_CUDA(cudaMemsetAsync(P.bbf, 0, bbytes, h->stream));
+    HMC_CUDA(cudaMalloc(&P.rbuf, size_t(P.ntiles) * ngroups * t2.NB * 16384));
+  }
   if (P.engine == 2) {
     const TcPlan& tp = P.tp;
     HMC_CUDA(cudaMalloc(&P.bbf, size_t(2 * tp.N) * P.p_pad * 2));     // hi and lo terms
@@ -415,7 +459,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
 void free_problem(Problem& P) {
   void* ptrs[] = {P.X, P.y, P.xscale, P.gpart, P.lpart, P.cs.beta, P.cs.eta, P.cs.grad, P.cs.beta0, P.cs.grad0,
                   P.us.beta, P.us.eta, P.us.grad, P.us.beta0, P.us.grad0, P.logk, P.logk0, P.h0, P.scal,
-                  P.tickets, P.accept, P.stats, P.iter, P.bbf};
+                  P.tickets, P.accept, P.stats, P.iter, P.bbf, P.rbuf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -452,6 +496,45 @@ hmc_status timer_harvest(hmc_ctx* h) {
 hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t stream) {
   if (P.n == 0) return HMC_OK;
   const size_t sb = state_bytes(h);
+  if (P.engine == 3) {
+    // Both passes for every chain of the call (the chain groups are inside the launches).
+    const Tc2Plan& t2 = P.tp2;
+    const int ngroups = (chains + t2.gc - 1) / t2.gc;
+    HMC_CUDA(tc2_beta_boxes(static_cast<const float*>(S.beta), P.bbf, P.Km1, t2.gc, chains, t2.N, t2.p_pad, ngroups,
+                            stream));
+    const bool inject = h->inject_timeout;
+    h->inject_timeout = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool timed = h->timing && (h->timing_seq++ % h->timing_period) == 0;
+    if (timed) {
+      HMC_CUDA(cudaStreamIsCapturing(stream, &cap));
+      HMC_TRY(timer_pair(h, &e0, &e1));
+      HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal)
+                                                    : cudaEventRecord(e0, stream));
+    }
+    Tc2Launch L{};
+    L.xs = P.X;
+    L.bs = P.bbf;
+    L.y = P.y;
+    L.rbuf = P.rbuf;
+    L.lpart = P.lpart;
+    L.lpart_cstride = h->max_chains;
+    L.gpart = P.gpart;
+    L.gpart_cstride = P.state_elems;
+    L.err = h->err_d;
+    L.n = P.n;
+    L.Km1 = P.Km1;
+    L.zlogit = P.zlogit;
+    L.chains = chains;
+    L.spin_limit = inject ? 0 : h->spin_limit;   // fault injection: every bounded wait gives up at once
+    const cudaError_t le = tc2_launch(t2, L, stream);
+    if (le != cudaSuccess) return fail(HMC_ECUDA, std::string("two-pass launch failed: ") + cudaGetErrorString(le));
+    if (timed)
+      HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
+                                                    : cudaEventRecord(e1, stream));
+    return HMC_OK;
+  }
   for (int c0 = 0; c0 < chains; c0 += P.group_chains) {
     const int c1 = std::min(chains, c0 + P.group_chains);
     const int C = (c1 - c0) * P.Km1;
@@ -794,7 +877,7 @@ hmc_status validate_opts(const hmc_opts* o) {
   if ((o->x_storage == HMC_F64) != (o->state == HMC_F64))
     return fail(HMC_EINVAL, "HMC_F64 storage of X goes with HMC_F64 state, and only with it");
   if (o->max_chains < 1 || o->max_chains > 4096) return fail(HMC_EINVAL, "opts.max_chains must be in [1, 4096]");
-  if (o->engine < 0 || o->engine > 2) return fail(HMC_EINVAL, "opts.engine must be 0, 1 or 2");
+  if (o->engine < 0 || o->engine > 3) return fail(HMC_EINVAL, "opts.engine must be 0, 1, 2 or 3");
   if (o->spin_limit < 0) return fail(HMC_EINVAL, "opts.spin_limit must be >= 0");
   const int* t = o->tile;
   if (t[0] < 0 || t[0] > 16) return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be in [0, 16]");
@@ -809,7 +892,8 @@ hmc_status validate_opts(const hmc_opts* o) {
 }
 
 void build_description(hmc_ctx* h) {
-  std::string s = "{\"engine\": \"" + std::string(h->probs.empty() || h->probs[0].engine == 1 ? "simt" : "tcgen05") +
+  const int e0 = h->probs.empty() ? 1 : h->probs[0].engine;
+  std::string s = "{\"engine\": \"" + std::string(e0 == 1 ? "simt" : e0 == 2 ? "tcgen05" : "tcgen05_2pass") +
                   "\", \"batched_launch\": " + std::string(h->batched || h->tc_batched ? "true" : "false") +
                   ", \"layout\": " + std::to_string(h->layout) +
                   ", \"x_storage\": " + std::to_string(h->xt) +
@@ -826,6 +910,15 @@ void build_description(hmc_ctx* h) {
                   P.smem, P.group_chains, P.ct_launch, P.engine == 2 ? P.tp.nz : 0, P.engine == 2 ? P.tp.slots : 0,
                   P.engine == 2 ? P.tp.la : 0);
     s += buf;
+    if (P.engine == 3) {
+      const Tc2Plan& t = P.tp2;
+      std::snprintf(buf, sizeof(buf),
+                    ", \"pass_a\": {\"grid\": %d, \"chain_group\": %d, \"N\": %d, \"ring\": %d, \"smem\": %zu}, "
+                    "\"pass_b\": {\"feature_blocks\": %d, \"feature_groups\": %d, \"row_ranges\": %d, \"ring\": %d, "
+                    "\"r_slots\": %d, \"smem\": %zu}",
+                    t.gridA, t.gc, t.N, t.nstA, t.smemA, t.MB, t.nfg, t.Q, t.nstB, t.nrsB, t.smemB);
+      s.insert(s.size() - 1, buf);   // inside this problem's object
+    }
   }
   s += "]}";
   h->desc = s;
@@ -1541,7 +1634,7 @@ hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales) {
   if (!dst) return fail(HMC_EINVAL, "dst is NULL");
   Problem& P = h->probs[b];
   const size_t xb = dtype_bytes(h->xt);
-  if (P.n > 0 && P.engine == 2) {
+  if (P.n > 0 && P.engine >= 2) {
     void* tmp = nullptr;
     HMC_CUDA(cudaMalloc(&tmp, size_t(P.n) * P.p * xb));
     cudaError_t e = tc_tiles_to_rows(P.X, tmp, P.n, P.p, P.p_pad, h->xt == HMC_FP8E4M3, h->stream);

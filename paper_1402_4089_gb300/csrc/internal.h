@@ -131,6 +131,39 @@ cudaError_t tc_beta_to_tiles_batched(const void* d_table, int m, int chains, int
 cudaError_t tc_launch_batched(const void* d_table, const int* d_first, int m, int chains, int total_clusters, int S,
                               bool fp8, size_t smem, cudaStream_t stream);
 
+// Two-pass tensor-core engine (BF16 X), lpg_tc2.cu: pass A forms the logits,
+// softmax and residual R of every (row tile, chain group) unit, pass B the
+// partial gradients X^T R of every (feature group, chain group, row range) unit.
+struct Tc2Plan {
+  int p_pad = 0;            // p rounded to 128
+  int gc = 0, N = 0, NB = 0;  // chains per group, MMA N (>= gc (K-1), multiple of 16), R boxes (64 columns)
+  int gridA = 0, nstA = 0;  // pass A CTAs and ring slots
+  size_t smemA = 0;
+  int MB = 0, nfg = 0, Q = 0;   // pass B: 128-feature blocks per CTA, feature groups, row ranges
+  int nstB = 0, nrsB = 0;   // pass B X ring slots and R slots
+  size_t smemB = 0;
+};
+struct Tc2Launch {
+  const void* xs;           // X boxes (tc_x_to_tiles layout with p_pad columns)
+  const void* bs;           // coefficient operand of every group (tc2_beta_boxes)
+  const int32_t* y;
+  void* rbuf;               // R boxes [ntiles][groups][NB][16 KB]
+  double* lpart;            // [gridA][lpart_cstride]
+  int32_t lpart_cstride;
+  void* gpart;              // [Q][chains Km1][p_pad] FP32
+  int64_t gpart_cstride;
+  int* err;
+  int64_t n;
+  int32_t Km1, zlogit, chains;
+  long long spin_limit;
+};
+bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, Tc2Plan* out);
+int tc2_threads();
+cudaError_t tc2_prepare();
+cudaError_t tc2_beta_boxes(const float* beta, void* out, int Km1, int gc, int chains, int N, int p_pad, int ngroups,
+                           cudaStream_t s);
+cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream);
+
 // Element-wise / reduction kernels (update.cu).
 struct UpdateArgs {
   void* beta;  void* eta;  void* grad;          // [chains][Km1][p_pad] state type

@@ -1,0 +1,709 @@
+// Two-pass evaluation of the log-posterior and its gradient on the tensor
+// cores (tcgen05), X stored in BF16 (Eqs. softmax, loglike, logkernel and
+// gradient of Sec. 2.1, for C = chains*(K-1) coefficient columns at once).
+//
+// The fused engine (lpg_tc.cu) keeps each CTA's gradient slice in TMEM for the
+// whole pass, which caps the chains of one launch (TMEM holds p/16 x N FP32
+// values per SM) and ties the CTAs of a cluster together through a logit
+// exchange every row tile.  Here the two contractions run as two streaming
+// passes with nothing held across tiles but the accumulators of one unit:
+//
+//  pass A  (logits, softmax, residual)  units (row tile t of 128 rows, chain
+//          group g): D[128 x N] = X_t B_g^T over all p features, B as two BF16
+//          terms (hi + lo, ~16 bits), accumulated in TMEM (two accumulators, so
+//          the epilogue of one unit overlaps the MMAs of the next).  The
+//          epilogue (one thread per row) forms the softmax of every chain with
+//          the zero logit of class K, the row log-likelihood and the residual
+//          R = Y - P, which it writes in BF16 as the MN-major, 128-byte-swizzled
+//          boxes pass B reads.  Every CTA adds its units' log-likelihoods per
+//          chain in unit order: one FP64 partial per CTA and chain.
+//  pass B  (gradient X^T R)  units (feature group f of MB blocks of 128
+//          features, chain group g, row range q): D[mb][128 features x N] +=
+//          X_blk^T R over the tiles of the range, one TMEM accumulator per
+//          feature block; written once at the end as the range's partial slice
+//          (fixed-order reduction afterwards, no atomics).
+//
+// X crosses HBM twice per gradient when it is larger than L2 (once when the
+// second pass finds it in L2); in exchange every SM streams (no cluster
+// exchange, no TMEM limit on the chains of one call) and both passes are
+// balanced over the SM count.
+//
+// Warp roles in both kernels: warp 0 bulk-copy producer (lane 0), warp 1 TMEM
+// owner and MMA issuer (lane 0), warps 2-5 epilogue (TMEM lane quarter
+// warp % 4).  Every wait is bounded; a wait that runs out sets an error bit
+// and an abort flag, and every role then leaves its loop.
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace hmc {
+namespace tc2 {
+
+using tc::fence_after_sync;
+using tc::fence_before_sync;
+using tc::idesc_bf16;
+using tc::mma_bf16;
+using tc::mma_commit;
+using tc::smem_desc;
+using tc::tmem_alloc;
+using tc::tmem_dealloc;
+using tc::tmem_ld16;
+
+constexpr int kRows = 128;
+constexpr int kBox = 64;                 // BF16 values per 128-byte row of a box
+constexpr int kBoxBytes = kRows * 128;   // one 128 x 64 BF16 box
+constexpr int kThreads = 192;
+
+__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, long long limit, volatile int* abort) {
+  const uint32_t a = smem_u32(bar);
+  for (long long i = 0; i < limit; ++i) {
+    if (mbar_test_cta(a, parity)) return true;
+    if ((i & 63) == 63 && *abort) return false;
+  }
+  return false;
+}
+
+// Bounded wait that does not give up on the abort flag: used where a role must
+// see its own bulk copies or MMAs complete before shared memory or TMEM is
+// released, also on the error path.
+__device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity, long long limit) {
+  const uint32_t a = smem_u32(bar);
+  for (long long i = 0; i < limit; ++i)
+    if (mbar_test_cta(a, parity)) return;
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// The epilogue warps' barrier, ANDing a flag over its 128 threads (so every
+// epilogue warp leaves its loop at the same unit).
+__device__ __forceinline__ bool epi_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 1, 128, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+
+__host__ __device__ inline size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ pass A
+struct LogitArgs {
+  const unsigned char* xs;   // X boxes [ntiles][nkb][16 KB]
+  const unsigned char* bs;   // coefficient operand [ngroups][nkb][2N rows x 128 B] (hi rows, then lo rows)
+  const int32_t* y;
+  unsigned char* rout;       // R boxes [ntiles][ngroups][NB][16 KB]
+  double* lpart;             // [gridDim.x][lpart_cstride]: this CTA's log-likelihood per chain
+  int32_t lpart_cstride;
+  int* err;
+  int64_t n, ntiles;
+  int32_t nkb, N, NB, Km1, zlogit, gc, ngroups, chains, NST;
+  uint32_t stage_bytes, tmem_cols;
+  long long spin_limit;
+};
+
+struct LogitSmem {
+  size_t ring, mx, sm, zy, llr, llc, bars, total;
+};
+
+__host__ __device__ inline LogitSmem logit_smem(int NST, uint32_t stage_bytes, int gc, int chains) {
+  LogitSmem L;
+  size_t off = 0;
+  L.ring = off;  off = al(off + size_t(NST) * stage_bytes, 1024);
+  L.mx = off;    off = al(off + size_t(gc) * kRows * 4, 16);
+  L.sm = off;    off = al(off + size_t(gc) * kRows * 4, 16);
+  L.zy = off;    off = al(off + size_t(gc) * kRows * 4, 16);
+  L.llr = off;   off = al(off + size_t(gc) * kRows * 8, 16);
+  L.llc = off;   off = al(off + size_t(chains) * 8, 16);
+  L.bars = off;  off = al(off + size_t(2 * NST + 5) * 8 + 16, 16);
+  L.total = off + 1024;   // slack for aligning the dynamic base to 1024
+  return L;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = A.N, NST = A.NST, Km1 = A.Km1, gc = A.gc;
+  const bool zl = A.zlogit != 0;
+  const LogitSmem Lo = logit_smem(NST, A.stage_bytes, gc, A.chains);
+  unsigned char* ring = smem + Lo.ring;
+  float* s_m = reinterpret_cast<float*>(smem + Lo.mx);     // [gc][128] running maximum
+  float* s_s = reinterpret_cast<float*>(smem + Lo.sm);     // [gc][128] running sum of exponentials
+  float* s_zy = reinterpret_cast<float*>(smem + Lo.zy);    // [gc][128] logit of the observed class
+  double* s_llr = reinterpret_cast<double*>(smem + Lo.llr);  // [gc][128] row log-likelihoods
+  double* s_llc = reinterpret_cast<double*>(smem + Lo.llc);  // [chains] this CTA's sums
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lo.bars);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + NST;
+  uint64_t* zdone = bars + 2 * NST;      // [2] accumulator a holds a finished unit
+  uint64_t* zfree = zdone + 2;           // [2] accumulator a drained
+  uint64_t* mdrain = zfree + 2;          // every MMA of this CTA complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdrain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mdrain + 2);
+
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&zdone[a], 1);
+      mbar_init(&zfree[a], 4);
+    }
+    mbar_init(mdrain, 1);
+    *abort_flag = 0;
+    fence_mbar_init_cluster();
+  }
+  for (int c = tid; c < A.chains; c += kThreads) s_llc[c] = 0.0;
+  if (warp == 1) tmem_alloc(tmem_slot, A.tmem_cols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t units = A.ntiles * A.ngroups;
+  const int64_t G = gridDim.x;
+  const int64_t nmine = (int64_t(blockIdx.x) < units) ? (units - 1 - blockIdx.x) / G + 1 : 0;
+  auto fail = [&](int bit) {
+    *abort_flag = 1;
+    atomicOr(A.err, bit);
+  };
+  const uint32_t coef_bytes = uint32_t(2 * N * 128);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t s = 0, issued = 0;
+      for (int64_t j = 0; j < nmine && !*abort_flag; ++j) {
+        const int64_t u = blockIdx.x + j * G;
+        const int64_t t = u / A.ngroups;
+        const int g = int(u % A.ngroups);
+        const unsigned char* xt = A.xs + size_t(t) * A.nkb * kBoxBytes;
+        const unsigned char* bt = A.bs + size_t(g) * A.nkb * coef_bytes;
+        for (int kb = 0; kb < A.nkb; ++kb, ++s) {
+          const int st = int(s % NST);
+          if (!wait_bounded(&empty[st], uint32_t(((s / NST) & 1) ^ 1), A.spin_limit, abort_flag)) {
+            fail(ERR_TIMEOUT_STAGE);
+            break;
+          }
+          unsigned char* sp = ring + size_t(st) * A.stage_bytes;
+          mbar_arrive_expect_tx(&full[st], uint32_t(kBoxBytes) + coef_bytes);
+          bulk_g2s(sp, xt + size_t(kb) * kBoxBytes, uint32_t(kBoxBytes), &full[st]);
+          bulk_g2s(sp + kBoxBytes, bt + size_t(kb) * coef_bytes, coef_bytes, &full[st]);
+          issued = s + 1;
+        }
+      }
+      // Every copy issued must land before shared memory is released.
+      for (int64_t q = (issued > NST ? issued - NST : 0); q < issued; ++q)
+        wait_drain(&full[q % NST], uint32_t((q / NST) & 1), A.spin_limit);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kRows, N, false, false);
+      int64_t s = 0;
+      for (int64_t j = 0; j < nmine && !*abort_flag; ++j) {
+        const int a = int(j & 1);
+        if (j >= 2 && !wait_bounded(&zfree[a], uint32_t(((j >> 1) - 1) & 1), A.spin_limit, abort_flag)) {
+          fail(ERR_TIMEOUT_MMA);
+          break;
+        }
+        fence_after_sync();
+        const uint32_t d = tmem + uint32_t(a * N);
+        for (int kb = 0; kb < A.nkb; ++kb, ++s) {
+          const int st = int(s % NST);
+          if (!wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag)) {
+            fail(ERR_TIMEOUT_STAGE);
+            break;
+          }
+          fence_after_sync();
+          const uint32_t xa = smem_u32(ring + size_t(st) * A.stage_bytes);
+          const uint32_t ba = xa + uint32_t(kBoxBytes);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t ad = smem_desc(xa + 32u * k, 16u, 1024u, 2u);
+            const uint64_t bh = smem_desc(ba + 32u * k, 16u, 1024u, 2u);
+            const uint64_t bl = smem_desc(ba + uint32_t(N) * 128u + 32u * k, 16u, 1024u, 2u);
+            mma_bf16(d, ad, bh, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            mma_bf16(d, ad, bl, idesc, 1u);
+          }
+          mma_commit(&empty[st]);
+        }
+        if (*abort_flag) break;
+        mma_commit(&zdone[a]);
+      }
+      // TMEM and shared memory stay allocated until every MMA has completed.
+      mma_commit(mdrain);
+      wait_drain(mdrain, 0u, A.spin_limit);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2-5)
+    const int q = warp & 3;
+    const int r = 32 * q + lane;                   // tile row = TMEM lane
+    const uint32_t tq = tmem + (uint32_t(32 * q) << 16);
+    for (int64_t j = 0; j < nmine; ++j) {
+      const int a = int(j & 1);
+      bool ok = (lane == 0) ? wait_bounded(&zdone[a], uint32_t((j >> 1) & 1), A.spin_limit, abort_flag) : true;
+      if (!ok) fail(ERR_TIMEOUT_MMA);
+      if (!epi_bar_and(ok)) break;
+      fence_after_sync();
+      const int64_t u = blockIdx.x + j * G;
+      const int64_t t = u / A.ngroups;
+      const int g = int(u % A.ngroups);
+      const int nch = min(gc, A.chains - g * gc);   // chains of this group
+      const int Cg = nch * Km1;
+      const int64_t grow = t * kRows + r;
+      const bool valid = grow < A.n;
+      const int yv = valid ? __ldg(A.y + grow) : -1;
+      for (int c = 0; c < nch; ++c) {
+        s_m[c * kRows + r] = zl ? 0.f : -INFINITY;   // the zero logit of class K, or nothing yet
+        s_s[c * kRows + r] = zl ? 1.f : 0.f;
+        s_zy[c * kRows + r] = 0.f;
+      }
+      const uint32_t acc = tq + uint32_t(a * N);
+      // Pass 1: running maximum and sum of exponentials of every chain's
+      // logits (online: the sum is rescaled when the maximum grows).
+      for (int c0 = 0; c0 < Cg; c0 += 16) {
+        float v[16];
+        tmem_ld16(acc + uint32_t(c0), v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int col = c0 + e;
+          if (col < Cg) {
+            const int c = col / Km1, k = col - c * Km1;
+            const float z = v[e];
+            const float mo = s_m[c * kRows + r], so = s_s[c * kRows + r];
+            if (z > mo) {
+              s_s[c * kRows + r] = so * expf(mo - z) + 1.f;
+              s_m[c * kRows + r] = z;
+            } else {
+              s_s[c * kRows + r] = so + expf(z - mo);
+            }
+            if (k == yv) s_zy[c * kRows + r] = z;
+          }
+        }
+      }
+      // Pass 2: R = Y - P for the group's columns (zero past Cg and on rows past
+      // n), written as BF16 in the MN-major 128-byte-swizzled boxes of pass B:
+      // 16-byte chunk j (8 columns) of row r of box b at chunk j ^ (r % 8).
+      unsigned char* rb = A.rout + (size_t(t) * A.ngroups + g) * A.NB * kBoxBytes;
+      for (int c0 = 0; c0 < A.NB * kBox; c0 += 16) {
+        float v[16];
+        if (c0 < Cg) tmem_ld16(acc + uint32_t(c0), v);
+        uint32_t w[8];
+#pragma unroll
+        for (int e = 0; e < 16; e += 2) {
+          float rv[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int col = c0 + e + h;
+            rv[h] = 0.f;
+            if (valid && col < Cg) {
+              const int c = col / Km1, k = col - c * Km1;
+              const float pk = expf(v[e + h] - s_m[c * kRows + r]) / s_s[c * kRows + r];
+              rv[h] = (k == yv ? 1.f : 0.f) - pk;
+            }
+          }
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(rv[0], rv[1]);
+          w[e / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int cc = c0 + 8 * hh;                // first column of this 16-byte chunk
+          const int box = cc / kBox, chunk = (cc % kBox) / 8;
+          unsigned char* dst = rb + size_t(box) * kBoxBytes + size_t(r) * 128 + size_t((chunk ^ (r & 7)) << 4);
+          *reinterpret_cast<uint4*>(dst) = make_uint4(w[4 * hh], w[4 * hh + 1], w[4 * hh + 2], w[4 * hh + 3]);
+        }
+      }
+      // The accumulator is read: the MMA issuer may start unit j + 2 in it.
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&zfree[a]);
+      // Row log-likelihoods, then their sum per chain over the 128 rows in row
+      // order, added to this CTA's per-chain sums in unit order.
+      for (int c = 0; c < nch; ++c)
+        s_llr[c * kRows + r] = valid ? double(s_zy[c * kRows + r] - s_m[c * kRows + r] - logf(s_s[c * kRows + r]))
+                                     : 0.0;
+      epi_bar();
+      if (r < nch) {
+        double sum = 0.0;
+        for (int i = 0; i < kRows; ++i) sum += s_llr[r * kRows + i];
+        s_llc[g * gc + r] += sum;
+      }
+      epi_bar();
+    }
+  }
+  __syncthreads();
+  for (int c = tid; c < A.chains; c += kThreads) A.lpart[size_t(blockIdx.x) * A.lpart_cstride + c] = s_llc[c];
+  if (warp == 1) {
+    fence_after_sync();
+    tmem_dealloc(tmem, A.tmem_cols);
+  }
+}
+
+// ------------------------------------------------------------------ pass B
+struct GradArgs {
+  const unsigned char* xs;   // X boxes [ntiles][nkb][16 KB]
+  const unsigned char* rs;   // R boxes [ntiles][ngroups][NB][16 KB]
+  float* gpart;              // [Q][C][p_pad] partial gradient slices
+  int64_t gpart_cstride;
+  int* err;
+  int64_t ntiles;
+  int32_t nkb, p_pad, N, NB, Km1, gc, ngroups, chains;
+  int32_t MB, nfg, Q, NST, NRS;
+  uint32_t tmem_cols;
+  long long spin_limit;
+};
+
+struct GradSmem {
+  size_t ring, rring, bars, total;
+};
+
+__host__ __device__ inline GradSmem grad_smem(int NST, int NRS, int NB) {
+  GradSmem L;
+  size_t off = 0;
+  L.ring = off;   off = al(off + size_t(NST) * 2 * kBoxBytes, 1024);
+  L.rring = off;  off = al(off + size_t(NRS) * NB * kBoxBytes, 1024);
+  L.bars = off;   off = al(off + size_t(2 * NST + 2 * NRS + 2) * 8 + 16, 16);
+  L.total = off + 1024;
+  return L;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = A.N, NST = A.NST, NRS = A.NRS;
+  const GradSmem Lo = grad_smem(NST, NRS, A.NB);
+  unsigned char* ring = smem + Lo.ring;
+  unsigned char* rring = smem + Lo.rring;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lo.bars);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + NST;
+  uint64_t* rfull = bars + 2 * NST;
+  uint64_t* rempty = rfull + NRS;
+  uint64_t* gdone = rempty + NRS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gdone + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gdone + 2);
+
+  // This CTA's unit: feature group f, chain group g, row range q.
+  const int b = blockIdx.x;
+  const int f = b % A.nfg, g = (b / A.nfg) % A.ngroups, q = b / (A.nfg * A.ngroups);
+  const int nblk = A.p_pad / 128;
+  const int mb0 = f * A.MB, mbn = max(0, min(A.MB, nblk - mb0));
+  const int64_t t0 = int64_t(q) * A.ntiles / A.Q, t1 = int64_t(q + 1) * A.ntiles / A.Q;
+  const int64_t T = t1 - t0;
+  const int nch = min(A.gc, A.chains - g * A.gc);
+  const int Cg = nch * A.Km1;
+
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < NRS; ++s) {
+      mbar_init(&rfull[s], 1);
+      mbar_init(&rempty[s], 1);
+    }
+    mbar_init(gdone, 1);
+    *abort_flag = 0;
+    fence_mbar_init_cluster();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, A.tmem_cols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  auto fail = [&](int bit) {
+    *abort_flag = 1;
+    atomicOr(A.err, bit);
+  };
+  const uint32_t rbytes = uint32_t(A.NB) * kBoxBytes;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t s = 0, issued = 0, rissued = 0;
+      for (int64_t i = 0; i < T && !*abort_flag && mbn > 0; ++i) {
+        const int64_t t = t0 + i;
+        const int rsl = int(i % NRS);
+        if (!wait_bounded(&rempty[rsl], uint32_t(((i / NRS) & 1) ^ 1), A.spin_limit, abort_flag)) {
+          fail(ERR_TIMEOUT_STAGE);
+          break;
+        }
+        mbar_arrive_expect_tx(&rfull[rsl], rbytes);
+        bulk_g2s(rring + size_t(rsl) * rbytes, A.rs + (size_t(t) * A.ngroups + g) * rbytes, rbytes, &rfull[rsl]);
+        rissued = i + 1;
+        const unsigned char* xt = A.xs + size_t(t) * A.nkb * kBoxBytes;
+        for (int mb = 0; mb < mbn; ++mb, ++s) {
+          const int st = int(s % NST);
+          if (!wait_bounded(&empty[st], uint32_t(((s / NST) & 1) ^ 1), A.spin_limit, abort_flag)) {
+            fail(ERR_TIMEOUT_STAGE);
+            break;
+          }
+          mbar_arrive_expect_tx(&full[st], uint32_t(2 * kBoxBytes));
+          bulk_g2s(ring + size_t(st) * 2 * kBoxBytes, xt + size_t(2 * (mb0 + mb)) * kBoxBytes, uint32_t(2 * kBoxBytes),
+                   &full[st]);
+          issued = s + 1;
+        }
+      }
+      for (int64_t qq = (issued > NST ? issued - NST : 0); qq < issued; ++qq)
+        wait_drain(&full[qq % NST], uint32_t((qq / NST) & 1), A.spin_limit);
+      for (int64_t qq = (rissued > NRS ? rissued - NRS : 0); qq < rissued; ++qq)
+        wait_drain(&rfull[qq % NRS], uint32_t((qq / NRS) & 1), A.spin_limit);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kRows, N, true, true);
+      int64_t s = 0;
+      for (int64_t i = 0; i < T && !*abort_flag && mbn > 0; ++i) {
+        const int rsl = int(i % NRS);
+        if (!wait_bounded(&rfull[rsl], uint32_t((i / NRS) & 1), A.spin_limit, abort_flag)) {
+          fail(ERR_TIMEOUT_STAGE);
+          break;
+        }
+        fence_after_sync();
+        const uint32_t rb = smem_u32(rring + size_t(rsl) * rbytes);
+        for (int mb = 0; mb < mbn; ++mb, ++s) {
+          const int st = int(s % NST);
+          if (!wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag)) {
+            fail(ERR_TIMEOUT_STAGE);
+            break;
+          }
+          fence_after_sync();
+          const uint32_t xa = smem_u32(ring + size_t(st) * 2 * kBoxBytes);
+          const uint32_t d = tmem + uint32_t(mb * N);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const uint64_t ad = smem_desc(xa + 2048u * k, uint32_t(kBoxBytes), 1024u, 2u);
+            const uint64_t bd = smem_desc(rb + 2048u * k, uint32_t(kBoxBytes), 1024u, 2u);
+            mma_bf16(d, ad, bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[st]);
+        }
+        if (*abort_flag) break;
+        mma_commit(&rempty[rsl]);
+      }
+      mma_commit(gdone);
+      wait_drain(gdone, 0u, A.spin_limit);   // every MMA complete before TMEM is released
+    }
+  } else {
+    // ------------------------------------------------------------ drain (warps 2-5)
+    const int qd = warp & 3;
+    const int row = 32 * qd + lane;               // feature within a block = TMEM lane
+    const uint32_t tq = tmem + (uint32_t(32 * qd) << 16);
+    bool ok = (lane == 0) ? wait_bounded(gdone, 0u, A.spin_limit, abort_flag) : true;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok && lane == 0) fail(ERR_TIMEOUT_MMA);
+    fence_after_sync();
+    float* gp = A.gpart + size_t(q) * A.gpart_cstride + size_t(g) * A.gc * A.Km1 * A.p_pad;
+    for (int mb = 0; mb < mbn; ++mb) {
+      const int col = (mb0 + mb) * 128 + row;
+      for (int c0 = 0; c0 < Cg; c0 += 16) {
+        float v[16];
+        if (ok && T > 0) tmem_ld16(tq + uint32_t(mb * N + c0), v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (c0 + e < Cg) gp[size_t(c0 + e) * A.p_pad + col] = (ok && T > 0) ? v[e] : 0.f;
+      }
+    }
+    fence_before_sync();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    fence_after_sync();
+    tmem_dealloc(tmem, A.tmem_cols);
+  }
+}
+
+// Coefficients [chains][Km1][p_pad] (FP32) -> operand boxes of every chain group,
+// [group][p_pad / 64][2N rows x 128 B]: rows [0, N) the hi term bf16(v), rows
+// [N, 2N) the lo term bf16(v - hi); columns past the group's C are zero.
+__global__ void beta_boxes_kernel(const float* beta, unsigned char* out, int32_t Km1, int32_t gc, int32_t chains,
+                                  int32_t N, int32_t p_pad) {
+  const int g = blockIdx.y;
+  const int nch = min(gc, chains - g * gc);
+  const int Cg = nch * Km1;
+  const float* bg = beta + size_t(g) * gc * Km1 * p_pad;
+  unsigned char* og = out + size_t(g) * (p_pad / kBox) * 2 * N * 128;
+  const int64_t total = int64_t(N) * p_pad;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int k = int(i / p_pad);
+    const int64_t col = i - int64_t(k) * p_pad;
+    const float v = (k < Cg) ? bg[size_t(k) * p_pad + col] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    unsigned char* box = og + size_t(col / kBox) * 2 * N * 128;
+    const int cc = int(col % kBox);
+    const uint32_t off_h = uint32_t(k) * 128u + uint32_t(((cc >> 3) ^ (k & 7)) << 4) + uint32_t((cc & 7) * 2);
+    const uint32_t off_l = uint32_t(N + k) * 128u + uint32_t(((cc >> 3) ^ ((N + k) & 7)) << 4) + uint32_t((cc & 7) * 2);
+    *reinterpret_cast<__nv_bfloat16*>(box + off_h) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(box + off_l) = lo;
+  }
+}
+
+}  // namespace tc2
+
+// ------------------------------------------------------------------ host side
+int tc2_threads() { return tc2::kThreads; }
+
+size_t tc2_logit_smem(int NST, int N, int gc, int chains) {
+  const uint32_t stage = uint32_t(tc2::al(size_t(tc2::kBoxBytes) + size_t(2 * N) * 128, 1024));
+  return tc2::logit_smem(NST, stage, gc, chains).total;
+}
+
+size_t tc2_grad_smem(int NST, int NRS, int NB) { return tc2::grad_smem(NST, NRS, NB).total; }
+
+cudaError_t tc2_prepare() {
+  int dev = 0, smem_max = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tc2::logits_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tc2::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  return e;
+}
+
+cudaError_t tc2_beta_boxes(const float* beta, void* out, int Km1, int gc, int chains, int N, int p_pad, int ngroups,
+                           cudaStream_t s) {
+  const int64_t total = int64_t(N) * p_pad;
+  const int gx = std::max(1, int(std::min<int64_t>(1024, (total + 255) / 256)));
+  tc2::beta_boxes_kernel<<<dim3(gx, ngroups), 256, 0, s>>>(beta, static_cast<unsigned char*>(out), Km1, gc, chains, N,
+                                                            p_pad);
+  return cudaGetLastError();
+}
+
+static uint32_t pow2_cols(int cols) {
+  uint32_t t = 32;
+  while (t < uint32_t(cols)) t <<= 1;
+  return t;
+}
+
+cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream) {
+  {
+    tc2::LogitArgs a{};
+    a.xs = static_cast<const unsigned char*>(L.xs);
+    a.bs = static_cast<const unsigned char*>(L.bs);
+    a.y = L.y;
+    a.rout = static_cast<unsigned char*>(L.rbuf);
+    a.lpart = L.lpart;
+    a.lpart_cstride = L.lpart_cstride;
+    a.err = L.err;
+    a.n = L.n;
+    a.ntiles = (L.n + tc2::kRows - 1) / tc2::kRows;
+    a.nkb = P.p_pad / tc2::kBox;
+    a.N = P.N;
+    a.NB = P.NB;
+    a.Km1 = L.Km1;
+    a.zlogit = L.zlogit;
+    a.gc = P.gc;
+    a.ngroups = (L.chains + P.gc - 1) / P.gc;
+    a.chains = L.chains;
+    a.NST = P.nstA;
+    a.stage_bytes = uint32_t(tc2::al(size_t(tc2::kBoxBytes) + size_t(2 * P.N) * 128, 1024));
+    a.tmem_cols = pow2_cols(2 * P.N);
+    a.spin_limit = L.spin_limit;
+    tc2::logits_kernel<<<P.gridA, tc2::kThreads, P.smemA, stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  tc2::GradArgs b{};
+  b.xs = static_cast<const unsigned char*>(L.xs);
+  b.rs = static_cast<const unsigned char*>(L.rbuf);
+  b.gpart = static_cast<float*>(L.gpart);
+  b.gpart_cstride = L.gpart_cstride;
+  b.err = L.err;
+  b.ntiles = (L.n + tc2::kRows - 1) / tc2::kRows;
+  b.nkb = P.p_pad / tc2::kBox;
+  b.p_pad = P.p_pad;
+  b.N = P.N;
+  b.NB = P.NB;
+  b.Km1 = L.Km1;
+  b.gc = P.gc;
+  b.ngroups = (L.chains + P.gc - 1) / P.gc;
+  b.chains = L.chains;
+  b.MB = P.MB;
+  b.nfg = P.nfg;
+  b.Q = P.Q;
+  b.NST = P.nstB;
+  b.NRS = P.nrsB;
+  b.tmem_cols = pow2_cols(P.MB * P.N);
+  b.spin_limit = L.spin_limit;
+  tc2::grad_kernel<<<P.nfg * b.ngroups * P.Q, tc2::kThreads, P.smemB, stream>>>(b);
+  return cudaGetLastError();
+}
+
+// Plan for `chains` chains of a problem (n, p, Km1) on nsm SMs with smem_max
+// bytes of shared memory per block: the chain group (largest whose MMA N <= 256
+// fits pass A's shared memory with >= 3 ring slots), pass A's grid, and pass B's
+// split (feature blocks per CTA, row ranges) that minimises the bytes the
+// busiest CTA streams.
+bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, Tc2Plan* out) {
+  Tc2Plan P{};
+  P.p_pad = int((p + 127) / 128 * 128);
+  const int64_t ntiles = (n + 127) / 128;
+  if (ntiles < 1 || Km1 < 1) return false;
+  int gc = 0;
+  for (int g = chains; g >= 1; --g) {
+    const int N = std::max(16, (g * Km1 + 15) / 16 * 16);
+    if (N > 256) continue;
+    const int ngroups = (chains + g - 1) / g;
+    const int gb = (chains + ngroups - 1) / ngroups;   // even groups
+    const int Nb = std::max(16, (gb * Km1 + 15) / 16 * 16);
+    if (tc2_logit_smem(3, Nb, gb, chains) > size_t(smem_max)) continue;
+    gc = gb;
+    break;
+  }
+  if (!gc) return false;
+  P.gc = gc;
+  P.N = std::max(16, (gc * Km1 + 15) / 16 * 16);
+  P.NB = (P.N + 63) / 64;
+  const int ngroups = (chains + gc - 1) / gc;
+  P.nstA = 3;
+  for (int s = 8; s > 3; --s)
+    if (tc2_logit_smem(s, P.N, gc, chains) <= size_t(smem_max)) {
+      P.nstA = s;
+      break;
+    }
+  P.smemA = std::max(tc2_logit_smem(P.nstA, P.N, gc, chains), size_t(116 * 1024));
+  P.gridA = int(std::min<int64_t>(nsm, ntiles * ngroups));
+  // Pass B.
+  const int nblk = P.p_pad / 128;
+  const int mbmax = std::min(nblk, std::max(1, 512 / P.N));
+  double best = -1.0;
+  for (int MB = 1; MB <= mbmax; ++MB) {
+    const int nfg = (nblk + MB - 1) / MB;
+    const int64_t base = int64_t(nfg) * ngroups;
+    const int Q = int(std::max<int64_t>(1, std::min<int64_t>(ntiles, nsm / std::max<int64_t>(1, base))));
+    const int64_t ctas = base * Q;
+    const double waves = double((ctas + nsm - 1) / nsm);
+    const double per_cta = double((ntiles + Q - 1) / Q) * (2.0 * MB + P.NB);   // boxes streamed by the busiest CTA
+    const double cost = per_cta * waves;
+    if (best < 0 || cost < best) {
+      best = cost;
+      P.MB = MB;
+      P.nfg = nfg;
+      P.Q = Q;
+    }
+  }
+  // Two R slots (the next tile's residual lands while this one is used) with at
+  // least three X slots, else one R slot.
+  P.nrsB = 2;
+  P.nstB = 0;
+  for (int r = 2; r >= 1 && !P.nstB; --r)
+    for (int s = 8; s >= (r == 2 ? 3 : 2) && !P.nstB; --s)
+      if (tc2_grad_smem(s, r, P.NB) <= size_t(smem_max)) {
+        P.nstB = s;
+        P.nrsB = r;
+      }
+  if (!P.nstB) return false;
+  P.smemB = std::max(tc2_grad_smem(P.nstB, P.nrsB, P.NB), size_t(116 * 1024));
+  *out = P;
+  return true;
+}
+
+}  // namespace hmc

@@ -42,17 +42,18 @@ def _errs(Xq, y, beta, lp, g, kind, scale, chains, X=None):
     return out
 
 
-@pytest.mark.parametrize("storage", ["bf16", "fp8"])
-def test_precision_workload_full_size(cuda, storage):
+@pytest.mark.parametrize("storage,engine", [("bf16", 0), ("fp8", 0), ("bf16", 3)])
+def test_precision_workload_full_size(cuda, storage, engine):
     import torch
     X, y, btrue, spec = synthetic.make_workload("precision")
     K, chains = spec["K"], spec["chains"]
     kind, scale = spec["prior"]
     rng = np.random.default_rng(21)
     beta = (0.01 * rng.standard_normal((chains, K - 1, X.shape[1]))).astype(np.float32)
-    with hmc.create(X, y, K, kind, scale, x_storage=storage, max_chains=chains) as h:
+    with hmc.create(X, y, K, kind, scale, x_storage=storage, max_chains=chains, engine=engine) as h:
         d = h.describe()
-        assert d["engine"] == "tcgen05" and d["problems"][0]["group_chains"] == chains, d
+        assert d["engine"] == ("tcgen05_2pass" if engine == 3 else "tcgen05"), d
+        assert d["problems"][0]["group_chains"] == chains, d
         bits, scales = h.get_x()
         lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
         torch.cuda.synchronize()
@@ -83,7 +84,8 @@ def test_batched_workload_64_chains_full_size(cuda):
     rng = np.random.default_rng(22)
     beta = (0.05 * rng.standard_normal((chains, K - 1, X.shape[1]))).astype(np.float32)
     with hmc.create(X, y, K, kind, scale, x_storage="bf16", max_chains=chains) as h:
-        assert h.describe()["engine"] == "tcgen05"
+        # 64 chains do not fit one fused launch: the two-pass engine takes them all at once
+        assert h.describe()["engine"] == "tcgen05_2pass"
         bits, _ = h.get_x()
         lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
         torch.cuda.synchronize()
@@ -124,16 +126,19 @@ def test_batched_uneven_32_problems_full_size(cuda):
         assert et <= TOL_TOTAL_BF16, (b, "total error", et)
 
 
-def test_autodiff_workload_full_size(cuda):
+@pytest.mark.parametrize("engine", [0, 2])
+def test_autodiff_workload_full_size(cuda, engine):
+    """Default engine (two-pass: the fused engine fits 3 of the 8 chains per
+    launch here) and the fused engine (three launches of 3, 3 and 2 chains)."""
     import torch
     X, y, btrue, spec = synthetic.make_workload("autodiff")
     n, p, K, chains = spec["n"], spec["p"], spec["K"], spec["chains"]
     kind, scale = spec["prior"]
     rng = np.random.default_rng(24)
     b0 = (0.01 * rng.standard_normal((chains, K - 1, p))).astype(np.float32)
-    with hmc.create(X, y, K, kind, scale, x_storage="bf16", max_chains=chains) as h:
+    with hmc.create(X, y, K, kind, scale, x_storage="bf16", max_chains=chains, engine=engine) as h:
         del X
-        assert h.describe()["engine"] == "tcgen05"
+        assert h.describe()["engine"] == ("tcgen05" if engine == 2 else "tcgen05_2pass")
         h.sample(chains, 5, spec["eps"], 2, 7, beta0=torch.from_numpy(b0).to(cuda))      # states the chains reach
         beta = torch.empty((chains, K - 1, p), dtype=torch.float32, device=cuda)
         h.get_state(chains, beta=beta)

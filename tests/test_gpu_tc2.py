@@ -1,0 +1,107 @@
+"""The two-pass tensor-core engine (opts.engine = 3, BF16 X): pass A forms the
+logits, softmax and residual of every (row tile, chain group), pass B the
+partial gradients X^T R; against the FP64 oracle on the stored BF16 X.
+
+Same operand precision as the fused tensor-core engine (two-term BF16
+coefficients, BF16 residual, FP32 accumulation), so the same gates: gradient
+3e-3 relative in norm and element-wise, log K 1e-4."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import model, quant
+from paper_1402_4089_gb300 import hmc, synthetic
+from parity_util import grad_errs, lk_err
+
+pytestmark = pytest.mark.gpu
+
+TOL_G, TOL_L = 3e-3, 1e-4
+
+
+def _run(cuda, n, p, K, chains, seed, layout="free", prior=("gaussian", 10.0), bscale=0.05):
+    import torch
+    X, y, _ = synthetic.make_problem(n, p, K, seed=seed)
+    rows = K - 1 if layout == "free" else K
+    beta = (bscale * np.random.default_rng(seed + 1).standard_normal((chains, rows, p))).astype(np.float32)
+    with hmc.create(X, y, K, prior[0], prior[1], x_storage="bf16", max_chains=chains, engine=3, layout=layout) as h:
+        d = h.describe()
+        assert d["engine"] == "tcgen05_2pass", d
+        bits, _ = h.get_x()
+        lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
+        torch.cuda.synchronize()
+        lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    Xq = quant.bf16_decode(bits).astype(np.float64)
+    for c in range(chains):
+        lk_o = model.log_kernel_layout(Xq, y, beta[c], prior[0], prior[1], layout)
+        g_o = model.grad_log_kernel_layout(Xq, y, beta[c], prior[0], prior[1], layout)
+        el = lk_err(lp[c], lk_o)
+        eg, ee = grad_errs(g[c], g_o)
+        assert el <= TOL_L and eg <= TOL_G and ee <= TOL_G, (d["problems"][0], c, el, eg, ee)
+    return d
+
+
+@pytest.mark.parametrize("n,p,K,chains", [(1000, 700, 6, 2), (333, 129, 3, 1), (2049, 1000, 20, 4), (128, 64, 2, 3),
+                                          (5000, 2000, 10, 7), (130, 4100, 5, 1), (257, 300, 33, 1)])
+def test_tc2_matches_oracle(cuda, n, p, K, chains):
+    _run(cuda, n, p, K, chains, seed=n + 7 * p)
+
+
+def test_tc2_many_chains_in_groups(cuda):
+    d = _run(cuda, 3000, 500, 10, 64, seed=71)
+    pa = d["problems"][0]["pass_a"]
+    assert pa["chain_group"] < 64                      # several chain groups inside the two launches
+
+
+@pytest.mark.parametrize("layout", ["masked", "unconstrained"])
+def test_tc2_layouts(cuda, layout):
+    _run(cuda, 1500, 400, 6, 3, seed=72, layout=layout, prior=("cauchy", 1.0))
+
+
+def test_tc2_deterministic_and_one_launch_pair(cuda):
+    import torch
+    X, y, _ = synthetic.make_problem(3000, 1500, 8, seed=73)
+    beta = torch.from_numpy((0.05 * np.random.default_rng(74).standard_normal((9, 7, 1500))).astype(np.float32)).to(cuda)
+    with hmc.create(X, y, 8, "gaussian", 10.0, x_storage="bf16", max_chains=9, engine=3) as h:
+        h.set_timing(True)
+        a = [t.cpu().numpy() for t in h.logpost_grad(beta)]
+        assert h.fused_kernel_time()[1] == 1          # both passes inside one timed pair of events
+        b = [t.cpu().numpy() for t in h.logpost_grad(beta)]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_tc2_sampling_follows_the_fused_engine(cuda):
+    """The same chains on both tensor-core engines: identical momenta and accept
+    draws, gradients equal to rounding, so the samples agree closely."""
+    import torch
+    X, y, _ = synthetic.make_problem(2000, 300, 5, seed=75)
+    out = []
+    for engine in (2, 3):
+        with hmc.create(X, y, 5, "gaussian", 10.0, x_storage="bf16", max_chains=2, engine=engine) as h:
+            s = torch.empty((6, 2, 4, 300), dtype=torch.float32, device=cuda)
+            st = h.sample(2, 10, 0.005, 6, 9, beta0=torch.zeros((2, 4, 300), device=cuda), samples=s)
+            out.append((s.cpu().numpy(), [x["accepted"] for x in st]))
+    assert out[0][1] == out[1][1]
+    scale = np.abs(out[0][0]).max()
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-3 * scale
+
+
+def test_tc2_timeout_is_reported_and_handle_recovers(cuda):
+    import torch
+    X, y, _ = synthetic.make_problem(600, 256, 3, seed=76)
+    beta = torch.from_numpy((0.1 * np.random.default_rng(77).standard_normal((1, 2, 256))).astype(np.float32)).to(cuda)
+    os.environ["HMC_FAULT"] = "timeout"
+    try:
+        h = hmc.create(X, y, 3, "gaussian", 1.0, x_storage="bf16", engine=3)
+    finally:
+        del os.environ["HMC_FAULT"]
+    with h:
+        with pytest.raises(hmc.HmcError) as ei:
+            h.logpost_grad(beta.cpu().numpy())        # host buffers: the call reads the error word
+        assert ei.value.status == hmc.ETIMEOUT
+        lp, g = h.logpost_grad(beta.cpu().numpy())
+        bits, _ = h.get_x()
+    Xq = quant.bf16_decode(bits).astype(np.float64)
+    b = beta.cpu().numpy()[0].astype(np.float64)
+    assert lk_err(lp[0], model.log_kernel(Xq, y, b, "gaussian", 1.0)) <= TOL_L
+    assert max(grad_errs(g[0], model.grad_log_kernel(Xq, y, b, "gaussian", 1.0))) <= TOL_G
