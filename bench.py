@@ -2,18 +2,24 @@
 """Benchmark of the HMC hot path on GB300: prints ONE JSON line.
 
 A step is one HMC iteration over the synthetic workload: momentum draw, L
-leapfrog updates (each one fused log-posterior + gradient pass over X, then
-the fixed-order split-K reduction and the leapfrog update), the Metropolis
-test and the keep/restore select -- all on the device, replayed from one
-CUDA graph.  ``value`` is gradient evaluations per second (chains * L per
-step) with X resident in HBM; ``e2e`` is the same metric through the C ABI
-with host buffers (the chain state uploaded and the sample read back every
-step); ``roofline`` is the fused kernel's X-stream bandwidth against the
-measured HBM copy bandwidth; ``cpu_baseline`` is the FP64 oracle on the
-host cores on a bounded sample of the same workload.
+leapfrog updates (each one gradient evaluation of every chain -- the fused
+pass, or the two passes of the two-pass engine, over X -- then the
+fixed-order split-K reduction and the leapfrog update), the Metropolis test
+and the keep/restore select -- all on the device, replayed from one CUDA
+graph.  The default workload is the largest configuration: n = 1e5, p = 2e4,
+K = 10, 8 chains, X in BF16 (4 GB), L = 100.  ``value`` is gradient
+evaluations per second (chains * L per step) with X resident in HBM; ``e2e``
+is the same metric through the C ABI with host buffers (the chain state
+uploaded and the sample read back every step); ``roofline`` is the dominant
+kernel's algorithmic bytes per launch over its duration against the measured
+HBM copy bandwidth (``gradient_roofline``: one gradient against X read once);
+``cpu_baseline`` is the FP64 oracle on the host cores on a bounded sample of
+the same workload; ``ess`` compares ESS/s of FP32 single-chain and BF16
+multi-chain sampling from stationary chains at equal posterior accuracy.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload highdim_fp32|plain_fp64|precision|batched|autodiff]
+                    [--workload autodiff|precision|batched|highdim_fp32|plain_fp64|mnist_shaped|
+                                batched_uneven|sweep]
 """
 import argparse
 import hashlib
@@ -50,7 +56,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="highdim_fp32")
+    ap.add_argument("--workload", default="autodiff",
+                    help="autodiff (default: n=1e5 p=2e4 K=10, 8 chains, BF16 X), precision, batched, highdim_fp32, "
+                         "plain_fp64, mnist_shaped, batched_uneven, sweep")
+    ap.add_argument("--engine", type=int, default=0, help="library engine (0 auto, 1 CUDA cores, 2 fused tcgen05, "
+                                                           "3 two-pass tcgen05)")
     ap.add_argument("--xdtype", default=None, help="override the workload's X storage (f32, bf16, fp8, f64)")
     ap.add_argument("--chains", type=int, default=None)
     ap.add_argument("--L", type=int, default=None)
@@ -60,7 +70,10 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true", help="use the library's tile choice instead of measuring")
-    ap.add_argument("--ess-iters", type=int, default=200, help="HMC iterations of the ESS/s run (0: skip)")
+    ap.add_argument("--ess-iters", type=int, default=1000, help="timed HMC iterations of each ESS/s run (0: skip)")
+    ap.add_argument("--ess-burn", type=int, default=200, help="untimed burn-in iterations before each ESS/s run")
+    ap.add_argument("--ess-chains", type=int, default=8, help="chains of the BF16 multi-chain ESS/s run")
+    ap.add_argument("--ess-coords", type=int, default=4000, help="coordinates (seeded subset) of the ESS estimates")
     ap.add_argument("--sweep-limit", type=int, default=0, help="sweep workload: first k shapes only (0: all 224)")
     ap.add_argument("--sweep-oracle-np", type=float, default=2e7,
                     help="sweep workload: time the oracle only where N p is at most this")
@@ -178,12 +191,13 @@ def max_over_ranks(value, dist, device):
 
 # ------------------------------------------------------------ measurements
 def measured_peaks():
+    """(HBM GB/s, sustained BF16 TFLOP/s, source) from MEASURED_PEAKS.json, else the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops_sustained", 1700.0)), "measured"
+    return 6800.0, 1700.0, "fallback"
 
 
 def code_only(text):
@@ -224,22 +238,33 @@ def kernel_source_hash(engine, read=None):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, xdt, engine):
-    """DRAM bytes per fused launch from a committed ncu summary of this workload and X
-    storage, if it was taken on the current kernel source."""
+def recorded_traffic(workload, xdt, engine, kernel=None):
+    """DRAM bytes per launch from a committed ncu summary of this workload and X
+    storage (and, for the two-pass engine, kernel), if it was taken on the current
+    kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get(f"{workload}:{xdt}")
+    e = d.get(f"{workload}:{xdt}" + (f":{kernel}" if kernel else ""))
     if not e or e.get("engine") != engine or e.get("source_sha") != kernel_source_hash(engine):
         return None
     return e.get("bytes_per_launch")
 
 
-def cpu_baseline(X64, y, spec, seconds):
-    """The FP64 oracle as it stands: leapfrog steps (one gradient each) on the host."""
+def blas_threads_default():
+    """Threads the host BLAS may use: the CPUs this process may run on (the BLAS
+    default), unless a thread-count variable limits it."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            cores = min(cores, int(os.environ[var]))
+    return cores
+
+
+def oracle_rate(X64, y, spec, seconds):
+    """Oracle leapfrog steps (one FP64 gradient each) per second on the rows given."""
     from oracle import hmc as ohmc
     from oracle import model
     kind, scale = spec["prior"]
@@ -253,50 +278,148 @@ def cpu_baseline(X64, y, spec, seconds):
     steps = max(1, int(seconds / max(t_one, 1e-6)))
     t0 = time.perf_counter()
     ohmc.leapfrog(X64, y, beta, eta, spec["eps"], steps, kind, scale, grad0=g)
-    el = time.perf_counter() - t0
-    cores = os.cpu_count()
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
-        if os.environ.get(var, "").isdigit():
-            cores = int(os.environ[var])
-    return {"value": steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} FP64 leapfrog steps (one gradient each) of the full workload in {el:.1f} s, "
-                      f"numpy/BLAS on the host"}
+    return steps, time.perf_counter() - t0
 
 
-def oracle_accuracy(h, X64, y, spec, xdt, tdt, dev):
-    """Error of the GPU log K and gradient at chain 0's current state against the
-    FP64 oracle on the X values the device stores (part of the CPU-baseline leg)."""
+def sample_rows(n, p, spec, seconds):
+    """Rows of the bounded CPU sample: all of them when an FP64 copy of X is at most
+    2 GB, else a leading block sized for about `seconds` of oracle gradients."""
+    if n * p * 8 <= 2e9:
+        return n
+    return int(min(n, max(500, 2e9 / (8 * p))))
+
+
+def cpu_baseline(X, y, spec, seconds):
+    """The FP64 oracle as it stands: leapfrog steps (one gradient each) on the host,
+    over the leading rows of X when the whole workload is too large for a bounded
+    sample (the oracle's cost is linear in the rows, so the rate is scaled by
+    rows / n); plus the same with the host BLAS held to one thread (a subprocess)."""
+    n, p = X.shape
+    m = sample_rows(n, p, spec, seconds)
+    X64 = np.asarray(X[:m], dtype=np.float64)
+    steps, el = oracle_rate(X64, y[:m], spec, seconds)
+    value = steps / el * m / n
+    one = None
+    try:
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ("import json,sys,numpy as np;sys.path.insert(0,%r);import bench;from paper_1402_4089_gb300 import synthetic;"
+                "X,y,_,spec=synthetic.make_workload(%r,n=%d);spec=dict(spec,**json.loads(%r));"
+                "s,e=bench.oracle_rate(np.asarray(X,dtype=np.float64),y,spec,%f);print(s/e)"
+                % (ROOT, spec["name"], min(m, 4000), json.dumps({"eps": spec["eps"]}), max(2.0, seconds / 3)))
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        if r.returncode == 0:
+            one = float(r.stdout.strip().splitlines()[-1]) * min(m, 4000) / n
+    except (subprocess.SubprocessError, ValueError, OSError):
+        one = None
+    rows = "all" if m == n else f"the first {m} of {n}"
+    return {"value": value, "unit": UNIT, "cores": blas_threads_default(), "kind": "oracle",
+            "value_1thread": one,
+            "sample": f"{steps} FP64 leapfrog steps (one gradient each) over {rows} rows in {el:.1f} s, numpy/BLAS on "
+                      f"the host with its default threads (= cores); rate scaled to the full {n} rows "
+                      f"(linear in rows); value_1thread: the same on at most 4000 rows with BLAS held to 1 thread"}
+
+
+def oracle_accuracy(h, X, y, spec, xdt, tdt, dev, chains_to_check):
+    """Error of the GPU log K and gradient at the chains' current state against the
+    FP64 oracle, evaluated in row blocks: on the X values the device stores
+    (arithmetic error) and on the original X (total error)."""
     import torch
     from oracle import model, quant
     K, chains = spec["K"], spec["chains"]
     kind, scale = spec["prior"]
-    p = X64.shape[1]
+    n, p = X.shape
     beta = torch.empty((chains, K - 1, p), dtype=tdt, device=dev)
     h.get_state(chains, beta=beta)
     lp, g = h.logpost_grad(beta)
     torch.cuda.synchronize()
     bits, sc = h.get_x()
-    if xdt == "bf16":
-        Xs = quant.bf16_decode(bits).astype(np.float64)
-    elif xdt == "fp8":
-        Xs = quant.fp8_dequantize(bits, sc)
-    else:
-        Xs = X64
-    b0 = beta[0].double().cpu().numpy()
-    lk_o = model.log_kernel(Xs, y, b0, kind, scale)
-    g_o = model.grad_log_kernel(Xs, y, b0, kind, scale)
-    g0 = g[0].double().cpu().numpy()
-    return {"chain": 0, "state": "after the timed iterations",
-            "vs": "FP64 oracle on the stored X values",
-            "logk_rel_err": float(abs(float(lp[0]) - lk_o) / max(1.0, abs(lk_o))),
-            "grad_rel_err": float(np.linalg.norm(g0 - g_o) / max(np.linalg.norm(g_o), 1e-300)),
-            "tol_grad": {"f64": 1e-11, "f32": 1e-5, "bf16": 1e-2, "fp8": 1e-2}[xdt]}
+    B = max(1, int(2e8 // p))
+
+    def stored(a):
+        if xdt == "bf16":
+            return quant.bf16_decode(bits[a:a + B])
+        if xdt == "fp8":
+            return quant.fp8_dequantize(bits[a:a + B], sc)
+        return bits[a:a + B]
+
+    bs = [beta[c].double().cpu().numpy() for c in chains_to_check]
+    lk_s, g_s, _ = model.log_kernel_and_grad_by_rows(((stored(a), y[a:a + B]) for a in range(0, n, B)), bs, kind, scale)
+    lk_t, g_t, _ = model.log_kernel_and_grad_by_rows(((X[a:a + B], y[a:a + B]) for a in range(0, n, B)), bs, kind, scale)
+    out = {"chains": list(chains_to_check), "state": "after the timed iterations",
+           "tol_grad": {"f64": 1e-11, "f32": 1e-5, "bf16": 1e-2, "fp8": 1e-2}[xdt]}
+    for tag, lks, gs in (("stored_x", lk_s, g_s), ("original_x", lk_t, g_t)):
+        el, eg, ee = [], [], []
+        for i, c in enumerate(chains_to_check):
+            gc = g[c].double().cpu().numpy()
+            el.append(abs(float(lp[c]) - lks[i]) / max(1.0, abs(lks[i])))
+            eg.append(float(np.linalg.norm(gc - gs[i]) / max(np.linalg.norm(gs[i]), 1e-300)))
+            ee.append(float(np.abs(gc - gs[i]).max() / max(np.abs(gs[i]).max(), 1e-30)))
+        out[tag] = {"logk_rel_err": max(el), "grad_rel_err": max(eg), "grad_elem_err": max(ee)}
+    out["vs"] = ("stored_x: FP64 oracle on the X values the device stores (arithmetic error); original_x: on the FP32 "
+                 "input X (total error, storage rounding included)")
+    return out
+
+
+def ess_comparison(args, dev):
+    """ESS/s of the FP32 single-chain CUDA-core path and of the BF16 multi-chain
+    tensor-core path on the high-dimensional problem (n=1e4, p=5000, K=10), both
+    from stationary chains: `ess_burn` iterations from beta = 0 (not timed), then
+    `ess_iters` timed iterations whose draws are kept on the device.  ESS
+    (Geyer, chains pooled) and MCSE on a seeded subset of coordinates; the two
+    posteriors' means are compared per coordinate within 3 combined MCSE."""
+    import torch
+    from paper_1402_4089_gb300 import diagnostics, hmc, synthetic
+    X, y, _, spec = synthetic.make_workload("highdim_fp32")
+    K, p, L, eps = spec["K"], spec["p"], spec["L"], spec["eps"]
+    kind, scale = spec["prior"]
+    rng = np.random.default_rng(7)
+    coords = np.sort(rng.choice((K - 1) * p, size=min(args.ess_coords, (K - 1) * p), replace=False))
+    idx = torch.from_numpy(coords).to(dev)
+    runs = {}
+    for tag, xs, chains, engine in (("fp32_1chain", "f32", 1, 1), (f"bf16_{args.ess_chains}chains", "bf16", args.ess_chains, 0)):
+        stream = torch.cuda.Stream(device=dev)
+        h = hmc.create(X, y, K, kind, scale, x_storage=xs, max_chains=chains, engine=engine, stream=stream)
+        h.sample(chains, L, eps, args.ess_burn, 11, beta0=torch.zeros((chains, K - 1, p), device=dev))
+        draws = torch.empty((args.ess_iters, chains, K - 1, p), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = h.sample(chains, L, eps, args.ess_iters, 12, samples=draws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        sub = draws.reshape(args.ess_iters, chains, -1)[:, :, idx].double().cpu().numpy()
+        del draws
+        e = diagnostics.ess(sub)
+        flat = sub.reshape(-1, sub.shape[2])
+        mean, sd = flat.mean(axis=0), flat.std(axis=0)
+        runs[tag] = {"x_storage": xs, "chains": chains, "engine": h.describe()["engine"], "iters": args.ess_iters,
+                     "burn_in": args.ess_burn, "seconds": round(secs, 3), "ess_min": round(float(e.min()), 2),
+                     "ess_median": round(float(np.median(e)), 2), "ess_min_per_s": round(float(e.min()) / secs, 3),
+                     "ess_median_per_s": round(float(np.median(e)) / secs, 3),
+                     "accept_rate": round(sum(s["accepted"] for s in st) / max(1, sum(s["iterations"] for s in st)), 4),
+                     "_m": mean, "_se": sd / np.sqrt(np.maximum(e, 1.0))}
+        h.close()
+    a, b = list(runs.values())
+    z = np.abs(a["_m"] - b["_m"]) / np.sqrt(a["_se"] ** 2 + b["_se"] ** 2 + 1e-300)
+    for r in runs.values():
+        del r["_m"], r["_se"]
+    tags = list(runs)
+    return {"problem": "highdim_fp32: n=10000 p=5000 K=10, N(0,1) prior, L=100, eps=2e-3", "coords": int(coords.size),
+            **runs,
+            "ess_per_s_ratio_min": round(runs[tags[1]]["ess_min_per_s"] / max(runs[tags[0]]["ess_min_per_s"], 1e-12), 2),
+            "ess_per_s_ratio_median": round(runs[tags[1]]["ess_median_per_s"] /
+                                            max(runs[tags[0]]["ess_median_per_s"], 1e-12), 2),
+            "equal_accuracy": {"criterion": "|m_a - m_b| <= 3 sqrt(MCSE_a^2 + MCSE_b^2) per coordinate; pass if at most "
+                                            "1% of coordinates exceed it and none exceeds 5",
+                               "frac_above_3": round(float(np.mean(z > 3.0)), 4), "max_z": round(float(z.max()), 2),
+                               "pass": bool(np.mean(z > 3.0) <= 0.01 and z.max() <= 5.0)}}
 
 
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
-    from paper_1402_4089_gb300 import build, diagnostics, hmc, synthetic, tune
+    from paper_1402_4089_gb300 import build, hmc, synthetic, tune
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -310,6 +433,7 @@ def run_ours(args):
     build.build()
 
     spec = workload_spec(args)
+    spec["name"] = args.workload
     X, y, btrue, _ = synthetic.make_workload(args.workload)
     n, p, K = spec["n"], spec["p"], spec["K"]
     chains, L, eps = spec["chains"], spec["L"], spec["eps"]
@@ -320,17 +444,21 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     Xin = X if xdt != "f64" else X.astype(np.float64)
     tile_source, tune_table = ("given", None) if tile else ("library", None)
-    engine = 0
-    if tile is None and not args.no_autotune:
+    engine = args.engine
+    big = n * p > 2e8
+    if tile is None and not args.no_autotune and not engine and not big:
         with torch.cuda.stream(stream):
             t_eng, t_tile, tune_table = tune.autotune(Xin, y, K, kind, scale, x_storage=xdt, state=state,
                                                       chains=chains, stream=stream)
         if t_tile is not None:
             engine, tile, tile_source = t_eng, t_tile, "autotuned"
+    elif big and tile is None and not args.no_autotune:
+        tile_source = "library (autotune skipped: every candidate would upload the whole X again)"
     h = hmc.create(Xin, y, K, kind, scale, x_storage=xdt, state=state, max_chains=chains, stream=stream, tile=tile,
                    engine=engine)
     desc_all = h.describe()
     desc = desc_all["problems"][0]
+    eng_name = desc_all["engine"]
     tdt = torch.float64 if state == "f64" else torch.float32
     seed = 20140217
     zeros = torch.zeros((chains, K - 1, p), dtype=tdt, device=dev)
@@ -347,7 +475,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # timed region: K iterations from the cached graph, CUDA events around every
-    # 10th fused launch (an event node per launch would slow the graph itself)
+    # 10th gradient evaluation (an event node per launch would slow the graph itself)
     h.set_timing(True, every=10)
     if dist:
         dist.barrier()
@@ -363,31 +491,61 @@ def run_ours(args):
         torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     fused_ms, fused_n = h.fused_kernel_time()
+    first_ms = h.first_pass_time()
     h.set_timing(False)
     elapsed = max_over_ranks(elapsed, dist, dev)
     grads = chains * L * args.steps
     value = world * grads / elapsed
     groups = -(-chains // desc["group_chains"])
-    # traj_start + per leapfrog step (per chain group: [operand boxes +] fused pass, then the
+    # traj_start + per leapfrog step (per chain group: [operand boxes +] the pass(es), then the
     # reduce/update) + select
-    per_group = 2 if desc_all["engine"] == "tcgen05" else 1
+    per_group = {"simt": 1, "tcgen05": 2, "tcgen05_2pass": 3}[eng_name]
     launches_per_step = 1 + L * (groups * per_group + 1) + 1
 
-    # roofline of the fused pass (X streamed once per gradient)
+    # rooflines: the gradient (X once) and the dominant kernel
     xb = XBYTES[xdt]
     c_launch = min(chains, desc["group_chains"]) * (K - 1)
-    alg_bytes = n * p * xb + 4 * n + 8 * p * c_launch
-    avg_launch_s = (fused_ms / 1e3) / max(fused_n, 1)
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / avg_launch_s / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, xdt, desc_all["engine"]),
-            "kernel": ("lpg_tc_kernel (tcgen05)" if h.describe()["engine"] == "tcgen05" else "lpg_kernel (CUDA cores)")
-            + f" X={xdt} C={c_launch}", "avg_launch_us": round(avg_launch_s * 1e6, 2),
-            "launches_timed": fused_n, "timed_launches_from": "every 10th fused launch of the last HMC iteration "
-                                                               "of the timed region",
-            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-            if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    hbm_peak, tc_peak, peak_kind = measured_peaks()
+    per_grad_s = (fused_ms / 1e3) / max(fused_n, 1)          # one gradient of the launch's chains
+    x_bytes = n * p * xb
+    grad_bytes = x_bytes + 4 * n + 8 * p * c_launch
+    grad_flops = 4.0 * n * p * c_launch                       # two contractions, 2 n p C each
+    if eng_name == "tcgen05_2pass":
+        ta = (first_ms / 1e3) / max(fused_n, 1)
+        tb = per_grad_s - ta
+        passes = {"A (logits, softmax, residual)": (ta, x_bytes + 4 * n + 4 * p * c_launch + 2 * n * c_launch),
+                  "B (X^T R)": (tb, x_bytes + 2 * n * c_launch + 4 * p * c_launch)}
+        dom = max(passes, key=lambda k: passes[k][0])
+        t_dom, b_dom = passes[dom]
+        kernel = f"tc2::{'logits_kernel' if dom.startswith('A') else 'grad_kernel'} (tcgen05, pass {dom})"
+        f_dom = 2.0 * n * p * c_launch
+        traffic = recorded_traffic(args.workload, xdt, eng_name, "A" if dom.startswith("A") else "B")
+        per_pass = {k: {"us": round(v[0] * 1e6, 2), "bytes": int(v[1]), "gbs": round(v[1] / v[0] / 1e9, 1),
+                        "frac": round(v[1] / v[0] / 1e9 / hbm_peak, 4),
+                        "tflops": round(2.0 * n * p * c_launch / v[0] / 1e12, 1)} for k, v in passes.items()}
+    else:
+        t_dom, b_dom, f_dom = per_grad_s, grad_bytes, grad_flops
+        kernel = ("lpg_tc_kernel (tcgen05)" if eng_name == "tcgen05" else "lpg_kernel (CUDA cores)")
+        traffic = recorded_traffic(args.workload, xdt, eng_name)
+        per_pass = None
+    achieved = b_dom / t_dom / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+            "kernel": kernel + f" X={xdt} C={c_launch}", "avg_launch_us": round(t_dom * 1e6, 2),
+            "algorithmic_bytes": int(b_dom),
+            "launches_timed": fused_n, "timed_launches_from": "every 10th gradient of the timed region",
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    gradient = {"us": round(per_grad_s * 1e6, 2), "x_once_bytes": int(grad_bytes),
+                "x_once_gbs": round(grad_bytes / per_grad_s / 1e9, 1),
+                "x_once_frac": round(grad_bytes / per_grad_s / 1e9 / hbm_peak, 4),
+                "note": "one gradient evaluation of the launch's chains against X read once from HBM (the per-gradient "
+                        "HBM roofline)" + ("; the two-pass engine reads X twice when X exceeds L2" if per_pass else "")}
+    tensor = None
+    if xdt in ("bf16", "fp8"):
+        tensor = {"achieved_tflops": round(f_dom / t_dom / 1e12, 2), "peak": tc_peak, "unit": "TFLOP/s",
+                  "frac": round(f_dom / t_dom / 1e12 / tc_peak, 4),
+                  "flops": "algorithmic 2 n p C per contraction (the two-term coefficient MMAs of the logits pass "
+                           "issue twice that)", "peak_source": f"{peak_kind} bf16_tflops_sustained"}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -413,51 +571,29 @@ def run_ours(args):
                "note": "per step: upload the chain state (pinned host), one HMC iteration from it (plus the "
                        "gradient at the uploaded state), read the sample back"}
 
-    # effective samples per second: a fresh run from beta = 0, draws kept on the device
-    ess_info = None
-    if args.ess_iters > 0:
-        iters = args.ess_iters
-        draws = torch.empty((iters, chains, K - 1, p), dtype=tdt, device=dev)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h.sample(chains, L, eps, iters, seed + 7, beta0=zeros, samples=draws)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        secs = e0.elapsed_time(e1) / 1e3
-        burn = iters // 10
-        flat = draws[burn:].reshape(iters - burn, chains, -1)
-        m = flat.shape[2]
-        if m > 20000:      # a seeded subset of coordinates keeps the host-side FFTs small
-            idx = torch.from_numpy(np.sort(np.random.default_rng(0).choice(m, 20000, replace=False))).to(dev)
-            flat = flat[:, :, idx]
-        ess = diagnostics.ess(flat.double().cpu().numpy())
-        ess_info = {"iters": iters, "burn_in": burn, "coords": int(ess.size), "min": round(float(ess.min()), 2),
-                    "median": round(float(np.median(ess)), 2), "seconds": round(secs, 4),
-                    "min_per_s": round(float(ess.min()) / secs, 3), "median_per_s": round(float(np.median(ess)) / secs, 3),
-                    "note": "from beta = 0 over all iterations' sampling time; Geyer initial monotone sequence on the "
-                            "draws after burn-in, chains pooled"}
-        del draws, flat
-
     cpu, accuracy = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        X64 = X.astype(np.float64)
-        cpu = cpu_baseline(X64, y, spec, args.cpu_seconds)
-        accuracy = oracle_accuracy(h, X64, y, spec, xdt, tdt, dev)
-
+        cpu = cpu_baseline(X, y, spec, args.cpu_seconds)
+        accuracy = oracle_accuracy(h, X, y, spec, xdt, tdt, dev, sorted({0, chains - 1}))
     acc = sum(s["accepted"] for s in stats) / max(1, sum(s["iterations"] for s in stats))
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": xdt, "data": DATA_TEXT.get(args.workload, "synthetic (seeded, shaped like the paper's "
-                                                                  "high-dimensional multinomial setting)"), "config": config_of(args, spec, n * p * xb),
-        "roofline": roof, "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "xpass_gbs": round(achieved, 1), "accept_rate": round(acc, 4), "impl": "ours",
-        "clocks": clk.summary(), "engine": desc_all["engine"], "ess": ess_info, "tile_source": tile_source,
-        "tune": sorted(tune_table, key=lambda r: r["us"])[:6] if tune_table else None,
-        "tile": {k: desc[k] for k in ("S", "BM", "CR", "NSTAGE", "PC", "nclusters", "group_chains", "smem") if k in desc},
+        "scaling": "weak", "vs_baseline": None, "dtype": xdt,
+        "data": DATA_TEXT.get(args.workload, "synthetic (seeded, shaped like the paper's high-dimensional multinomial "
+                                             "setting; random-init coefficients)"),
+        "config": config_of(args, spec, n * p * xb),
+        "roofline": roof, "gradient_roofline": gradient, "passes": per_pass, "tensor": tensor,
+        "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "accept_rate": round(acc, 4), "impl": "ours", "clocks": clk.summary(), "engine": eng_name,
+        "tile_source": tile_source, "tune": sorted(tune_table, key=lambda r: r["us"])[:6] if tune_table else None,
+        "tile": {k: desc[k] for k in ("S", "BM", "CR", "NSTAGE", "PC", "nclusters", "group_chains", "smem",
+                                      "pass_a", "pass_b") if k in desc},
     }
+    h.close()
+    del X, Xin
+    if args.ess_iters > 0 and rank == 0:
+        line["ess"] = ess_comparison(args, dev)
     if "burn_in" in spec:
         its = spec["iters"]
         line["paper_run"] = {
@@ -467,7 +603,6 @@ def run_ours(args):
                     "context only: Sec. 3.2 reports 3 min 54 s for this run shape on real digit data on a Tesla K20"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -528,7 +663,7 @@ def run_batch_uneven(args):
     alg = sum(n * p * xb + 4 * n + 8 * p * (K - 1) * chains for (n, p, K) in shapes)
     per_launch = (fused_ms / 1e3) / max(fused_n, 1)
     launches_per_grad = fused_n / max(1, L)          # timed launches: the last iteration
-    peak, peak_kind = measured_peaks()
+    peak, _, peak_kind = measured_peaks()
     achieved = alg / (per_launch * launches_per_grad) / 1e9
     line = {
         "metric": METRIC, "value": round(world * grads / elapsed, 2), "unit": UNIT, "n_gpus": world,
@@ -698,34 +833,39 @@ def run_reference(args):
 
     spec = workload_spec(args)
     X, y, _, _ = synthetic.make_workload(args.workload)
-    X64 = np.asarray(X, dtype=np.float64)
+    n, p = X.shape
+    m = sample_rows(n, p, spec, 10.0)                        # rows the oracle runs on (all, or a leading block)
+    X64 = np.asarray(X[:m], dtype=np.float64)
+    ys = y[:m]
+    del X
     kind, scale = spec["prior"]
     K = spec["K"]
     rng = np.random.default_rng(0)
-    beta = np.zeros((K - 1, X64.shape[1]))
+    beta = np.zeros((K - 1, p))
     eta = rng.standard_normal(beta.shape)
     t0 = time.perf_counter()
-    g = model.grad_log_kernel(X64, y, beta, kind, scale)
+    g = model.grad_log_kernel(X64, ys, beta, kind, scale)
     t_one = time.perf_counter() - t0
     budget = 150.0 / max(1, args.steps + args.warmup)        # whole run within a few minutes
     per_step = max(1, min(spec["L"], int(budget / max(t_one, 1e-6))))
     for _ in range(args.warmup):
-        ohmc.leapfrog(X64, y, beta, eta, spec["eps"], per_step, kind, scale, grad0=g)
+        ohmc.leapfrog(X64, ys, beta, eta, spec["eps"], per_step, kind, scale, grad0=g)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        beta, eta, _, g = ohmc.leapfrog(X64, y, beta, eta, spec["eps"], per_step, kind, scale, grad0=g)
+        beta, eta, _, g = ohmc.leapfrog(X64, ys, beta, eta, spec["eps"], per_step, kind, scale, grad0=g)
     el = time.perf_counter() - t0
-    value = args.steps * per_step / el
-    cores = os.cpu_count()
-    sample = (f"each step: {per_step} FP64 leapfrog steps (one gradient each) of the full workload "
-              f"(a bounded sample of one {spec['L']}-step HMC iteration)")
+    value = args.steps * per_step / el * m / n               # the oracle's cost is linear in the rows
+    cores = blas_threads_default()
+    rows = "all rows" if m == n else f"the first {m} of {n} rows (rate scaled by rows / n: the cost is linear in rows)"
+    sample = (f"each step: {per_step} FP64 leapfrog steps (one gradient each) over {rows} "
+              f"(a bounded sample of one {spec['L']}-step HMC iteration); numpy/BLAS, default threads")
     line = {
-        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(args, spec, X64.nbytes // 2), "impl": "reference",
-        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": config_of(args, spec, n * p * XBYTES[spec["xdtype"]]), "impl": "reference",
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)

@@ -87,9 +87,14 @@ typedef struct {
   hmc_dtype x_storage;    /* storage type of X on the device (default HMC_F32)   */
   hmc_dtype state;        /* HMC_F64 or HMC_F32 (default HMC_F32)                */
   int32_t max_chains;     /* largest `chains` any later call may pass (default 1) */
-  int32_t engine;         /* 0 auto (tensor cores for BF16 / FP8 storage when the chains' columns fit
-                             TMEM, else CUDA cores), 1 CUDA-core fused kernel, 2 tensor-core fused
-                             kernel (BF16 or FP8 storage; MMA operands BF16, FP32 accumulation) */
+  int32_t engine;         /* 0 auto, 1 CUDA-core fused kernel, 2 tensor-core fused kernel (BF16 or
+                             FP8 storage; MMA operands BF16, FP32 accumulation), 3 tensor-core
+                             two-pass kernels (BF16 storage: logits, softmax and residual of every
+                             row tile in a first pass, X^T R in a second; no TMEM limit on the
+                             chains of one launch; X crosses HBM twice when larger than L2).  Auto:
+                             FP32 / FP64 storage on CUDA cores; FP8 on engine 2 when the chains'
+                             columns fit TMEM, else CUDA cores; BF16 on engine 2 when every chain
+                             fits one fused launch, else engine 3 */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
   int32_t tile[4];        /* {cluster size 1..16, exchange depth, sweep lookahead, ring slots}; 0 =
@@ -302,6 +307,14 @@ const char* hmc_describe(hmc_handle h);
  */
 hmc_status hmc_set_timing(hmc_handle h, int32_t enable);
 hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launches);
+
+/*
+ * hmc_first_pass_time -- for the two-pass tensor-core engine (opts.engine 3):
+ * the part of hmc_fused_kernel_time's total spent in the first pass (logits,
+ * softmax and residual), measured by an event between the two passes of every
+ * timed gradient; 0 for the single-pass engines.  Reset by hmc_set_timing.
+ */
+hmc_status hmc_first_pass_time(hmc_handle h, double* first_ms);
 
 /*
  * hmc_logpost_grad_noalloc -- log K and its gradient (the quantities of

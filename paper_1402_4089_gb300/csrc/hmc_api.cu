@@ -98,7 +98,9 @@ struct Problem {
 };
 
 struct FusedTimer {
-  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<cudaEvent_t> ev;   // pairs
+  std::vector<cudaEvent_t> mid;  // per pair: end of the first pass (two-pass engine), else unused
+  std::vector<char> has_mid;
   size_t used = 0;
 };
 
@@ -122,6 +124,7 @@ struct hmc_ctx {
   int timing_period = 1;    // events around every timing_period-th fused launch
   int64_t timing_seq = 0;   // fused launches issued since timing was enabled
   double timing_ms = 0.0;
+  double timing_first_ms = 0.0;   // two-pass engine: the first pass's share of timing_ms
   int64_t timing_launches = 0;
   FusedTimer timer;
   std::string desc;
@@ -465,15 +468,23 @@ void free_problem(Problem& P) {
 }
 
 // ----------------------------------------------------------------- launches
-hmc_status timer_pair(hmc_ctx* h, cudaEvent_t* a, cudaEvent_t* b) {
+hmc_status timer_pair(hmc_ctx* h, cudaEvent_t* a, cudaEvent_t* b, cudaEvent_t* m = nullptr) {
   FusedTimer& T = h->timer;
   while (T.ev.size() < 2 * (T.used + 1)) {
     cudaEvent_t e;
     HMC_CUDA(cudaEventCreate(&e));
     T.ev.push_back(e);
   }
+  while (T.mid.size() < T.used + 1) {
+    cudaEvent_t e;
+    HMC_CUDA(cudaEventCreate(&e));
+    T.mid.push_back(e);
+    T.has_mid.push_back(0);
+  }
   *a = T.ev[2 * T.used];
   *b = T.ev[2 * T.used + 1];
+  T.has_mid[T.used] = m ? 1 : 0;
+  if (m) *m = T.mid[T.used];
   T.used += 1;
   return HMC_OK;
 }
@@ -488,6 +499,10 @@ hmc_status timer_harvest(hmc_ctx* h) {
     HMC_CUDA(cudaEventElapsedTime(&ms, T.ev[2 * i], T.ev[2 * i + 1]));
     h->timing_ms += ms;
     h->timing_launches += 1;
+    if (T.has_mid[i]) {
+      HMC_CUDA(cudaEventElapsedTime(&ms, T.ev[2 * i], T.mid[i]));
+      h->timing_first_ms += ms;
+    }
   }
   T.used = 0;
   return HMC_OK;
@@ -504,12 +519,12 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
                             stream));
     const bool inject = h->inject_timeout;
     h->inject_timeout = false;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, em = nullptr;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     const bool timed = h->timing && (h->timing_seq++ % h->timing_period) == 0;
     if (timed) {
       HMC_CUDA(cudaStreamIsCapturing(stream, &cap));
-      HMC_TRY(timer_pair(h, &e0, &e1));
+      HMC_TRY(timer_pair(h, &e0, &e1, &em));
       HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal)
                                                     : cudaEventRecord(e0, stream));
     }
@@ -528,7 +543,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     L.zlogit = P.zlogit;
     L.chains = chains;
     L.spin_limit = inject ? 0 : h->spin_limit;   // fault injection: every bounded wait gives up at once
-    const cudaError_t le = tc2_launch(t2, L, stream);
+    const cudaError_t le =
+        tc2_launch(t2, L, stream, timed ? em : nullptr, cap == cudaStreamCaptureStatusActive);
     if (le != cudaSuccess) return fail(HMC_ECUDA, std::string("two-pass launch failed: ") + cudaGetErrorString(le));
     if (timed)
       HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e1, stream, cudaEventRecordExternal)
@@ -1141,6 +1157,7 @@ hmc_status hmc_destroy(hmc_handle h) {
   for (void* s : h->staging)
     if (s) cudaFree(s);
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->timer.mid) cudaEventDestroy(e);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->b_table) cudaFree(h->b_table);
   if (h->b_first) cudaFree(h->b_first);
@@ -1660,6 +1677,7 @@ hmc_status hmc_set_timing(hmc_handle h, int32_t enable) {
   h->timing_period = enable > 1 ? enable : 1;
   h->timing_seq = 0;
   h->timing_ms = 0.0;
+  h->timing_first_ms = 0.0;
   h->timing_launches = 0;
   h->timer.used = 0;
   return HMC_OK;
@@ -1669,6 +1687,12 @@ hmc_status hmc_fused_kernel_time(hmc_handle h, double* total_ms, int64_t* launch
   if (!h) return fail(HMC_EINVAL, "NULL handle");
   if (total_ms) *total_ms = h->timing_ms;
   if (launches) *launches = h->timing_launches;
+  return HMC_OK;
+}
+
+hmc_status hmc_first_pass_time(hmc_handle h, double* first_ms) {
+  if (!h) return fail(HMC_EINVAL, "NULL handle");
+  if (first_ms) *first_ms = h->timing_first_ms;
   return HMC_OK;
 }
 

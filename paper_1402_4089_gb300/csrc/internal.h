@@ -162,7 +162,8 @@ int tc2_threads();
 cudaError_t tc2_prepare();
 cudaError_t tc2_beta_boxes(const float* beta, void* out, int Km1, int gc, int chains, int N, int p_pad, int ngroups,
                            cudaStream_t s);
-cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream);
+// `between` (or nullptr): an event recorded between the two passes (a graph node when capturing).
+cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream, cudaEvent_t between, bool capturing);
 
 // Element-wise / reduction kernels (update.cu).
 struct UpdateArgs {

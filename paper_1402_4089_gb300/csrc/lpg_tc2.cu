@@ -583,7 +583,7 @@ static uint32_t pow2_cols(int cols) {
   return t;
 }
 
-cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream) {
+cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream, cudaEvent_t between, bool capturing) {
   {
     tc2::LogitArgs a{};
     a.xs = static_cast<const unsigned char*>(L.xs);
@@ -610,6 +610,10 @@ cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream
     tc2::logits_kernel<<<P.gridA, tc2::kThreads, P.smemA, stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (between) {
+      e = capturing ? cudaEventRecordWithFlags(between, stream, cudaEventRecordExternal) : cudaEventRecord(between, stream);
+      if (e != cudaSuccess) return e;
+    }
   }
   tc2::GradArgs b{};
   b.xs = static_cast<const unsigned char*>(L.xs);

@@ -80,6 +80,7 @@ def lib():
         "hmc_describe": (ctypes.c_char_p, [P]),
         "hmc_set_timing": (st, [P, I32]),
         "hmc_fused_kernel_time": (st, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "hmc_first_pass_time": (st, [P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -288,6 +289,12 @@ class Handle:
         n = ctypes.c_int64(0)
         _check(lib().hmc_fused_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def first_pass_time(self):
+        """Two-pass engine: milliseconds of the timed launches spent in the first pass."""
+        ms = ctypes.c_double(0)
+        _check(lib().hmc_first_pass_time(self._h, ctypes.byref(ms)))
+        return ms.value
 
     # -- helpers
     def _chains_of(self, beta, chains):

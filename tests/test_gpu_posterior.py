@@ -37,7 +37,7 @@ def oracle_posterior():
     return X, y, _means_and_mcse(ref["samples"][BURN:])
 
 
-@pytest.mark.parametrize("storage,engine", [("f32", 1), ("bf16", 2)])
+@pytest.mark.parametrize("storage,engine", [("f32", 1), ("bf16", 2), ("bf16", 3)])
 def test_posterior_means_within_three_mcse(cuda, oracle_posterior, storage, engine):
     import torch
     X, y, (m_o, se_o) = oracle_posterior

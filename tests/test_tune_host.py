@@ -55,8 +55,16 @@ def test_reduced_precision_tries_both_engines(fake):
     X, y = _xy()
     eng, tile, _ = tune.autotune(X, y, 3, x_storage="bf16", chains=1)
     assert (eng, tile) == (2, (8, 0, 0, 3))
-    assert {c[0] for c in calls} == {1, 2}
-    assert len(calls) == (len(tune.SIMT_S) + len(tune.TC_S)) * len(tune.RING)
+    assert {c[0] for c in calls} == {1, 2, 3}
+    assert len(calls) == (len(tune.SIMT_S) + len(tune.TC_S)) * len(tune.RING) + 1     # one two-pass candidate
+
+
+def test_two_pass_engine_can_win(fake):
+    calls, timer, _ = fake
+    timer({(2, 8, 3): 30.0, (3, 0, 0): 20.0})
+    X, y = _xy()
+    assert tune.autotune(X, y, 3, x_storage="bf16", chains=4)[:2] == (3, (0, 0, 0, 0))
+    assert [c for c in calls if c[0] == 3] == [(3, (0, 0, 0, 0), "free")]
 
 
 def test_no_tile_runs_leaves_the_choice_to_the_library(fake):
