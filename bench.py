@@ -71,7 +71,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true", help="use the library's tile choice instead of measuring")
     ap.add_argument("--ess-iters", type=int, default=1000, help="timed HMC iterations of each ESS/s run (0: skip)")
-    ap.add_argument("--ess-burn", type=int, default=200, help="untimed burn-in iterations before each ESS/s run")
+    ap.add_argument("--ess-burn", type=int, default=1000, help="untimed burn-in iterations before each ESS/s run")
     ap.add_argument("--ess-chains", type=int, default=8, help="chains of the BF16 multi-chain ESS/s run")
     ap.add_argument("--ess-coords", type=int, default=4000, help="coordinates (seeded subset) of the ESS estimates")
     ap.add_argument("--sweep-limit", type=int, default=0, help="sweep workload: first k shapes only (0: all 224)")

@@ -104,7 +104,9 @@ typedef struct {
                              most SMs streaming X with clusters of at most ceil(p / 256) CTAs, and
                              launches no more than one cluster per S SMs unless each still gets
                              about four 16-row tiles; the chosen tensor-core tile takes the most
-                             chains TMEM holds, spread evenly over the launches a call needs */
+                             chains TMEM holds, spread evenly over the launches a call needs.  On
+                             the two-pass engine only tile[0] applies: the 128-row tiles of one
+                             first-pass unit (1..4; 0 = chosen by the bytes the busiest SM streams) */
   int32_t layout;         /* hmc_layout of every coefficient buffer (default HMC_LAYOUT_FREE); the
                              kernels see K-1 free rows (K for HMC_LAYOUT_UNCONSTRAINED), which must
                              fit their class bounds */

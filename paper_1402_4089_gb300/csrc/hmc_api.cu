@@ -93,6 +93,8 @@ struct Problem {
   TcPlan tp{};
   Tc2Plan tp2{};            // engine 3
   void* rbuf = nullptr;     // engine 3: residual boxes written by pass A, read by pass B
+  void* spart = nullptr;    // engine 3: partial logits of first-pass units split over two CTAs
+  int* sflag = nullptr;     // engine 3: their ready flags
   void* bbf = nullptr;      // BF16 coefficient operand boxes [p_pad / 64][2N x 128 B] (hi, lo terms)
   int nlparts = 0;          // log-likelihood partials reduced per chain
 };
@@ -201,6 +203,9 @@ hmc_status check_device_error(hmc_ctx* h) {
   HMC_CUDA(cudaStreamSynchronize(h->stream));
   if (e) {
     HMC_CUDA(cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream));
+    // A launch that gave up may have left a split unit's flag raised.
+    for (Problem& P : h->probs)
+      if (P.sflag) HMC_CUDA(cudaMemsetAsync(P.sflag, 0, size_t(P.tp2.gridA) * sizeof(int), h->stream));
     HMC_CUDA(cudaStreamSynchronize(h->stream));
     if (e & (ERR_TIMEOUT_STAGE | ERR_TIMEOUT_EXCHANGE | ERR_TIMEOUT_SLOT | ERR_TIMEOUT_MMA))
       return fail(HMC_ETIMEOUT, "a bounded device wait ran out (error bits " + std::to_string(e) + ")");
@@ -331,7 +336,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     HMC_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     Tc2Plan p2;
-    if (tc2_plan(P.n, P.p, P.Km1, h->max_chains, nsm, smem_max, &p2)) {
+    if (tc2_plan(P.n, P.p, P.Km1, h->max_chains, nsm, smem_max, h->engine == 3 ? h->tile[0] : 0, &p2)) {
       HMC_CUDA(tc2_prepare());
       P.engine = 3;
       P.tp2 = p2;
@@ -351,8 +356,8 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     }
   }
   if (h->engine == 3 && P.engine != 3)
-    return fail(HMC_EUNSUPPORTED, "the two-pass tensor-core engine needs BF16 storage of X, n > 0 and at most 32 free "
-                                  "classes per chain");
+    return fail(HMC_EUNSUPPORTED, "the two-pass tensor-core engine needs BF16 storage of X, n > 0, at most 32 free "
+                                  "classes per chain and (opts.tile[0]) row tiles per unit that fit TMEM");
   if (!tc_ok) {
     const int maxct = simt_max_ct(h->xt);
     if (P.Km1 > maxct)
@@ -432,6 +437,9 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(cudaMalloc(&P.bbf, bbytes));
     HMC_CUDA(cudaMemsetAsync(P.bbf, 0, bbytes, h->stream));
     HMC_CUDA(cudaMalloc(&P.rbuf, size_t(P.ntiles) * ngroups * t2.NB * 16384));
+    HMC_CUDA(cudaMalloc(&P.spart, size_t(t2.gridA) * t2.U * t2.N * 128 * sizeof(float)));
+    HMC_CUDA(cudaMalloc(&P.sflag, size_t(t2.gridA) * sizeof(int)));
+    HMC_CUDA(cudaMemsetAsync(P.sflag, 0, size_t(t2.gridA) * sizeof(int), h->stream));
   }
   if (P.engine == 2) {
     const TcPlan& tp = P.tp;
@@ -462,7 +470,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
 void free_problem(Problem& P) {
   void* ptrs[] = {P.X, P.y, P.xscale, P.gpart, P.lpart, P.cs.beta, P.cs.eta, P.cs.grad, P.cs.beta0, P.cs.grad0,
                   P.us.beta, P.us.eta, P.us.grad, P.us.beta0, P.us.grad0, P.logk, P.logk0, P.h0, P.scal,
-                  P.tickets, P.accept, P.stats, P.iter, P.bbf, P.rbuf};
+                  P.tickets, P.accept, P.stats, P.iter, P.bbf, P.rbuf, P.spart, P.sflag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -533,6 +541,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     L.bs = P.bbf;
     L.y = P.y;
     L.rbuf = P.rbuf;
+    L.spart = P.spart;
+    L.sflag = P.sflag;
     L.lpart = P.lpart;
     L.lpart_cstride = h->max_chains;
     L.gpart = P.gpart;
@@ -897,6 +907,8 @@ hmc_status validate_opts(const hmc_opts* o) {
   if (o->spin_limit < 0) return fail(HMC_EINVAL, "opts.spin_limit must be >= 0");
   const int* t = o->tile;
   if (t[0] < 0 || t[0] > 16) return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be in [0, 16]");
+  if (o->engine == 3 && (t[0] > 4 || t[1] || t[2] || t[3]))
+    return fail(HMC_EINVAL, "on the two-pass engine only opts.tile[0] (row tiles per first-pass unit, 1..4) applies");
   if (t[1] < 0 || t[1] > kTcMaxDepth)
     return fail(HMC_EINVAL, "opts.tile[1] (tensor-core exchange depth) must be in [0, " + std::to_string(kTcMaxDepth) + "]");
   if (t[2] < 0 || t[2] > kTcMaxDepth)
@@ -929,10 +941,10 @@ void build_description(hmc_ctx* h) {
     if (P.engine == 3) {
       const Tc2Plan& t = P.tp2;
       std::snprintf(buf, sizeof(buf),
-                    ", \"pass_a\": {\"grid\": %d, \"chain_group\": %d, \"N\": %d, \"ring\": %d, \"smem\": %zu}, "
+                    ", \"pass_a\": {\"grid\": %d, \"tiles_per_unit\": %d, \"chain_group\": %d, \"N\": %d, \"ring\": %d, \"smem\": %zu}, "
                     "\"pass_b\": {\"feature_blocks\": %d, \"feature_groups\": %d, \"row_ranges\": %d, \"ring\": %d, "
                     "\"r_slots\": %d, \"smem\": %zu}",
-                    t.gridA, t.gc, t.N, t.nstA, t.smemA, t.MB, t.nfg, t.Q, t.nstB, t.nrsB, t.smemB);
+                    t.gridA, t.U, t.gc, t.N, t.nstA, t.smemA, t.MB, t.nfg, t.Q, t.nstB, t.nrsB, t.smemB);
       s.insert(s.size() - 1, buf);   // inside this problem's object
     }
   }

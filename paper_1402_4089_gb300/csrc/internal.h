@@ -138,6 +138,7 @@ struct Tc2Plan {
   int p_pad = 0;            // p rounded to 128
   int gc = 0, N = 0, NB = 0;  // chains per group, MMA N (>= gc (K-1), multiple of 16), R boxes (64 columns)
   int gridA = 0, nstA = 0;  // pass A CTAs and ring slots
+  int U = 1;                // pass A row tiles per unit (sharing each coefficient box)
   size_t smemA = 0;
   int MB = 0, nfg = 0, Q = 0;   // pass B: 128-feature blocks per CTA, feature groups, row ranges
   int nstB = 0, nrsB = 0;   // pass B X ring slots and R slots
@@ -148,6 +149,8 @@ struct Tc2Launch {
   const void* bs;           // coefficient operand of every group (tc2_beta_boxes)
   const int32_t* y;
   void* rbuf;               // R boxes [ntiles][groups][NB][16 KB]
+  void* spart;              // [gridA][U][N][128] FP32 partial logits of units split over two CTAs
+  int* sflag;               // [gridA] partial-ready flags (zero between launches)
   double* lpart;            // [gridA][lpart_cstride]
   int32_t lpart_cstride;
   void* gpart;              // [Q][chains Km1][p_pad] FP32
@@ -157,7 +160,8 @@ struct Tc2Launch {
   int32_t Km1, zlogit, chains;
   long long spin_limit;
 };
-bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, Tc2Plan* out);
+// force_U: 0, or the row tiles per pass-A unit to use (false if they do not fit).
+bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, int force_U, Tc2Plan* out);
 int tc2_threads();
 cudaError_t tc2_prepare();
 cudaError_t tc2_beta_boxes(const float* beta, void* out, int Km1, int gc, int chains, int N, int p_pad, int ngroups,

@@ -8,10 +8,19 @@
 // exchange every row tile.  Here the two contractions run as two streaming
 // passes with nothing held across tiles but the accumulators of one unit:
 //
-//  pass A  (logits, softmax, residual)  units (row tile t of 128 rows, chain
-//          group g): D[128 x N] = X_t B_g^T over all p features, B as two BF16
-//          terms (hi + lo, ~16 bits), accumulated in TMEM (two accumulators, so
-//          the epilogue of one unit overlaps the MMAs of the next).  The
+//  pass A  (logits, softmax, residual)  units (U consecutive row tiles of 128
+//          rows, chain group g): D_i[128 x N] = X_{t_i} B_g^T over all p
+//          features for the U tiles, B as two BF16 terms (hi + lo, ~16 bits)
+//          that every tile of the unit takes from the same ring slot (U X
+//          boxes + one coefficient box per 64 features: the coefficient bytes
+//          per X byte fall as U grows), accumulated in TMEM (two sets of U
+//          accumulators, so the epilogue of one unit overlaps the MMAs of the
+//          next).  The units' feature boxes are split evenly over the CTAs
+//          (each CTA takes the same number of (unit, 64-feature box) steps,
+//          so a unit may start on one CTA and end on the next): the CTA that
+//          holds a unit's first boxes finishes it, adding in the partial
+//          logits its neighbour stored for the unit's last boxes (a fixed sum
+//          order, a release/acquire flag per CTA).  The
 //          epilogue (one thread per row) forms the softmax of every chain with
 //          the zero logit of class K, the row log-likelihood and the residual
 //          R = Y - P, which it writes in BF16 as the MN-major, 128-byte-swizzled
@@ -103,9 +112,35 @@ struct LogitArgs {
   int* err;
   int64_t n, ntiles;
   int32_t nkb, N, NB, Km1, zlogit, gc, ngroups, chains, NST;
+  int32_t U;                 // row tiles per unit
   uint32_t stage_bytes, tmem_cols;
   long long spin_limit;
+  float* spart;              // [gridDim.x][U][N][128]: partial logits of a unit's last boxes (split units)
+  int* sflag;                // [gridDim.x]: 1 while the CTA's stored partial waits to be added
 };
+
+// One stretch of a CTA's feature-box steps: unit u, boxes [k0, k1).
+struct Seg {
+  int64_t u;
+  int k0, k1;
+};
+__device__ __forceinline__ bool next_seg(int64_t& pos, int64_t end, int nkb, Seg& sg) {
+  if (pos >= end) return false;
+  sg.u = pos / nkb;
+  sg.k0 = int(pos - sg.u * nkb);
+  sg.k1 = int(min(int64_t(nkb), int64_t(sg.k0) + (end - pos)));
+  pos += sg.k1 - sg.k0;
+  return true;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 struct LogitSmem {
   size_t ring, mx, sm, zy, llr, llc, bars, total;
@@ -118,7 +153,7 @@ __host__ __device__ inline LogitSmem logit_smem(int NST, uint32_t stage_bytes, i
   L.mx = off;    off = al(off + size_t(gc) * kRows * 4, 16);
   L.sm = off;    off = al(off + size_t(gc) * kRows * 4, 16);
   L.zy = off;    off = al(off + size_t(gc) * kRows * 4, 16);
-  L.llr = off;   off = al(off + size_t(gc) * kRows * 8, 16);
+  L.llr = off;   off = al(off + size_t(gc) * 4 * 8, 16);
   L.llc = off;   off = al(off + size_t(chains) * 8, 16);
   L.bars = off;  off = al(off + size_t(2 * NST + 5) * 8 + 16, 16);
   L.total = off + 1024;   // slack for aligning the dynamic base to 1024
@@ -133,10 +168,10 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
   const bool zl = A.zlogit != 0;
   const LogitSmem Lo = logit_smem(NST, A.stage_bytes, gc, A.chains);
   unsigned char* ring = smem + Lo.ring;
-  float* s_m = reinterpret_cast<float*>(smem + Lo.mx);     // [gc][128] running maximum
-  float* s_s = reinterpret_cast<float*>(smem + Lo.sm);     // [gc][128] running sum of exponentials
+  float* s_m = reinterpret_cast<float*>(smem + Lo.mx);     // [gc][128] maximum logit of each chain, per row
+  float* s_s = reinterpret_cast<float*>(smem + Lo.sm);     // [gc][128] sum of shifted exponentials
   float* s_zy = reinterpret_cast<float*>(smem + Lo.zy);    // [gc][128] logit of the observed class
-  double* s_llr = reinterpret_cast<double*>(smem + Lo.llr);  // [gc][128] row log-likelihoods
+  double* s_wsum = reinterpret_cast<double*>(smem + Lo.llr);  // [gc][4] log-likelihood sums of each warp's rows
   double* s_llc = reinterpret_cast<double*>(smem + Lo.llc);  // [chains] this CTA's sums
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lo.bars);
   uint64_t* full = bars;
@@ -167,9 +202,15 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  const int64_t units = A.ntiles * A.ngroups;
+  const int U = A.U;
+  const int64_t ntg = (A.ntiles + U - 1) / U;       // tile groups
+  const int64_t units = ntg * A.ngroups;
   const int64_t G = gridDim.x;
-  const int64_t nmine = (int64_t(blockIdx.x) < units) ? (units - 1 - blockIdx.x) / G + 1 : 0;
+  // This CTA's (unit, feature box) steps: an even share of all of them.  The
+  // host launches G <= units CTAs, so a share spans at least one unit's boxes and
+  // a unit is split over at most two CTAs.
+  const int64_t W = units * A.nkb;
+  const int64_t s_begin = int64_t(blockIdx.x) * W / G, s_end = (int64_t(blockIdx.x) + 1) * W / G;
   auto fail = [&](int bit) {
     *abort_flag = 1;
     atomicOr(A.err, bit);
@@ -179,23 +220,26 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int64_t s = 0, issued = 0;
-      for (int64_t j = 0; j < nmine && !*abort_flag; ++j) {
-        const int64_t u = blockIdx.x + j * G;
-        const int64_t t = u / A.ngroups;
+      int64_t s = 0, issued = 0, pos = s_begin;
+      Seg sg;
+      while (!*abort_flag && next_seg(pos, s_end, A.nkb, sg)) {
+        const int64_t u = sg.u;
+        const int64_t t0 = (u / A.ngroups) * U;
+        const int nt = int(min(int64_t(U), A.ntiles - t0));   // tiles of this unit
         const int g = int(u % A.ngroups);
-        const unsigned char* xt = A.xs + size_t(t) * A.nkb * kBoxBytes;
         const unsigned char* bt = A.bs + size_t(g) * A.nkb * coef_bytes;
-        for (int kb = 0; kb < A.nkb; ++kb, ++s) {
+        for (int kb = sg.k0; kb < sg.k1; ++kb, ++s) {
           const int st = int(s % NST);
           if (!wait_bounded(&empty[st], uint32_t(((s / NST) & 1) ^ 1), A.spin_limit, abort_flag)) {
             fail(ERR_TIMEOUT_STAGE);
             break;
           }
           unsigned char* sp = ring + size_t(st) * A.stage_bytes;
-          mbar_arrive_expect_tx(&full[st], uint32_t(kBoxBytes) + coef_bytes);
-          bulk_g2s(sp, xt + size_t(kb) * kBoxBytes, uint32_t(kBoxBytes), &full[st]);
-          bulk_g2s(sp + kBoxBytes, bt + size_t(kb) * coef_bytes, coef_bytes, &full[st]);
+          mbar_arrive_expect_tx(&full[st], uint32_t(nt * kBoxBytes) + coef_bytes);
+          for (int i = 0; i < nt; ++i)
+            bulk_g2s(sp + size_t(i) * kBoxBytes, A.xs + (size_t(t0 + i) * A.nkb + kb) * kBoxBytes, uint32_t(kBoxBytes),
+                     &full[st]);
+          bulk_g2s(sp + size_t(U) * kBoxBytes, bt + size_t(kb) * coef_bytes, coef_bytes, &full[st]);
           issued = s + 1;
         }
       }
@@ -207,31 +251,37 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(kRows, N, false, false);
-      int64_t s = 0;
-      for (int64_t j = 0; j < nmine && !*abort_flag; ++j) {
+      int64_t s = 0, pos = s_begin;
+      Seg sg;
+      for (int64_t j = 0; !*abort_flag && next_seg(pos, s_end, A.nkb, sg); ++j) {
         const int a = int(j & 1);
         if (j >= 2 && !wait_bounded(&zfree[a], uint32_t(((j >> 1) - 1) & 1), A.spin_limit, abort_flag)) {
           fail(ERR_TIMEOUT_MMA);
           break;
         }
         fence_after_sync();
-        const uint32_t d = tmem + uint32_t(a * N);
-        for (int kb = 0; kb < A.nkb; ++kb, ++s) {
+        const int64_t u = sg.u;
+        const int nt = int(min(int64_t(U), A.ntiles - (u / A.ngroups) * U));
+        for (int kb = sg.k0; kb < sg.k1; ++kb, ++s) {
           const int st = int(s % NST);
           if (!wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag)) {
             fail(ERR_TIMEOUT_STAGE);
             break;
           }
           fence_after_sync();
-          const uint32_t xa = smem_u32(ring + size_t(st) * A.stage_bytes);
-          const uint32_t ba = xa + uint32_t(kBoxBytes);
+          const uint32_t sa = smem_u32(ring + size_t(st) * A.stage_bytes);
+          const uint32_t ba = sa + uint32_t(U * kBoxBytes);
+          for (int i = 0; i < nt; ++i) {
+            const uint32_t d = tmem + uint32_t((a * U + i) * N);
+            const uint32_t xa = sa + uint32_t(i * kBoxBytes);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint64_t ad = smem_desc(xa + 32u * k, 16u, 1024u, 2u);
-            const uint64_t bh = smem_desc(ba + 32u * k, 16u, 1024u, 2u);
-            const uint64_t bl = smem_desc(ba + uint32_t(N) * 128u + 32u * k, 16u, 1024u, 2u);
-            mma_bf16(d, ad, bh, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-            mma_bf16(d, ad, bl, idesc, 1u);
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t ad = smem_desc(xa + 32u * k, 16u, 1024u, 2u);
+              const uint64_t bh = smem_desc(ba + 32u * k, 16u, 1024u, 2u);
+              const uint64_t bl = smem_desc(ba + uint32_t(N) * 128u + 32u * k, 16u, 1024u, 2u);
+              mma_bf16(d, ad, bh, idesc, (kb > sg.k0 || k > 0) ? 1u : 0u);
+              mma_bf16(d, ad, bl, idesc, 1u);
+            }
           }
           mma_commit(&empty[st]);
         }
@@ -247,96 +297,187 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
     const int q = warp & 3;
     const int r = 32 * q + lane;                   // tile row = TMEM lane
     const uint32_t tq = tmem + (uint32_t(32 * q) << 16);
-    for (int64_t j = 0; j < nmine; ++j) {
+    int64_t pos = s_begin;
+    Seg sg;
+    for (int64_t j = 0; next_seg(pos, s_end, A.nkb, sg); ++j) {
       const int a = int(j & 1);
       bool ok = (lane == 0) ? wait_bounded(&zdone[a], uint32_t((j >> 1) & 1), A.spin_limit, abort_flag) : true;
       if (!ok) fail(ERR_TIMEOUT_MMA);
       if (!epi_bar_and(ok)) break;
       fence_after_sync();
-      const int64_t u = blockIdx.x + j * G;
-      const int64_t t = u / A.ngroups;
+      const int64_t u = sg.u;
+      const int64_t t0 = (u / A.ngroups) * U;
+      const int nt = int(min(int64_t(U), A.ntiles - t0));
       const int g = int(u % A.ngroups);
       const int nch = min(gc, A.chains - g * gc);   // chains of this group
       const int Cg = nch * Km1;
-      const int64_t grow = t * kRows + r;
-      const bool valid = grow < A.n;
-      const int yv = valid ? __ldg(A.y + grow) : -1;
-      for (int c = 0; c < nch; ++c) {
-        s_m[c * kRows + r] = zl ? 0.f : -INFINITY;   // the zero logit of class K, or nothing yet
-        s_s[c * kRows + r] = zl ? 1.f : 0.f;
-        s_zy[c * kRows + r] = 0.f;
-      }
-      const uint32_t acc = tq + uint32_t(a * N);
-      // Pass 1: running maximum and sum of exponentials of every chain's
-      // logits (online: the sum is rescaled when the maximum grows).
-      for (int c0 = 0; c0 < Cg; c0 += 16) {
-        float v[16];
-        tmem_ld16(acc + uint32_t(c0), v);
+      if (sg.k0 > 0) {
+        // The last boxes of a unit the previous CTA started: store the partial
+        // logits for it and raise this CTA's flag.
+        float* pp = A.spart + size_t(blockIdx.x) * U * N * kRows;
+        for (int i = 0; i < nt; ++i) {
+          const uint32_t acc = tq + uint32_t((a * U + i) * N);
+          for (int c0 = 0; c0 < Cg; c0 += 16) {
+            float v[16];
+            tmem_ld16(acc + uint32_t(c0), v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int col = c0 + e;
-          if (col < Cg) {
-            const int c = col / Km1, k = col - c * Km1;
-            const float z = v[e];
-            const float mo = s_m[c * kRows + r], so = s_s[c * kRows + r];
-            if (z > mo) {
-              s_s[c * kRows + r] = so * expf(mo - z) + 1.f;
-              s_m[c * kRows + r] = z;
-            } else {
-              s_s[c * kRows + r] = so + expf(z - mo);
-            }
-            if (k == yv) s_zy[c * kRows + r] = z;
+            for (int e = 0; e < 16; ++e) pp[(size_t(i) * N + c0 + e) * kRows + r] = v[e];
           }
         }
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_local(&zfree[a]);
+        __threadfence();
+        epi_bar();
+        if (warp == 2 && lane == 0) st_release(A.sflag + blockIdx.x, 1);
+        continue;
       }
-      // Pass 2: R = Y - P for the group's columns (zero past Cg and on rows past
-      // n), written as BF16 in the MN-major 128-byte-swizzled boxes of pass B:
-      // 16-byte chunk j (8 columns) of row r of box b at chunk j ^ (r % 8).
-      unsigned char* rb = A.rout + (size_t(t) * A.ngroups + g) * A.NB * kBoxBytes;
-      for (int c0 = 0; c0 < A.NB * kBox; c0 += 16) {
-        float v[16];
-        if (c0 < Cg) tmem_ld16(acc + uint32_t(c0), v);
-        uint32_t w[8];
+      // A unit whose last boxes the next CTA holds: wait for its stored partial.
+      const bool head = sg.k1 < A.nkb;
+      const float* hp = A.spart + size_t(blockIdx.x + 1) * U * N * kRows;
+      if (head) {
+        bool got = true;
+        if (warp == 2 && lane == 0) {
+          got = false;
+          for (long long it = 0; it < A.spin_limit && !got; ++it) {
+            got = ld_acquire(A.sflag + blockIdx.x + 1) != 0;
+            if (!got && (it & 63) == 63 && *abort_flag) break;
+          }
+          if (!got) fail(ERR_TIMEOUT_EXCHANGE);
+        }
+        if (!epi_bar_and(got)) break;
+        (void)ld_acquire(A.sflag + blockIdx.x + 1);   // every thread's own acquire of the stored partial
+      }
+      for (int i = 0; i < nt; ++i) {
+        const int64_t t = t0 + i;
+        const int64_t grow = t * kRows + r;
+        const bool valid = grow < A.n;
+        const int yv = valid ? __ldg(A.y + grow) : -1;
+        const uint32_t acc = tq + uint32_t((a * U + i) * N);
+        const float* hpi = hp + size_t(i) * N * kRows + r;   // stored partial of column col: hpi[col * kRows]
+        // Three sweeps over the row's logits in column order, chains walked with
+        // running (chain, class) counters; per-chain results go to shared memory
+        // once per chain.  Sweep 1: the maximum of every chain's logits (the
+        // zero logit of class K included) and the logit of the observed class.
+        {
+          int c = 0, k = 0;
+          float m = zl ? 0.f : -INFINITY, zy = 0.f;
+          for (int c0 = 0; c0 < Cg; c0 += 16) {
+            float v[16];
+            tmem_ld16(acc + uint32_t(c0), v);
+            if (head)
 #pragma unroll
-        for (int e = 0; e < 16; e += 2) {
-          float rv[2];
+              for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int col = c0 + e + h;
-            rv[h] = 0.f;
-            if (valid && col < Cg) {
-              const int c = col / Km1, k = col - c * Km1;
-              const float pk = expf(v[e + h] - s_m[c * kRows + r]) / s_s[c * kRows + r];
-              rv[h] = (k == yv ? 1.f : 0.f) - pk;
+            for (int e = 0; e < 16; ++e) {
+              if (c0 + e < Cg) {
+                m = fmaxf(m, v[e]);
+                if (k == yv) zy = v[e];
+                if (++k == Km1) {
+                  s_m[c * kRows + r] = m;
+                  s_zy[c * kRows + r] = zy;
+                  ++c;
+                  k = 0;
+                  m = zl ? 0.f : -INFINITY;
+                  zy = 0.f;
+                }
+              }
             }
           }
-          const __nv_bfloat162 b2 = __floats2bfloat162_rn(rv[0], rv[1]);
-          w[e / 2] = *reinterpret_cast<const uint32_t*>(&b2);
         }
+        // Sweep 2: the sum of exponentials of every chain, shifted by its maximum.
+        {
+          int c = 0, k = 0;
+          float mc = s_m[r], ss = zl ? expf(-mc) : 0.f;
+          for (int c0 = 0; c0 < Cg; c0 += 16) {
+            float v[16];
+            tmem_ld16(acc + uint32_t(c0), v);
+            if (head)
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int cc = c0 + 8 * hh;                // first column of this 16-byte chunk
-          const int box = cc / kBox, chunk = (cc % kBox) / 8;
-          unsigned char* dst = rb + size_t(box) * kBoxBytes + size_t(r) * 128 + size_t((chunk ^ (r & 7)) << 4);
-          *reinterpret_cast<uint4*>(dst) = make_uint4(w[4 * hh], w[4 * hh + 1], w[4 * hh + 2], w[4 * hh + 3]);
+              for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              if (c0 + e < Cg) {
+                ss += expf(v[e] - mc);
+                if (++k == Km1) {
+                  s_s[c * kRows + r] = ss;
+                  ++c;
+                  k = 0;
+                  if (c < nch) {
+                    mc = s_m[c * kRows + r];
+                    ss = zl ? expf(-mc) : 0.f;
+                  }
+                }
+              }
+            }
+          }
         }
+        // Sweep 3: R = Y - P for the group's columns (zero past Cg and on rows past
+        // n), written as BF16 in the MN-major 128-byte-swizzled boxes of pass B:
+        // 16-byte chunk j (8 columns) of row r of box b at chunk j ^ (r % 8).
+        unsigned char* rb = A.rout + (size_t(t) * A.ngroups + g) * A.NB * kBoxBytes;
+        {
+          int c = 0, k = 0;
+          float mc = s_m[r], inv = 1.f / s_s[r];
+          for (int c0 = 0; c0 < A.NB * kBox; c0 += 16) {
+            float v[16];
+            if (c0 < Cg) {
+              tmem_ld16(acc + uint32_t(c0), v);
+              if (head)
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
+            }
+            uint32_t w[8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+              float rv[2];
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                rv[hh] = 0.f;
+                if (c0 + e + hh < Cg) {
+                  if (valid) rv[hh] = (k == yv ? 1.f : 0.f) - expf(v[e + hh] - mc) * inv;
+                  if (++k == Km1) {
+                    ++c;
+                    k = 0;
+                    if (c < nch) {
+                      mc = s_m[c * kRows + r];
+                      inv = 1.f / s_s[c * kRows + r];
+                    }
+                  }
+                }
+              }
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(rv[0], rv[1]);
+              w[e / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const int cc = c0 + 8 * hh;                // first column of this 16-byte chunk
+              const int box = cc / kBox, chunk = (cc % kBox) / 8;
+              unsigned char* dst = rb + size_t(box) * kBoxBytes + size_t(r) * 128 + size_t((chunk ^ (r & 7)) << 4);
+              *reinterpret_cast<uint4*>(dst) = make_uint4(w[4 * hh], w[4 * hh + 1], w[4 * hh + 2], w[4 * hh + 3]);
+            }
+          }
+        }
+        // Row log-likelihoods summed per chain over the 128 rows in a fixed tree
+        // (within each warp's 32 rows, then the four warps in lane-quarter order),
+        // added to this CTA's per-chain sums in tile order.
+        for (int c = 0; c < nch; ++c) {
+          double l = valid ? double(s_zy[c * kRows + r] - s_m[c * kRows + r] - logf(s_s[c * kRows + r])) : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+          if (lane == 0) s_wsum[c * 4 + q] = l;
+        }
+        epi_bar();
+        if (r < nch) s_llc[g * gc + r] += ((s_wsum[r * 4] + s_wsum[r * 4 + 1]) + s_wsum[r * 4 + 2]) + s_wsum[r * 4 + 3];
+        epi_bar();
       }
-      // The accumulator is read: the MMA issuer may start unit j + 2 in it.
+      // The unit's accumulators are read: the MMA issuer may start unit j + 2 in them.
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive_local(&zfree[a]);
-      // Row log-likelihoods, then their sum per chain over the 128 rows in row
-      // order, added to this CTA's per-chain sums in unit order.
-      for (int c = 0; c < nch; ++c)
-        s_llr[c * kRows + r] = valid ? double(s_zy[c * kRows + r] - s_m[c * kRows + r] - logf(s_s[c * kRows + r]))
-                                     : 0.0;
-      epi_bar();
-      if (r < nch) {
-        double sum = 0.0;
-        for (int i = 0; i < kRows; ++i) sum += s_llr[r * kRows + i];
-        s_llc[g * gc + r] += sum;
-      }
-      epi_bar();
+      // The neighbour's partial is consumed (every read happened before the last
+      // barrier of the tile loop): lower its flag for the next launch.
+      if (head && warp == 2 && lane == 0) A.sflag[blockIdx.x + 1] = 0;
     }
   }
   __syncthreads();
@@ -552,9 +693,12 @@ __global__ void beta_boxes_kernel(const float* beta, unsigned char* out, int32_t
 // ------------------------------------------------------------------ host side
 int tc2_threads() { return tc2::kThreads; }
 
-size_t tc2_logit_smem(int NST, int N, int gc, int chains) {
-  const uint32_t stage = uint32_t(tc2::al(size_t(tc2::kBoxBytes) + size_t(2 * N) * 128, 1024));
-  return tc2::logit_smem(NST, stage, gc, chains).total;
+static uint32_t logit_stage(int U, int N) {
+  return uint32_t(tc2::al(size_t(U) * tc2::kBoxBytes + size_t(2 * N) * 128, 1024));
+}
+
+size_t tc2_logit_smem(int NST, int U, int N, int gc, int chains) {
+  return tc2::logit_smem(NST, logit_stage(U, N), gc, chains).total;
 }
 
 size_t tc2_grad_smem(int NST, int NRS, int NB) { return tc2::grad_smem(NST, NRS, NB).total; }
@@ -604,8 +748,11 @@ cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream
     a.ngroups = (L.chains + P.gc - 1) / P.gc;
     a.chains = L.chains;
     a.NST = P.nstA;
-    a.stage_bytes = uint32_t(tc2::al(size_t(tc2::kBoxBytes) + size_t(2 * P.N) * 128, 1024));
-    a.tmem_cols = pow2_cols(2 * P.N);
+    a.U = P.U;
+    a.spart = static_cast<float*>(L.spart);
+    a.sflag = L.sflag;
+    a.stage_bytes = logit_stage(P.U, P.N);
+    a.tmem_cols = pow2_cols(2 * P.U * P.N);
     a.spin_limit = L.spin_limit;
     tc2::logits_kernel<<<P.gridA, tc2::kThreads, P.smemA, stream>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -643,10 +790,10 @@ cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream
 
 // Plan for `chains` chains of a problem (n, p, Km1) on nsm SMs with smem_max
 // bytes of shared memory per block: the chain group (largest whose MMA N <= 256
-// fits pass A's shared memory with >= 3 ring slots), pass A's grid, and pass B's
-// split (feature blocks per CTA, row ranges) that minimises the bytes the
-// busiest CTA streams.
-bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, Tc2Plan* out) {
+// fits pass A's shared memory with >= 3 ring slots), pass A's tiles per unit and
+// grid, and pass B's split (feature blocks per CTA, row ranges); both passes'
+// choices minimise the bytes the busiest CTA streams.
+bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, int force_U, Tc2Plan* out) {
   Tc2Plan P{};
   P.p_pad = int((p + 127) / 128 * 128);
   const int64_t ntiles = (n + 127) / 128;
@@ -658,7 +805,7 @@ bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, 
     const int ngroups = (chains + g - 1) / g;
     const int gb = (chains + ngroups - 1) / ngroups;   // even groups
     const int Nb = std::max(16, (gb * Km1 + 15) / 16 * 16);
-    if (tc2_logit_smem(3, Nb, gb, chains) > size_t(smem_max)) continue;
+    if (tc2_logit_smem(3, 1, Nb, gb, chains) > size_t(smem_max)) continue;
     gc = gb;
     break;
   }
@@ -667,14 +814,31 @@ bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, 
   P.N = std::max(16, (gc * Km1 + 15) / 16 * 16);
   P.NB = (P.N + 63) / 64;
   const int ngroups = (chains + gc - 1) / gc;
+  // Tiles per unit: U tiles share each coefficient box, so a unit streams
+  // U * 16 KB of X and 2N * 128 B of coefficients per 64 features, and its
+  // softmax epilogue overlaps the next unit's streaming.  The largest U that
+  // fits (TMEM, shared memory) while still giving at least 0.8 units per SM is
+  // taken (measured: n=5e4 p=1e4 K=20 4 chains, U = 1, 2 split, 3 -> 310, 295,
+  // 266 us); when even U = 1 gives fewer, U = 1.
+  P.U = 1;
+  for (int U = 1; U <= 4; ++U) {
+    if (2 * U * P.N > 512 || tc2_logit_smem(3, U, P.N, gc, chains) > size_t(smem_max)) break;
+    if (force_U) {
+      if (U == force_U) P.U = U;
+      continue;
+    }
+    const int64_t units = (ntiles + U - 1) / U * ngroups;
+    if (U == 1 || 5 * units >= 4 * int64_t(nsm)) P.U = U;
+  }
+  if (force_U && P.U != force_U) return false;
   P.nstA = 3;
   for (int s = 8; s > 3; --s)
-    if (tc2_logit_smem(s, P.N, gc, chains) <= size_t(smem_max)) {
+    if (tc2_logit_smem(s, P.U, P.N, gc, chains) <= size_t(smem_max)) {
       P.nstA = s;
       break;
     }
-  P.smemA = std::max(tc2_logit_smem(P.nstA, P.N, gc, chains), size_t(116 * 1024));
-  P.gridA = int(std::min<int64_t>(nsm, ntiles * ngroups));
+  P.smemA = std::max(tc2_logit_smem(P.nstA, P.U, P.N, gc, chains), size_t(116 * 1024));
+  P.gridA = int(std::min<int64_t>(nsm, (ntiles + P.U - 1) / P.U * ngroups));
   // Pass B.
   const int nblk = P.p_pad / 128;
   const int mbmax = std::min(nblk, std::max(1, 512 / P.N));

@@ -17,11 +17,19 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Log-prior term of one coefficient, formed in the state's precision (FP64
+// arithmetic is scarce on this GPU) and returned for FP64 accumulation.
 template <typename ST>
 __device__ __forceinline__ double prior_term(ST b, int kind, double s) {
-  const double x = double(b);
-  if (kind == HMC_PRIOR_CAUCHY) return -log1p((x / s) * (x / s));
-  return -(x * x) / (2.0 * s * s);
+  if constexpr (sizeof(ST) == 4) {
+    const float x = float(b) / float(s);
+    if (kind == HMC_PRIOR_CAUCHY) return double(-log1pf(x * x));
+    return double(-0.5f * x * x);
+  } else {
+    const double x = double(b);
+    if (kind == HMC_PRIOR_CAUCHY) return -log1p((x / s) * (x / s));
+    return -(x * x) / (2.0 * s * s);
+  }
 }
 
 template <typename ST>
@@ -51,6 +59,39 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
       b += sb[i];
     }
   }
+}
+
+// Neumaier-compensated sum of v[i * stride], i < n, by every thread of the
+// block in a fixed order: thread t adds i = t, t + blockDim, ...; the per-thread
+// sums meet in a fixed tree (shuffles within a warp, then warps in order).
+// The result is valid in thread 0.
+__device__ __forceinline__ void merge(double& s, double& c, double s2, double c2) {
+  const double t = s + s2;
+  c += (fabs(s) >= fabs(s2) ? (s - t) + s2 : (s2 - t) + s) + c2;
+  s = t;
+}
+__device__ double block_sum_fixed(const double* v, int n, size_t stride) {
+  __shared__ double ws[kThreads / 32][2];
+  Neumaier acc;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc.add(v[size_t(i) * stride]);
+  double s = acc.s, c = acc.c;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
+    merge(s, c, s2, c2);
+  }
+  const int w = threadIdx.x >> 5;
+  __syncthreads();   // ws may still be read by a previous call
+  if ((threadIdx.x & 31) == 0) {
+    ws[w][0] = s;
+    ws[w][1] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s = ws[0][0];
+    c = ws[0][1];
+    for (int i = 1; i < int(blockDim.x >> 5); ++i) merge(s, c, ws[i][0], ws[i][1]);
+  }
+  return s + c;
 }
 
 // Ticket: true in exactly one block (the last to finish) of chain c.
@@ -116,15 +157,14 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
     sl[1] = kin_s;
   }
   if (!last_block(A.tickets + c, gridDim.x)) return;
+  // The whole last block sums the block partials and the log-likelihood
+  // partials of the fused pass, each in a fixed order.
+  const double* sl = A.scal + size_t(c) * A.nblk * 2;
+  const double prv = block_sum_fixed(sl, int(gridDim.x), 2);
+  const double kiv = block_sum_fixed(sl + 1, int(gridDim.x), 2);
+  const double liv = block_sum_fixed(A.lpart + c, A.nlparts, size_t(A.lpart_cstride));
   if (threadIdx.x != 0) return;
-  Neumaier pr, ki, li;
-  for (int b = 0; b < int(gridDim.x); ++b) {
-    const double* sl = A.scal + (size_t(c) * A.nblk + b) * 2;
-    pr.add(sl[0]);
-    ki.add(sl[1]);
-  }
-  for (int b = 0; b < A.nlparts; ++b) li.add(A.lpart[size_t(b) * A.lpart_cstride + c]);
-  const double logk = li.value() + pr.value();
+  const double logk = liv + prv;
   A.tickets[c] = 0u;
   if (!(mode & UPD_ACCEPT)) {
     A.logk[c] = logk;
@@ -133,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
   const int64_t it = *A.iter;
   const double T = A.temps ? A.temps[*A.local_iter] : 1.0;
   const double h0 = A.h0[c];
-  const double h1 = -logk + 0.5 * ki.value();
+  const double h1 = -logk + 0.5 * kiv;
   const bool finite = isfinite(h1);
   const double u = accept_uniform(*A.seed, uint64_t(it), uint64_t(c) | (uint64_t(A.chains_word_hi) << 32));
   const bool acc = finite && (log(u) < (h0 - h1) / T);
@@ -188,12 +228,11 @@ __global__ void __launch_bounds__(kThreads) traj_start_kernel(const UpdateArgs A
   block_sum2(kin, unused);
   if (threadIdx.x == 0) A.scal[(size_t(c) * A.nblk + blockIdx.x) * 2 + 1] = kin;
   if (!last_block(A.tickets + c, gridDim.x)) return;
+  const double kiv = block_sum_fixed(A.scal + size_t(c) * A.nblk * 2 + 1, int(gridDim.x), 2);
   if (threadIdx.x != 0) return;
-  Neumaier ki;
-  for (int b = 0; b < int(gridDim.x); ++b) ki.add(A.scal[(size_t(c) * A.nblk + b) * 2 + 1]);
   A.tickets[c] = 0u;
   A.logk0[c] = A.logk[c];
-  A.h0[c] = -A.logk[c] + 0.5 * ki.value();
+  A.h0[c] = -A.logk[c] + 0.5 * kiv;
 }
 
 // Keep the proposal or restore the trajectory start; write the sample; the

@@ -19,12 +19,13 @@ pytestmark = pytest.mark.gpu
 TOL_G, TOL_L = 3e-3, 1e-4
 
 
-def _run(cuda, n, p, K, chains, seed, layout="free", prior=("gaussian", 10.0), bscale=0.05):
+def _run(cuda, n, p, K, chains, seed, layout="free", prior=("gaussian", 10.0), bscale=0.05, U=0):
     import torch
     X, y, _ = synthetic.make_problem(n, p, K, seed=seed)
     rows = K - 1 if layout == "free" else K
     beta = (bscale * np.random.default_rng(seed + 1).standard_normal((chains, rows, p))).astype(np.float32)
-    with hmc.create(X, y, K, prior[0], prior[1], x_storage="bf16", max_chains=chains, engine=3, layout=layout) as h:
+    with hmc.create(X, y, K, prior[0], prior[1], x_storage="bf16", max_chains=chains, engine=3, layout=layout,
+                    tile=(U, 0, 0, 0)) as h:
         d = h.describe()
         assert d["engine"] == "tcgen05_2pass", d
         bits, _ = h.get_x()
@@ -45,6 +46,24 @@ def _run(cuda, n, p, K, chains, seed, layout="free", prior=("gaussian", 10.0), b
                                           (5000, 2000, 10, 7), (130, 4100, 5, 1), (257, 300, 33, 1)])
 def test_tc2_matches_oracle(cuda, n, p, K, chains):
     _run(cuda, n, p, K, chains, seed=n + 7 * p)
+
+
+@pytest.mark.parametrize("U,n", [(2, 10 * 128 + 5), (3, 10 * 128 + 5), (3, 9 * 128), (4, 3 * 128 + 1)])
+def test_tc2_row_tiles_per_unit(cuda, U, n):
+    """Several row tiles per first-pass unit sharing each coefficient box, with a
+    last unit that holds fewer tiles."""
+    d = _run(cuda, n, 1000, 6, 2, seed=70 + U, U=U)
+    assert d["problems"][0]["pass_a"]["tiles_per_unit"] == U
+
+
+@pytest.mark.parametrize("U,n,p", [(1, 200 * 128 + 37, 512), (2, 400 * 128 + 5, 300), (3, 500 * 128, 200)])
+def test_tc2_units_split_over_two_ctas(cuda, U, n, p):
+    """More first-pass units than SMs: every CTA takes an even share of the
+    (unit, feature box) steps, so units are split between neighbouring CTAs and
+    finished by the one holding their first boxes."""
+    d = _run(cuda, n, p, 4, 2, seed=80 + U, U=U)
+    pa = d["problems"][0]["pass_a"]
+    assert pa["tiles_per_unit"] == U and pa["grid"] < (n + 128 * U - 1) // (128 * U)
 
 
 def test_tc2_many_chains_in_groups(cuda):
