@@ -47,6 +47,7 @@ KERNEL_SOURCES = {
                 "paper_1402_4089_gb300/csrc/device_common.cuh"],
     "tcgen05_2pass": ["paper_1402_4089_gb300/csrc/lpg_tc2.cu", "paper_1402_4089_gb300/csrc/tc_common.cuh",
                       "paper_1402_4089_gb300/csrc/device_common.cuh"],
+    "simt_2pass": ["paper_1402_4089_gb300/csrc/lpg_simt2.cu", "paper_1402_4089_gb300/csrc/device_common.cuh"],
 }
 
 
@@ -499,7 +500,7 @@ def run_ours(args):
     groups = -(-chains // desc["group_chains"])
     # traj_start + per leapfrog step (per chain group: [operand boxes +] the pass(es), then the
     # reduce/update) + select
-    per_group = {"simt": 1, "tcgen05": 2, "tcgen05_2pass": 3}[eng_name]
+    per_group = {"simt": 1, "tcgen05": 2, "tcgen05_2pass": 3, "simt_2pass": 2}[eng_name]
     launches_per_step = 1 + L * (groups * per_group + 1) + 1
 
     # rooflines: the gradient (X once) and the dominant kernel
@@ -525,7 +526,8 @@ def run_ours(args):
                         "tflops": round(2.0 * n * p * c_launch / v[0] / 1e12, 1)} for k, v in passes.items()}
     else:
         t_dom, b_dom, f_dom = per_grad_s, grad_bytes, grad_flops
-        kernel = ("lpg_tc_kernel (tcgen05)" if eng_name == "tcgen05" else "lpg_kernel (CUDA cores)")
+        kernel = {"tcgen05": "lpg_tc_kernel (tcgen05)", "simt": "lpg_kernel (CUDA cores)",
+                  "simt_2pass": "simt2::logits_kernel + simt2::grad_kernel (CUDA cores, both passes)"}[eng_name]
         traffic = recorded_traffic(args.workload, xdt, eng_name)
         per_pass = None
     achieved = b_dom / t_dom / 1e9
@@ -728,7 +730,7 @@ def run_sweep(args):
             try:
                 h = hmc.create(X, y, K, "cauchy", 1.0, x_storage="f32", max_chains=1, stream=stream, layout=layout)
             except hmc.HmcError as e:
-                rows.append([layout, n, K, p, None, None, None, None, str(e)[:120]])
+                rows.append([layout, n, K, p, None, None, None, None, str(e)[:120], None])
                 continue
             with torch.cuda.stream(stream):
                 beta = torch.from_numpy(B.astype(np.float32)[None]).to(dev)
@@ -750,6 +752,7 @@ def run_sweep(args):
                 stream.synchronize()
             g_us = e0.elapsed_time(e1) * 1e3 / 5
             lf_us = e2.elapsed_time(e3) * 1e3 / 5
+            eng = h.describe()["engine"]
             h.close()
             cpu_us = None
             if n * p <= args.sweep_oracle_np:
@@ -759,7 +762,7 @@ def run_sweep(args):
                 model.grad_log_kernel_layout(X64, y, B, "cauchy", 1.0, layout)
                 cpu_us = (time.perf_counter() - t0) * 1e6
             rows.append([layout, n, K, p, round(g_us, 2), round(lf_us, 2), None if cpu_us is None else round(cpu_us, 1),
-                         None if cpu_us is None else round(cpu_us / g_us, 2), None])
+                         None if cpu_us is None else round(cpu_us / g_us, 2), None, eng])
     wall = time.perf_counter() - t_start
     # The headline value uses the same shapes as the reference arm: identifiable
     # model, N p <= the oracle cap (where the GPU runs the shape).
@@ -778,10 +781,11 @@ def run_sweep(args):
                    "oracle_np_cap": args.sweep_oracle_np},
         "impl": "ours", "gpu_launches": None, "cpu_baseline": None, "e2e": None, "roofline": None,
         "sweep": {"columns": ["model", "N", "K", "p", "gpu_grad_us", "gpu_leapfrog_step_us", "oracle_grad_us",
-                              "speedup_grad", "unsupported"],
+                              "speedup_grad", "unsupported", "engine"],
                   "rows": rows, "wall_s": round(wall, 1),
                   "value_all_shapes": round(float(np.median(every)), 2) if every else None,
                   "unsupported_shapes": sum(1 for r in rows if r[4] is None),
+                  "engines": {e: sum(1 for r in rows if r[9] == e) for e in sorted({r[9] for r in rows if r[9]})},
                   "speedup_median": {k: (round(float(np.median(v)), 1) if v else None) for k, v in sp.items()},
                   "speedup_max": {k: (round(float(np.max(v)), 1) if v else None) for k, v in sp.items()},
                   "gpu_grad_us_median_large": round(float(np.median([r[4] for r in big])), 2) if big else None,

@@ -91,10 +91,15 @@ typedef struct {
                              FP8 storage; MMA operands BF16, FP32 accumulation), 3 tensor-core
                              two-pass kernels (BF16 storage: logits, softmax and residual of every
                              row tile in a first pass, X^T R in a second; no TMEM limit on the
-                             chains of one launch; X crosses HBM twice when larger than L2).  Auto:
-                             FP32 / FP64 storage on CUDA cores; FP8 on engine 2 when the chains'
-                             columns fit TMEM, else CUDA cores; BF16 on engine 2 when every chain
-                             fits one fused launch, else engine 3 */
+                             chains of one launch; X crosses HBM twice when larger than L2), 4
+                             CUDA-core two-pass kernels (FP32 / FP64 storage: row logits, softmax
+                             and residual in a first pass, X^T R in a second; up to 64 coefficient
+                             columns per launch, no tile options).  Auto: FP32 / FP64 storage on
+                             engine 1, or on engine 4 where no engine-1 tile fits (wide problems with
+                             many classes: FP32 X with K - 1 > 12 and p > 10240) or K - 1 exceeds
+                             its class bound; FP8 on engine 2 when the chains' columns fit TMEM,
+                             else CUDA cores; BF16 on engine 2 when every chain fits one fused
+                             launch, else engine 3 */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
   int32_t tile[4];        /* {cluster size 1..16, exchange depth, sweep lookahead, ring slots}; 0 =

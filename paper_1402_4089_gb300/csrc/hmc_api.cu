@@ -89,10 +89,11 @@ struct Problem {
   int nblk = 1;
   int64_t state_elems = 0;  // max_chains * Km1 * p_pad
   // tensor-core engines
-  int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel, 3 tensor-core two-pass
+  int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel, 3 tensor-core two-pass,
+                            // 4 CUDA-core two-pass
   TcPlan tp{};
   Tc2Plan tp2{};            // engine 3
-  void* rbuf = nullptr;     // engine 3: residual boxes written by pass A, read by pass B
+  void* rbuf = nullptr;     // engines 3, 4: residuals written by the first pass, read by the second
   void* spart = nullptr;    // engine 3: partial logits of first-pass units split over two CTAs
   int* sflag = nullptr;     // engine 3: their ready flags
   void* bbf = nullptr;      // BF16 coefficient operand boxes [p_pad / 64][2N x 128 B] (hi, lo terms)
@@ -359,38 +360,64 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     return fail(HMC_EUNSUPPORTED, "the two-pass tensor-core engine needs BF16 storage of X, n > 0, at most 32 free "
                                   "classes per chain and (opts.tile[0]) row tiles per unit that fit TMEM");
   if (!tc_ok) {
-    const int maxct = simt_max_ct(h->xt);
-    if (P.Km1 > maxct)
-      return fail(HMC_EUNSUPPORTED, "free classes per chain " + std::to_string(P.Km1) + " exceed the CUDA-core kernel's class bound " +
-                                        std::to_string(maxct));
-    P.group_chains = balanced_group(h->max_chains, std::max(1, std::min(h->max_chains, maxct / P.Km1)));
-    P.ct_launch = P.group_chains * P.Km1;
     if (h->tile[1] || h->tile[2])
-      return fail(HMC_EINVAL, "tile[1] and tile[2] must be 0 on the CUDA-core engine (fixed super-tile height)");
-    P.ntiles = (P.n + kSimtRows - 1) / kSimtRows;
-    SimtTile tc{};
-    HMC_CUDA(simt_choose(h->xt, P.ct_launch, P.p, P.ntiles, h->tile[0], h->tile[3], 0, &tc));
-    if (!tc.S)
-      return fail(HMC_EUNSUPPORTED, "no CUDA-core tile configuration fits this problem (p too large for the cluster sizes "
-                                    "available, or the requested tile does not fit)");
-    P.S = tc.S;
-    P.BM = kSimtRows;
-    P.CR = kSimtRows;
-    P.NT = tc.NT;
-    P.NWL = tc.NWL;
-    P.NSTAGE = tc.NSTAGE;
-    P.PC = tc.PC;
-    P.smem = tc.smem;
-    P.p_pad = P.S * P.PC;
-    const int maxclu = tc.maxclu;
-    // Every cluster adds one partial slice to the fixed-order reduction, so
-    // clusters beyond one per S SMs are launched only while each still gets
-    // about four tiles.
+      return fail(HMC_EINVAL, "tile[1] and tile[2] must be 0 on the CUDA-core engines");
+    const int maxct = simt_max_ct(h->xt);
     int dev = 0, nsm = 0;
     HMC_CUDA(cudaGetDevice(&dev));
     HMC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t useful = std::max<int64_t>(nsm / P.S, (P.ntiles + 3) / 4);
-    P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>({int64_t(maxclu), P.ntiles, useful})));
+    // Fused CUDA-core pass first (X read once); two CUDA-core passes where it
+    // has no tile (wide problems with many classes: the coefficient slice and
+    // the ring of row tiles do not fit one cluster) or more classes per chain
+    // than it handles.
+    SimtTile tc{};
+    if (h->engine != 4 && P.Km1 <= maxct) {
+      P.group_chains = balanced_group(h->max_chains, std::max(1, std::min(h->max_chains, maxct / P.Km1)));
+      P.ct_launch = P.group_chains * P.Km1;
+      P.ntiles = (P.n + kSimtRows - 1) / kSimtRows;
+      HMC_CUDA(simt_choose(h->xt, P.ct_launch, P.p, P.ntiles, h->tile[0], h->tile[3], 0, &tc));
+    }
+    const bool two = (h->xt == HMC_F32 || h->xt == HMC_F64) && P.n > 0 && P.Km1 <= simt2_max_c() &&
+                     (h->engine == 4 || (h->engine == 0 && !tc.S && !h->tile[0] && !h->tile[3]));
+    if (two) {
+      P.engine = 4;
+      P.group_chains = balanced_group(h->max_chains, std::max(1, std::min(h->max_chains, simt2_max_c() / P.Km1)));
+      P.ct_launch = P.group_chains * P.Km1;
+      P.S = 1;
+      P.p_pad = (P.p + 3) / 4 * 4;
+      P.PC = P.p_pad;
+      P.BM = 1;
+      P.CR = 1;
+      P.NT = 256;
+      P.NSTAGE = 0;
+      P.smem = 0;
+      P.ntiles = P.n;
+      P.nclusters = simt2_row_ranges(P.n, P.p_pad, nsm);   // partial gradient slices of the second pass
+    } else if (h->engine == 4) {
+      return fail(HMC_EUNSUPPORTED, "the two-pass CUDA-core engine needs FP32 or FP64 storage of X, n > 0 and at most " +
+                                        std::to_string(simt2_max_c()) + " free classes per chain");
+    } else if (P.Km1 > maxct) {
+      return fail(HMC_EUNSUPPORTED, "free classes per chain " + std::to_string(P.Km1) +
+                                        " exceed the CUDA-core kernel's class bound " + std::to_string(maxct));
+    } else if (!tc.S) {
+      return fail(HMC_EUNSUPPORTED, "no CUDA-core tile configuration fits this problem (p too large for the cluster sizes "
+                                    "available, or the requested tile does not fit)");
+    } else {
+      P.S = tc.S;
+      P.BM = kSimtRows;
+      P.CR = kSimtRows;
+      P.NT = tc.NT;
+      P.NWL = tc.NWL;
+      P.NSTAGE = tc.NSTAGE;
+      P.PC = tc.PC;
+      P.smem = tc.smem;
+      P.p_pad = P.S * P.PC;
+      // Every cluster adds one partial slice to the fixed-order reduction, so
+      // clusters beyond one per S SMs are launched only while each still gets
+      // about four tiles.
+      const int64_t useful = std::max<int64_t>(nsm / P.S, (P.ntiles + 3) / 4);
+      P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>({int64_t(tc.maxclu), P.ntiles, useful})));
+    }
   }
 
   // X: convert on the device into the storage type, zero-padded columns.
@@ -402,7 +429,8 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(cudaMemcpyAsync(tmp, X, in_bytes, cudaMemcpyHostToDevice, h->stream));
     Xd = tmp;
   }
-  const int64_t n_alloc = P.engine >= 2 ? (P.n + 127) / 128 * 128 : P.n;
+  const bool tiled = P.engine == 2 || P.engine == 3;   // X in 128-row tensor-core tiles
+  const int64_t n_alloc = tiled ? (P.n + 127) / 128 * 128 : P.n;
   HMC_CUDA(cudaMalloc(&P.X, std::max<size_t>(16, size_t(n_alloc) * P.p_pad * xb)));
   if (h->xt == HMC_FP8E4M3) {
     HMC_CUDA(cudaMalloc(&P.xscale, size_t(P.p_pad) * sizeof(float)));
@@ -411,7 +439,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   if (P.n > 0) {
     if (P.engine == 2 && h->xt == HMC_FP8E4M3)
       HMC_CUDA(tc_x_to_tiles_fp8(x_dtype, Xd, P.xscale, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
-    else if (P.engine >= 2)
+    else if (tiled)
       HMC_CUDA(tc_x_to_tiles(x_dtype, Xd, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
     else
       HMC_CUDA(launch_convert_x(x_dtype, Xd, h->xt, P.X, P.xscale, P.n, P.p, P.p_pad, h->err_d, h->stream));
@@ -428,7 +456,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   const size_t sb = state_bytes(h);
   P.state_elems = int64_t(h->max_chains) * P.Km1 * P.p_pad;
   HMC_CUDA(cudaMalloc(&P.gpart, size_t(P.nclusters) * P.state_elems * sb));
-  P.nlparts = P.engine == 2 ? P.nclusters * P.S : P.engine == 3 ? P.tp2.gridA : P.nclusters;
+  P.nlparts = P.engine == 2 ? P.nclusters * P.S : P.engine == 3 ? P.tp2.gridA : P.engine == 4 ? int(P.n) : P.nclusters;
   HMC_CUDA(cudaMalloc(&P.lpart, size_t(P.nlparts) * h->max_chains * sizeof(double)));
   if (P.engine == 3) {
     const Tc2Plan& t2 = P.tp2;
@@ -441,6 +469,8 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(cudaMalloc(&P.sflag, size_t(t2.gridA) * sizeof(int)));
     HMC_CUDA(cudaMemsetAsync(P.sflag, 0, size_t(t2.gridA) * sizeof(int), h->stream));
   }
+  if (P.engine == 4)   // residuals of one chain group: [n][group_chains * Km1]
+    HMC_CUDA(cudaMalloc(&P.rbuf, size_t(P.n) * P.ct_launch * sb));
   if (P.engine == 2) {
     const TcPlan& tp = P.tp;
     HMC_CUDA(cudaMalloc(&P.bbf, size_t(2 * tp.N) * P.p_pad * 2));     // hi and lo terms
@@ -581,7 +611,26 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
                                                     : cudaEventRecord(e0, stream));
     }
     cudaError_t le;
-    if (P.engine == 2) {
+    if (P.engine == 4) {
+      Simt2Launch L{};
+      L.X = P.X;
+      L.y = P.y;
+      L.beta = beta;
+      L.rbuf = P.rbuf;
+      L.lrow = P.lpart + c0;
+      L.lrow_stride = h->max_chains;
+      L.gpart = gpart;
+      L.gpart_cstride = P.state_elems;
+      L.err = h->err_d;
+      L.n = P.n;
+      L.p_pad = P.p_pad;
+      L.C = C;
+      L.Km1 = P.Km1;
+      L.chains = c1 - c0;
+      L.zlogit = P.zlogit;
+      L.Q = P.nclusters;
+      le = simt2_launch(h->xt, L, stream);
+    } else if (P.engine == 2) {
       TcLaunch L{};
       L.xs = P.X;
       L.xscale = P.xscale;
@@ -903,12 +952,14 @@ hmc_status validate_opts(const hmc_opts* o) {
   if ((o->x_storage == HMC_F64) != (o->state == HMC_F64))
     return fail(HMC_EINVAL, "HMC_F64 storage of X goes with HMC_F64 state, and only with it");
   if (o->max_chains < 1 || o->max_chains > 4096) return fail(HMC_EINVAL, "opts.max_chains must be in [1, 4096]");
-  if (o->engine < 0 || o->engine > 3) return fail(HMC_EINVAL, "opts.engine must be 0, 1, 2 or 3");
+  if (o->engine < 0 || o->engine > 4) return fail(HMC_EINVAL, "opts.engine must be 0, 1, 2, 3 or 4");
   if (o->spin_limit < 0) return fail(HMC_EINVAL, "opts.spin_limit must be >= 0");
   const int* t = o->tile;
   if (t[0] < 0 || t[0] > 16) return fail(HMC_EINVAL, "opts.tile[0] (cluster size) must be in [0, 16]");
   if (o->engine == 3 && (t[0] > 4 || t[1] || t[2] || t[3]))
     return fail(HMC_EINVAL, "on the two-pass engine only opts.tile[0] (row tiles per first-pass unit, 1..4) applies");
+  if (o->engine == 4 && (t[0] || t[1] || t[2] || t[3]))
+    return fail(HMC_EINVAL, "the two-pass CUDA-core engine takes no tile options");
   if (t[1] < 0 || t[1] > kTcMaxDepth)
     return fail(HMC_EINVAL, "opts.tile[1] (tensor-core exchange depth) must be in [0, " + std::to_string(kTcMaxDepth) + "]");
   if (t[2] < 0 || t[2] > kTcMaxDepth)
@@ -921,7 +972,7 @@ hmc_status validate_opts(const hmc_opts* o) {
 
 void build_description(hmc_ctx* h) {
   const int e0 = h->probs.empty() ? 1 : h->probs[0].engine;
-  std::string s = "{\"engine\": \"" + std::string(e0 == 1 ? "simt" : e0 == 2 ? "tcgen05" : "tcgen05_2pass") +
+  std::string s = "{\"engine\": \"" + std::string(e0 == 1 ? "simt" : e0 == 2 ? "tcgen05" : e0 == 3 ? "tcgen05_2pass" : "simt_2pass") +
                   "\", \"batched_launch\": " + std::string(h->batched || h->tc_batched ? "true" : "false") +
                   ", \"layout\": " + std::to_string(h->layout) +
                   ", \"x_storage\": " + std::to_string(h->xt) +
@@ -1663,7 +1714,7 @@ hmc_status hmc_get_x(hmc_handle h, int32_t b, void* dst, float* scales) {
   if (!dst) return fail(HMC_EINVAL, "dst is NULL");
   Problem& P = h->probs[b];
   const size_t xb = dtype_bytes(h->xt);
-  if (P.n > 0 && P.engine >= 2) {
+  if (P.n > 0 && (P.engine == 2 || P.engine == 3)) {
     void* tmp = nullptr;
     HMC_CUDA(cudaMalloc(&tmp, size_t(P.n) * P.p * xb));
     cudaError_t e = tc_tiles_to_rows(P.X, tmp, P.n, P.p, P.p_pad, h->xt == HMC_FP8E4M3, h->stream);

@@ -169,6 +169,26 @@ cudaError_t tc2_beta_boxes(const float* beta, void* out, int Km1, int gc, int ch
 // `between` (or nullptr): an event recorded between the two passes (a graph node when capturing).
 cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream, cudaEvent_t between, bool capturing);
 
+// Two-pass CUDA-core engine (FP64 / FP32 X), lpg_simt2.cu: for shapes the fused
+// CUDA-core pass cannot tile.  X row-major [n][p_pad] (p_pad a multiple of 4).
+struct Simt2Launch {
+  const void* X;
+  const int32_t* y;
+  const float* xscale;      // nullptr (scales are folded into X for these storage types)
+  const void* beta;         // [C][p_pad] state type
+  void* rbuf;               // [n][C] residuals (state type)
+  double* lrow;             // [n][lrow_stride] row log-likelihoods, chains of this launch first
+  int32_t lrow_stride;
+  void* gpart;              // [Q][C][p_pad] state type
+  int64_t gpart_cstride;
+  int* err;
+  int64_t n;
+  int32_t p_pad, C, Km1, chains, zlogit, Q;
+};
+int simt2_max_c();
+int simt2_row_ranges(int64_t n, int32_t p_pad, int nsm);
+cudaError_t simt2_launch(int xt, const Simt2Launch& L, cudaStream_t s);
+
 // Element-wise / reduction kernels (update.cu).
 struct UpdateArgs {
   void* beta;  void* eta;  void* grad;          // [chains][Km1][p_pad] state type
