@@ -87,6 +87,7 @@ struct Problem {
   void* stats = nullptr;
   int64_t* iter = nullptr;  // [3]: global iteration, local iteration, generator seed
   int nblk = 1;
+  int glanes = 1;           // lanes sharing one coefficient's split-K sum in the reduction
   int64_t state_elems = 0;  // max_chains * Km1 * p_pad
   // tensor-core engines
   int engine = 1;           // 1 CUDA-core fused kernel, 2 tensor-core fused kernel, 3 tensor-core two-pass,
@@ -94,7 +95,9 @@ struct Problem {
   TcPlan tp{};
   Tc2Plan tp2{};            // engine 3
   void* rbuf = nullptr;     // engines 3, 4: residuals written by the first pass, read by the second
-  void* spart = nullptr;    // engine 3: partial logits of first-pass units split over two CTAs
+  void* spart = nullptr;    // engine 3: partial logits of first-pass units split over two CTAs;
+                            // engine 4: partial logits of the first pass's feature splits
+  int fs = 1;               // engine 4: feature splits of the first pass
   int* sflag = nullptr;     // engine 3: their ready flags
   void* bbf = nullptr;      // BF16 coefficient operand boxes [p_pad / 64][2N x 128 B] (hi, lo terms)
   int nlparts = 0;          // log-likelihood partials reduced per chain
@@ -156,6 +159,15 @@ struct hmc_ctx {
   cudaStream_t g_stream = nullptr;
   size_t g_pairs = 0;
   std::vector<cudaEvent_t> g_events;  // timing events baked into the cached graph
+  // Graphs of hmc_logpost_grad (slot 0) and hmc_leapfrog (slot 1) calls on
+  // device buffers: captured when the same call (chains, buffers, L, eps,
+  // stream) comes twice in a row and replayed while it keeps coming, so that a
+  // call costs one graph launch instead of one launch per kernel.
+  struct CallGraph {
+    std::vector<uint64_t> key;
+    bool seen = false;
+    cudaGraphExec_t exec = nullptr;
+  } cg[2];
 };
 
 namespace {
@@ -392,7 +404,9 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
       P.NSTAGE = 0;
       P.smem = 0;
       P.ntiles = P.n;
-      P.nclusters = simt2_row_ranges(P.n, P.p_pad, nsm);   // partial gradient slices of the second pass
+      P.nclusters = simt2_row_ranges(P.n, P.p_pad, P.ct_launch, nsm);   // partial gradient slices of the second pass
+      P.fs = simt2_feature_splits(P.n, P.p_pad, nsm);
+      HMC_CUDA(simt2_prepare(h->xt));
     } else if (h->engine == 4) {
       return fail(HMC_EUNSUPPORTED, "the two-pass CUDA-core engine needs FP32 or FP64 storage of X, n > 0 and at most " +
                                         std::to_string(simt2_max_c()) + " free classes per chain");
@@ -412,10 +426,15 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
       P.PC = tc.PC;
       P.smem = tc.smem;
       P.p_pad = P.S * P.PC;
-      // Every cluster adds one partial slice to the fixed-order reduction, so
-      // clusters beyond one per S SMs are launched only while each still gets
-      // about four tiles.
-      const int64_t useful = std::max<int64_t>(nsm / P.S, (P.ntiles + 3) / 4);
+      // A cluster's tiles run one after another through its pipeline (the
+      // per-tile latency dominates small problems), and every cluster adds one
+      // partial slice to the reduction: clusters beyond one per S SMs are
+      // launched while each still gets about four tiles, or, up to one tile per
+      // cluster, while the slices' bytes stay below X's (at least 8 MiB).
+      const double slice = double(P.ct_launch) * P.p_pad * state_bytes(h);
+      const double budget = std::max(double(P.n) * P.p_pad * dtype_bytes(h->xt), 8.0 * 1024 * 1024);
+      const int64_t useful = std::max<int64_t>(
+          {int64_t(nsm / P.S), (P.ntiles + 3) / 4, std::min<int64_t>(P.ntiles, int64_t(budget / slice))});
       P.nclusters = int(std::max<int64_t>(1, std::min<int64_t>({int64_t(tc.maxclu), P.ntiles, useful})));
     }
   }
@@ -456,7 +475,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   const size_t sb = state_bytes(h);
   P.state_elems = int64_t(h->max_chains) * P.Km1 * P.p_pad;
   HMC_CUDA(cudaMalloc(&P.gpart, size_t(P.nclusters) * P.state_elems * sb));
-  P.nlparts = P.engine == 2 ? P.nclusters * P.S : P.engine == 3 ? P.tp2.gridA : P.engine == 4 ? int(P.n) : P.nclusters;
+  P.nlparts = P.engine == 2 ? P.nclusters * P.S : P.engine == 3 ? P.tp2.gridA : P.engine == 4 ? int(simt2_ll_blocks(P.n)) : P.nclusters;
   HMC_CUDA(cudaMalloc(&P.lpart, size_t(P.nlparts) * h->max_chains * sizeof(double)));
   if (P.engine == 3) {
     const Tc2Plan& t2 = P.tp2;
@@ -469,8 +488,10 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(cudaMalloc(&P.sflag, size_t(t2.gridA) * sizeof(int)));
     HMC_CUDA(cudaMemsetAsync(P.sflag, 0, size_t(t2.gridA) * sizeof(int), h->stream));
   }
-  if (P.engine == 4)   // residuals of one chain group: [n][group_chains * Km1]
+  if (P.engine == 4) {   // residuals and split logits of one chain group: [n][group_chains * Km1]
     HMC_CUDA(cudaMalloc(&P.rbuf, size_t(P.n) * P.ct_launch * sb));
+    HMC_CUDA(cudaMalloc(&P.spart, size_t(P.fs) * P.n * P.ct_launch * sb));
+  }
   if (P.engine == 2) {
     const TcPlan& tp = P.tp;
     HMC_CUDA(cudaMalloc(&P.bbf, size_t(2 * tp.N) * P.p_pad * 2));     // hi and lo terms
@@ -482,7 +503,13 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
       HMC_CUDA(cudaMemsetAsync(*q, 0, size_t(P.state_elems) * sb, h->stream));
     }
   }
-  P.nblk = update_blocks_per_chain(int64_t(P.Km1) * P.p_pad);
+  {
+    int dev = 0, nsm = 0;
+    HMC_CUDA(cudaGetDevice(&dev));
+    HMC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    P.glanes = update_group_lanes(int64_t(P.Km1) * P.p_pad, h->max_chains, P.nclusters, nsm);
+  }
+  P.nblk = update_blocks_per_chain(int64_t(P.Km1) * P.p_pad * P.glanes);
   HMC_CUDA(cudaMalloc(&P.logk, 2 * h->max_chains * sizeof(double)));
   HMC_CUDA(cudaMalloc(&P.logk0, h->max_chains * sizeof(double)));
   HMC_CUDA(cudaMalloc(&P.h0, h->max_chains * sizeof(double)));
@@ -600,13 +627,13 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     h->inject_timeout = false;
     if (P.engine == 2)
       HMC_CUDA(tc_beta_to_tiles(static_cast<const float*>(beta), P.xscale, P.bbf, C, P.tp.N, P.p_pad, stream));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, em = nullptr;
     // Inside a stream capture the events must become graph nodes.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     const bool timed = h->timing && (h->timing_seq++ % h->timing_period) == 0;
     if (timed) {
       HMC_CUDA(cudaStreamIsCapturing(stream, &cap));
-      HMC_TRY(timer_pair(h, &e0, &e1));
+      HMC_TRY(timer_pair(h, &e0, &e1, P.engine == 4 ? &em : nullptr));
       HMC_CUDA(cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e0, stream, cudaEventRecordExternal)
                                                     : cudaEventRecord(e0, stream));
     }
@@ -617,6 +644,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       L.y = P.y;
       L.beta = beta;
       L.rbuf = P.rbuf;
+      L.zpart = P.spart;
       L.lrow = P.lpart + c0;
       L.lrow_stride = h->max_chains;
       L.gpart = gpart;
@@ -629,7 +657,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
       L.chains = c1 - c0;
       L.zlogit = P.zlogit;
       L.Q = P.nclusters;
-      le = simt2_launch(h->xt, L, stream);
+      L.FS = P.fs;
+      le = simt2_launch(h->xt, L, stream, timed ? em : nullptr, cap == cudaStreamCaptureStatusActive);
     } else if (P.engine == 2) {
       TcLaunch L{};
       L.xs = P.X;
@@ -914,6 +943,7 @@ UpdateArgs make_update(hmc_ctx* h, Problem& P, StateSet& S, int which_logk, int 
   u.gpart = P.gpart;
   u.gpart_cstride = P.state_elems;
   u.nparts = P.n > 0 ? P.nclusters : 0;
+  u.glanes = P.glanes;
   u.lpart = P.lpart;
   u.lpart_cstride = h->max_chains;
   u.nlparts = P.n > 0 ? P.nlparts : 0;
@@ -1162,12 +1192,68 @@ hmc_status check_chains(hmc_ctx* h, int chains) {
 }
 
 // log K and gradient at the state in `S` for every problem.
-hmc_status eval_state(hmc_ctx* h, bool chain_state, int chains) {
+// Enqueue `body` (work on h->stream) directly, or through the call graph of
+// `slot` when `cacheable` (device buffers only, no timing events, no pending
+// fault injection): the second identical call in a row is captured on the
+// private stream and launched as a graph, later ones replay it.
+template <typename F>
+hmc_status run_cached(hmc_ctx* h, int slot, std::vector<uint64_t> key, bool cacheable, F body) {
+  hmc_ctx::CallGraph& g = h->cg[slot];
+  key.push_back(uint64_t(reinterpret_cast<uintptr_t>(h->stream)));
+  if (!cacheable) {
+    g.seen = false;
+    return body();
+  }
+  if (g.exec && g.key == key) {
+    HMC_CUDA(cudaGraphLaunch(g.exec, h->stream));
+    return HMC_OK;
+  }
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (!g.seen || g.key != key) {
+    g.key = key;
+    g.seen = true;
+    return body();
+  }
+  cudaStream_t user = h->stream;
+  HMC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  h->stream = h->cap_stream;
+  const hmc_status st = body();
+  h->stream = user;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (st == HMC_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st != HMC_OK) {
+    g.exec = nullptr;
+    g.seen = false;
+    return st;
+  }
+  if (ce != cudaSuccess) {
+    g.exec = nullptr;
+    g.seen = false;
+    return fail(HMC_ECUDA, std::string("call graph capture failed: ") + cudaGetErrorString(ce));
+  }
+  HMC_CUDA(cudaGraphLaunch(g.exec, h->stream));
+  return HMC_OK;
+}
+
+uint64_t key_of(const void* p) { return uint64_t(reinterpret_cast<uintptr_t>(p)); }
+
+// Gradient and log K of the chains' (or the user scratch's) coefficients; the
+// reduction also writes them to `ugrad` (user beta layout) and `ulogk`
+// ([problem][chains]) when given.
+hmc_status eval_state(hmc_ctx* h, bool chain_state, int chains, void* ugrad = nullptr, double* ulogk = nullptr) {
   HMC_TRY(run_lpg_all(h, chain_state, chains, h->stream));
+  const size_t sb = state_bytes(h);
   for (size_t b = 0; b < h->probs.size(); ++b) {
     Problem& P = h->probs[b];
     StateSet& S = chain_state ? P.cs : P.us;
     UpdateArgs u = make_update(h, P, S, chain_state ? 0 : 1, chains, 0.0, int(b));
+    if (ugrad) u.ugrad = static_cast<char*>(ugrad) + size_t(block_offset(h, int(b), chains)) * sb;
+    if (ulogk) u.ulogk = ulogk + b * chains;
     HMC_CUDA(launch_reduce_update(h->st, u, UPD_SCALARS, h->stream));
   }
   return HMC_OK;
@@ -1222,6 +1308,8 @@ hmc_status hmc_destroy(hmc_handle h) {
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
   for (cudaEvent_t e : h->timer.mid) cudaEventDestroy(e);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto& g : h->cg)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->b_table) cudaFree(h->b_table);
   if (h->b_first) cudaFree(h->b_first);
   if (h->tb_table) cudaFree(h->tb_table);
@@ -1240,15 +1328,16 @@ hmc_status hmc_logpost_grad(hmc_handle h, const void* beta, int32_t chains, doub
   const size_t bytes = size_t(chains) * h->chain_size * state_bytes(h);
   const void* bd = nullptr;
   HMC_TRY(dev_in(h, 0, beta, bytes, &bd));
-  HMC_TRY(pack_all(h, bd, chains, false, &StateSet::beta));
-  HMC_TRY(eval_state(h, false, chains));
   bool gh = false, lh = false;
   void* gd = nullptr;
   void* ld = nullptr;
   HMC_TRY(dev_out(h, 1, grad, bytes, &gd, &gh));
   HMC_TRY(dev_out(h, 2, logpost, h->probs.size() * chains * sizeof(double), &ld, &lh));
-  if (gd) HMC_TRY(unpack_all(h, gd, chains, false, &StateSet::grad));
-  if (ld) HMC_TRY(copy_logk(h, static_cast<double*>(ld), chains, 1));
+  const bool cacheable = bd == beta && !gh && !lh && !h->timing && !h->inject_timeout;
+  HMC_TRY(run_cached(h, 0, {uint64_t(chains), key_of(bd), key_of(gd), key_of(ld)}, cacheable, [&]() -> hmc_status {
+    HMC_TRY(pack_all(h, bd, chains, false, &StateSet::beta));
+    return eval_state(h, false, chains, gd, static_cast<double*>(ld));
+  }));
   if (gh) HMC_CUDA(cudaMemcpyAsync(grad, gd, bytes, cudaMemcpyDeviceToHost, h->stream));
   if (lh)
     HMC_CUDA(cudaMemcpyAsync(logpost, ld, h->probs.size() * chains * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1276,30 +1365,37 @@ hmc_status hmc_leapfrog(hmc_handle h, void* beta, void* eta, void* grad, double*
   if (bh) HMC_CUDA(cudaMemcpyAsync(bd, beta, bytes, cudaMemcpyHostToDevice, h->stream));
   if (eh) HMC_CUDA(cudaMemcpyAsync(ed, eta, bytes, cudaMemcpyHostToDevice, h->stream));
   if (gh) HMC_CUDA(cudaMemcpyAsync(gd, grad, bytes, cudaMemcpyHostToDevice, h->stream));
-  HMC_TRY(pack_all(h, bd, chains, false, &StateSet::beta));
-  HMC_TRY(pack_all(h, ed, chains, false, &StateSet::eta));
-  if (gd) {
-    HMC_TRY(pack_all(h, gd, chains, false, &StateSet::grad));
-  }
-  if (!gd || L == 0) HMC_TRY(eval_state(h, false, chains));
-  if (L > 0) {
-    for (size_t b = 0; b < h->probs.size(); ++b) {
-      UpdateArgs u = make_update(h, h->probs[b], h->probs[b].us, 1, chains, eps, int(b));
-      HMC_CUDA(launch_leap_start(h->st, u, h->stream));
+  uint64_t eps_bits = 0;
+  std::memcpy(&eps_bits, &eps, sizeof(eps_bits));
+  const bool cacheable = !bh && !eh && !gh && !lh && !h->timing && !h->inject_timeout;
+  HMC_TRY(run_cached(h, 1, {uint64_t(chains), uint64_t(L), eps_bits, key_of(bd), key_of(ed), key_of(gd), key_of(ld)},
+                     cacheable, [&]() -> hmc_status {
+    HMC_TRY(pack_all(h, bd, chains, false, &StateSet::beta));
+    HMC_TRY(pack_all(h, ed, chains, false, &StateSet::eta));
+    if (gd) {
+      HMC_TRY(pack_all(h, gd, chains, false, &StateSet::grad));
     }
-    for (int l = 1; l <= L; ++l) {
-      HMC_TRY(run_lpg_all(h, false, chains, h->stream));
-      const int mode = (l < L) ? (UPD_ETA_FULL | UPD_BETA) : (UPD_ETA_HALF | UPD_SCALARS);
+    if (!gd || L == 0) HMC_TRY(eval_state(h, false, chains));
+    if (L > 0) {
       for (size_t b = 0; b < h->probs.size(); ++b) {
         UpdateArgs u = make_update(h, h->probs[b], h->probs[b].us, 1, chains, eps, int(b));
-        HMC_CUDA(launch_reduce_update(h->st, u, mode, h->stream));
+        HMC_CUDA(launch_leap_start(h->st, u, h->stream));
+      }
+      for (int l = 1; l <= L; ++l) {
+        HMC_TRY(run_lpg_all(h, false, chains, h->stream));
+        const int mode = (l < L) ? (UPD_ETA_FULL | UPD_BETA) : (UPD_ETA_HALF | UPD_SCALARS);
+        for (size_t b = 0; b < h->probs.size(); ++b) {
+          UpdateArgs u = make_update(h, h->probs[b], h->probs[b].us, 1, chains, eps, int(b));
+          HMC_CUDA(launch_reduce_update(h->st, u, mode, h->stream));
+        }
       }
     }
-  }
-  HMC_TRY(unpack_all(h, bd, chains, false, &StateSet::beta));
-  HMC_TRY(unpack_all(h, ed, chains, false, &StateSet::eta));
-  if (gd) HMC_TRY(unpack_all(h, gd, chains, false, &StateSet::grad));
-  if (ld) HMC_TRY(copy_logk(h, static_cast<double*>(ld), chains, 1));
+    HMC_TRY(unpack_all(h, bd, chains, false, &StateSet::beta));
+    HMC_TRY(unpack_all(h, ed, chains, false, &StateSet::eta));
+    if (gd) HMC_TRY(unpack_all(h, gd, chains, false, &StateSet::grad));
+    if (ld) HMC_TRY(copy_logk(h, static_cast<double*>(ld), chains, 1));
+    return HMC_OK;
+  }));
   if (bh) HMC_CUDA(cudaMemcpyAsync(beta, bd, bytes, cudaMemcpyDeviceToHost, h->stream));
   if (eh) HMC_CUDA(cudaMemcpyAsync(eta, ed, bytes, cudaMemcpyDeviceToHost, h->stream));
   if (gh) HMC_CUDA(cudaMemcpyAsync(grad, gd, bytes, cudaMemcpyDeviceToHost, h->stream));

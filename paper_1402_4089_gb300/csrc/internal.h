@@ -177,25 +177,34 @@ struct Simt2Launch {
   const float* xscale;      // nullptr (scales are folded into X for these storage types)
   const void* beta;         // [C][p_pad] state type
   void* rbuf;               // [n][C] residuals (state type)
-  double* lrow;             // [n][lrow_stride] row log-likelihoods, chains of this launch first
+  void* zpart;              // [FS][n][C] partial logits of the feature splits (state type)
+  double* lrow;             // [ceil(n / 8)][lrow_stride] log-likelihoods of 8-row blocks, chains of this launch first
   int32_t lrow_stride;
   void* gpart;              // [Q][C][p_pad] state type
   int64_t gpart_cstride;
   int* err;
   int64_t n;
-  int32_t p_pad, C, Km1, chains, zlogit, Q;
+  int32_t p_pad, C, Km1, chains, zlogit, Q, FS;
 };
 int simt2_max_c();
-int simt2_row_ranges(int64_t n, int32_t p_pad, int nsm);
-cudaError_t simt2_launch(int xt, const Simt2Launch& L, cudaStream_t s);
+int64_t simt2_ll_blocks(int64_t n);   // log-likelihood partials per chain
+int simt2_row_ranges(int64_t n, int32_t p_pad, int32_t C, int nsm);
+int simt2_feature_splits(int64_t n, int32_t p_pad, int nsm);
+cudaError_t simt2_prepare(int xt);
+// `between` (optional) is recorded after the first pass (as an external node
+// when the stream is capturing).
+cudaError_t simt2_launch(int xt, const Simt2Launch& L, cudaStream_t s, cudaEvent_t between, bool capturing);
 
 // Element-wise / reduction kernels (update.cu).
 struct UpdateArgs {
   void* beta;  void* eta;  void* grad;          // [chains][Km1][p_pad] state type
   void* beta0; void* grad0;                     // saved trajectory start
   const void* gpart; int64_t gpart_cstride; int32_t nparts;   // partial gradients
+  int32_t glanes;   // lanes sharing one coefficient's partial sum (power of two <= 32; 0 or 1: one)
   const double* lpart; int32_t lpart_cstride; int32_t nlparts; // partial log-likelihoods
   double* logk;     // [chains] current log K
+  void* ugrad;      // optional: the gradient also written in the user layout [chains][ku][p] (masked row zero)
+  double* ulogk;    // optional: log K also written here [chains]
   double* logk0;    // [chains] at trajectory start
   double* h0;       // [chains] H at trajectory start
   double* scal;     // scratch [chains][nblk][2] block partials
@@ -226,7 +235,8 @@ enum : int {
 cudaError_t launch_reduce_update(int st, const UpdateArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_traj_start(int st, const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_select(int st, const UpdateArgs& a, unsigned int* ticket_all, cudaStream_t s);
-int update_blocks_per_chain(int64_t per_chain);
+int update_blocks_per_chain(int64_t per_chain);   // per_chain: coefficients x group lanes
+int update_group_lanes(int64_t per_chain, int chains, int nparts, int nsm);
 cudaError_t launch_leap_start(int st, const UpdateArgs& a, cudaStream_t s);
 
 // Layout conversion between the user layout [chains][ku][p] (state type)

@@ -4,20 +4,25 @@
 // coefficient column of its feature slice next to a ring of row tiles in
 // shared memory, which does not fit for wide problems with many classes (FP32
 // X, K - 1 > 12 and p > 10240, i.e. the K = 15, 20 columns of Table 1 at
-// p = 20000).  Nothing here is held across rows but one row's logits:
+// p = 20000), nor for more classes per chain than that pass handles.
 //
-//  pass 1 (one warp per 1 to 4 rows): lane l accumulates the dot products of
-//         the rows with every coefficient column over features 4l, 4l + 128,
-//         ... (float4 / double2 loads, each coefficient load from L2 serving
-//         every row of the warp), a butterfly reduction gives every lane the
-//         rows' logits; the softmax with the
-//         zero logit of class K (or without it, unconstrained layout), the
-//         residual R[i][C] and the row log-likelihood of every chain are
-//         written to global memory (FP64 log-likelihoods, summed later in row
-//         order by the reduction).
-//  pass 2 (one thread per feature j and row range q): G_q[c][j] = sum over the
-//         range's rows of X[i][j] R[i][c], the rows' residuals staged in shared
-//         memory; one partial slice per row range, summed in range order.
+//  pass 1a (logits_kernel): Z = X B^T for a block of 8 warps x RW rows over one
+//          feature split.  Coefficient chunks of 128 features x C columns are
+//          staged in shared memory by cp.async (double-buffered) and shared by
+//          the block's warps; lane l takes features 4l .. 4l + 3 of a chunk
+//          (float4 / 2 x double2 loads of X, prefetched one chunk ahead), a
+//          butterfly reduction gives the warp its rows' logits, written as one
+//          partial per feature split.  Feature splits give small N enough
+//          blocks.
+//  pass 1b (softmax_kernel): one warp per row sums the splits in a fixed
+//          order, forms the softmax with the zero logit of class K (or
+//          without it, unconstrained layout), the residual R[i][C] and the row
+//          log-likelihoods (FP64), summed over the block's 8 rows in row order
+//          (the reduction sums the blocks in order).
+//  pass 2  (grad_kernel): G_q[c][j] = sum over row range q of X[i][j] R[i][c];
+//          a thread takes FT consecutive features, the residual rows are
+//          staged in shared memory, X loads are issued 8 rows at a time; one
+//          partial slice per row range, summed in range order.
 //
 // X is read from HBM twice (once per pass).
 #include <algorithm>
@@ -28,9 +33,12 @@
 namespace hmc {
 namespace simt2 {
 
-constexpr int kMaxC = 64;          // coefficient columns of one launch
-constexpr int kRowsPerBlock = 8;   // pass 1: warps (rows) per block
-constexpr int kStage = 32;         // pass 2: residual rows staged per step
+constexpr int kMaxC = 64;       // coefficient columns of one launch
+constexpr int kWarps = 8;       // warps per block (both passes: 256 threads)
+constexpr int kChunk = 128;     // pass 1a: features per staged coefficient chunk
+constexpr int kStage = 32;      // pass 2: residual rows staged per step
+constexpr int kUnroll = 8;      // pass 2: X rows loaded together
+constexpr int kRowsMax = 32;    // pass 1a: rows of a block at most (feature-split sizing)
 
 template <typename AT>
 __device__ __forceinline__ AT ex(AT x);
@@ -45,7 +53,8 @@ __device__ __forceinline__ float lg<float>(float x) { return logf(x); }
 template <>
 __device__ __forceinline__ double lg<double>(double x) { return log(x); }
 
-// Four consecutive values of X (aligned) in the state type.
+// Four consecutive values (16-byte aligned for float, 32-byte for double) in
+// the state type.
 template <typename XT, typename AT>
 __device__ __forceinline__ void load4(const XT* p, AT* o) {
   if constexpr (sizeof(XT) == 4) {
@@ -58,24 +67,83 @@ __device__ __forceinline__ void load4(const XT* p, AT* o) {
   }
 }
 
-// Rows one warp takes in pass 1: every coefficient load (from L2) serves RW
-// rows, with the logit registers (RW x CB per lane) kept at about 64 words.
-template <typename AT, int CB>
-__host__ __device__ constexpr int rows_per_warp() {
-  return sizeof(AT) == 4 ? (CB <= 16 ? 4 : CB <= 32 ? 2 : 1) : (CB <= 8 ? 4 : CB <= 16 ? 2 : 1);
+// FT consecutive values (FT in {1, 2, 4}, aligned to FT elements).
+template <typename XT, typename AT, int FT>
+__device__ __forceinline__ void loadft(const XT* p, AT* o) {
+  if constexpr (FT == 4) {
+    load4<XT, AT>(p, o);
+  } else if constexpr (FT == 2) {
+    if constexpr (sizeof(XT) == 4) {
+      const float2 v = *reinterpret_cast<const float2*>(p);
+      o[0] = AT(v.x); o[1] = AT(v.y);
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(p);
+      o[0] = AT(v.x); o[1] = AT(v.y);
+    }
+  } else {
+    o[0] = AT(*p);
+  }
 }
 
-// CB: class bound of the instantiation (>= C).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Rows one warp takes in pass 1a: every staged coefficient value serves RW
+// rows, with RW x CB <= 32 logit accumulators per lane (64 at CB = 64; 16 for
+// FP64), so that two blocks fit an SM's registers.
+template <typename AT, int CB>
+__host__ __device__ constexpr int rows_per_warp() {
+  return sizeof(AT) == 8 ? (CB <= 8 ? 2 : 1) : (CB <= 8 ? 4 : CB <= 16 ? 2 : 1);
+}
+
+// Features one thread takes in pass 2: FT x CB <= 32 accumulators (64 at CB = 64).
+template <typename AT, int CB>
+__host__ __device__ constexpr int features_per_thread() {
+  return CB <= 8 ? 4 : CB <= 16 ? 2 : 1;
+}
+
+// Blocks per SM the register budget is sized for: two, except FP64 at 64 columns.
+template <typename AT, int CB>
+__host__ __device__ constexpr int min_blocks() {
+  return sizeof(AT) == 8 && CB == 64 ? 1 : 2;
+}
+
+// Stage coefficient chunk k (columns c < C, features [128 k, 128 k + 128) that
+// lie below p_pad) into `dst` [C][kChunk].
+template <typename AT>
+__device__ __forceinline__ void stage_chunk(AT* dst, const AT* __restrict__ beta, int k, int32_t p_pad, int32_t C) {
+  constexpr int kVec = 16 / sizeof(AT);             // values per 16-byte copy
+  constexpr int kPerRow = kChunk / kVec;
+  const int j0 = k * kChunk;
+  const int valid = min(kChunk, p_pad - j0);       // multiple of 4 (p_pad is)
+  for (int e = threadIdx.x; e < C * kPerRow; e += blockDim.x) {
+    const int c = e / kPerRow, v = e - c * kPerRow;
+    if (v * kVec < valid)
+      cp_async16(dst + c * kChunk + v * kVec, beta + size_t(c) * p_pad + j0 + v * kVec);
+    else   // past p_pad: zeros (X is zero there too, and 0 x a stale NaN would not be)
+      *reinterpret_cast<uint4*>(dst + c * kChunk + v * kVec) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// CB: class bound of the instantiation (>= C).  Grid: (row blocks, feature
+// splits); split s covers chunks [s * cps, min((s + 1) * cps, nchunks)).
+// zpart: [FS][n][C].  Dynamic shared memory: 2 x C x kChunk state values.
 template <typename XT, typename AT, int CB>
-__global__ void __launch_bounds__(32 * kRowsPerBlock) logits_kernel(const XT* __restrict__ X, const int32_t* __restrict__ y,
-                                                                     const AT* __restrict__ beta, AT* __restrict__ R,
-                                                                     double* __restrict__ lrow, int32_t lstride, int64_t n,
-                                                                     int32_t p_pad, int32_t C, int32_t Km1, int32_t chains,
-                                                                     int32_t zlogit, int* err) {
+__global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) logits_kernel(const XT* __restrict__ X, const AT* __restrict__ beta,
+                                                             AT* __restrict__ zpart, int64_t n, int32_t p_pad,
+                                                             int32_t C, int32_t cps) {
   constexpr int RW = rows_per_warp<AT, CB>();
-  const int lane = threadIdx.x & 31;
-  const int64_t i0 = (int64_t(blockIdx.x) * kRowsPerBlock + (threadIdx.x >> 5)) * RW;
-  if (i0 >= n) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AT* bs = reinterpret_cast<AT*>(smem_raw);        // [2][C][kChunk]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nchunks = (p_pad + kChunk - 1) / kChunk;
+  const int k0 = blockIdx.y * cps, k1 = min(nchunks, k0 + cps);
+  const int64_t i0 = (int64_t(blockIdx.x) * kWarps + warp) * RW;
   const XT* xr[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r) xr[r] = X + size_t(min(i0 + r, n - 1)) * p_pad;   // rows past n: read, not written
@@ -84,20 +152,51 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock) logits_kernel(const XT* __
   for (int r = 0; r < RW; ++r)
 #pragma unroll
     for (int c = 0; c < CB; ++c) z[r][c] = AT(0);
-  for (int j = 4 * lane; j < p_pad; j += 128) {
-    AT xv[RW][4];
+  if (k0 < k1) {
+    stage_chunk<AT>(bs, beta, k0, p_pad, C);
+    cp_async_commit();
+    AT xn[RW][4];
+    {
+      const int j = k0 * kChunk + 4 * lane;
 #pragma unroll
-    for (int r = 0; r < RW; ++r) load4<XT, AT>(xr[r] + j, xv[r]);
-#pragma unroll
-    for (int c = 0; c < CB; ++c) {
-      if (c < C) {
-        AT b[4];
-        load4<AT, AT>(beta + size_t(c) * p_pad + j, b);
-#pragma unroll
-        for (int r = 0; r < RW; ++r)
-          z[r][c] = fma(xv[r][0], b[0], fma(xv[r][1], b[1], fma(xv[r][2], b[2], fma(xv[r][3], b[3], z[r][c]))));
+      for (int r = 0; r < RW; ++r) {
+        if (j < p_pad) load4<XT, AT>(xr[r] + j, xn[r]);
+        else xn[r][0] = xn[r][1] = xn[r][2] = xn[r][3] = AT(0);
       }
     }
+    for (int k = k0; k < k1; ++k) {
+      const int buf = (k - k0) & 1;
+      if (k + 1 < k1) stage_chunk<AT>(bs + (buf ^ 1) * C * kChunk, beta, k + 1, p_pad, C);
+      cp_async_commit();                           // (possibly empty) group of chunk k + 1
+      AT xv[RW][4];
+#pragma unroll
+      for (int r = 0; r < RW; ++r)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) xv[r][f] = xn[r][f];
+      const int jn = (k + 1) * kChunk + 4 * lane;
+      if (k + 1 < k1) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+          if (jn < p_pad) load4<XT, AT>(xr[r] + jn, xn[r]);
+          else xn[r][0] = xn[r][1] = xn[r][2] = xn[r][3] = AT(0);
+        }
+      }
+      cp_async_wait<1>();                          // chunk k has landed (this thread's copies)
+      __syncthreads();                             // ... and every thread's
+      const AT* b = bs + buf * C * kChunk + 4 * lane;
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        if (c < C) {
+          AT bv[4];
+          load4<AT, AT>(b + c * kChunk, bv);       // features past p_pad: X is 0 there
+#pragma unroll
+          for (int r = 0; r < RW; ++r)
+            z[r][c] = fma(xv[r][0], bv[0], fma(xv[r][1], bv[1], fma(xv[r][2], bv[2], fma(xv[r][3], bv[3], z[r][c]))));
+        }
+      }
+      __syncthreads();                             // buffer buf is refilled two chunks on
+    }
+    cp_async_wait<0>();
   }
 #pragma unroll
   for (int r = 0; r < RW; ++r)
@@ -105,118 +204,230 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock) logits_kernel(const XT* __
     for (int c = 0; c < CB; ++c)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) z[r][c] += __shfl_xor_sync(0xffffffffu, z[r][c], o);
+  AT* zp = zpart + size_t(blockIdx.y) * n * C;
 #pragma unroll
   for (int r = 0; r < RW; ++r) {
-    const int64_t i = i0 + r;
-    if (i >= n) break;
+    if (i0 + r >= n) break;
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      if ((c & 31) == lane && c < C) zp[size_t(i0 + r) * C + c] = z[r][c];
+  }
+}
+
+// One warp per row: the lanes sum the row's logits over the FS splits in split
+// order (columns across lanes, 8 split loads in flight), lane ch < chains forms
+// chain ch's maximum, normaliser and row log-likelihood, and the lanes write
+// the residual row R[i][0 .. C) column by column.  The block's 8 row
+// log-likelihoods of each chain are summed in row order into lblk[block].
+template <typename AT>
+__global__ void __launch_bounds__(32 * kWarps) softmax_kernel(const AT* __restrict__ zpart, const int32_t* __restrict__ y,
+                                                             AT* __restrict__ R, double* __restrict__ lblk,
+                                                             int32_t lstride, int64_t n, int32_t C, int32_t Km1,
+                                                             int32_t chains, int32_t FS, int32_t zlogit, int* err) {
+  __shared__ AT zs[kWarps][kMaxC];
+  __shared__ AT ms[kWarps][kMaxC], is[kWarps][kMaxC];   // per chain: maximum, 1 / normaliser
+  __shared__ double ls[kWarps][kMaxC];                  // per chain: row log-likelihood
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = int64_t(blockIdx.x) * kWarps + w;
+  if (i < n) {                                          // warp-uniform
+    const size_t sstride = size_t(n) * C;
+    for (int c = lane; c < C; c += 32) {
+      const AT* zc = zpart + size_t(i) * C + c;
+      AT v = zc[0];
+      int sp = 1;
+      for (; sp + 8 <= FS; sp += 8) {
+        AT t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = zc[size_t(sp + u) * sstride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v += t[u];
+      }
+      for (; sp < FS; ++sp) v += zc[size_t(sp) * sstride];
+      zs[w][c] = v;
+    }
+    __syncwarp();
     int yi = y[i];
     if (yi < 0 || yi >= Km1 + zlogit) {
       if (lane == 0) atomicOr(err, ERR_BAD_LABEL);
       yi = 0;
     }
-    // Lane ch < chains takes chain ch: softmax over its Km1 logits (plus the
-    // zero logit of class K in the identifiable layouts), residual and
-    // log-likelihood.
     for (int ch = lane; ch < chains; ch += 32) {
-      AT m = zlogit ? AT(0) : AT(-INFINITY), zy = AT(0);
-#pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (c >= ch * Km1 && c < (ch + 1) * Km1) {
-          m = max(m, z[r][c]);
-          if (c - ch * Km1 == yi) zy = z[r][c];
-        }
-      AT s = zlogit ? ex<AT>(-m) : AT(0);
-#pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (c >= ch * Km1 && c < (ch + 1) * Km1) s += ex<AT>(z[r][c] - m);
-      const AT inv = AT(1) / s;
-#pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (c >= ch * Km1 && c < (ch + 1) * Km1)
-          R[size_t(i) * C + c] = (c - ch * Km1 == yi ? AT(1) : AT(0)) - ex<AT>(z[r][c] - m) * inv;
-      lrow[size_t(i) * lstride + ch] = double(zy - m - lg<AT>(s));
+      const AT* z = zs[w] + ch * Km1;
+      AT m = zlogit ? AT(0) : AT(-INFINITY);
+      for (int k = 0; k < Km1; ++k) m = max(m, z[k]);
+      AT sum = zlogit ? ex<AT>(-m) : AT(0);
+      for (int k = 0; k < Km1; ++k) sum += ex<AT>(z[k] - m);
+      ms[w][ch] = m;
+      is[w][ch] = AT(1) / sum;
+      const AT zy = yi < Km1 ? z[yi] : AT(0);     // yi == Km1: class K, logit 0
+      ls[w][ch] = double(zy - m - lg<AT>(sum));
     }
+    __syncwarp();
+    AT* ri = R + size_t(i) * C;
+    for (int c = lane; c < C; c += 32) {
+      const int ch = c / Km1, k = c - ch * Km1;
+      ri[c] = (k == yi ? AT(1) : AT(0)) - ex<AT>(zs[w][c] - ms[w][ch]) * is[w][ch];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < chains) {
+    const int rows = int(min(int64_t(kWarps), n - int64_t(blockIdx.x) * kWarps));
+    double acc = 0.0;
+    for (int r = 0; r < rows; ++r) acc += ls[r][threadIdx.x];
+    lblk[size_t(blockIdx.x) * lstride + threadIdx.x] = acc;
   }
 }
 
-// One thread per feature j of the block's 256-feature slice, rows [r0, r1).
+// Thread: FT consecutive features of the block's 256 FT-feature slice, rows of
+// range q = [q n / Q, (q + 1) n / Q).
 template <typename XT, typename AT, int CB>
-__global__ void __launch_bounds__(256) grad_kernel(const XT* __restrict__ X, const AT* __restrict__ R, AT* __restrict__ gpart,
-                                                   int64_t gpart_cstride, int64_t n, int32_t p_pad, int32_t C, int32_t Q,
-                                                   const float* xscale) {
-  __shared__ AT rs[kStage][CB];
-  const int nfb = (p_pad + 255) / 256;
+__global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) grad_kernel(const XT* __restrict__ X, const AT* __restrict__ R,
+                                                           AT* __restrict__ gpart, int64_t gpart_cstride, int64_t n,
+                                                           int32_t p_pad, int32_t C, int32_t Q, const float* xscale) {
+  constexpr int FT = features_per_thread<AT, CB>();
+  __shared__ __align__(16) AT rs[kStage][CB];
+  const int span = 32 * kWarps * FT;
+  const int nfb = (p_pad + span - 1) / span;
   const int fb = blockIdx.x % nfb, q = blockIdx.x / nfb;
-  const int64_t j = int64_t(fb) * 256 + threadIdx.x;
+  const int64_t j = int64_t(fb) * span + int64_t(threadIdx.x) * FT;
+  const bool active = j < p_pad;                    // p_pad % 4 == 0: all FT features valid
   const int64_t r0 = int64_t(q) * n / Q, r1 = int64_t(q + 1) * n / Q;
-  AT g[CB];
+  AT g[FT][CB];
 #pragma unroll
-  for (int c = 0; c < CB; ++c) g[c] = AT(0);
+  for (int f = 0; f < FT; ++f)
+#pragma unroll
+    for (int c = 0; c < CB; ++c) g[f][c] = AT(0);
   for (int64_t i0 = r0; i0 < r1; i0 += kStage) {
     const int rows = int(min(int64_t(kStage), r1 - i0));
     __syncthreads();
-    for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
+    for (int e = threadIdx.x; e < kStage * CB; e += blockDim.x) {
       const int rr = e / CB, c = e - rr * CB;
-      rs[rr][c] = (c < C) ? R[size_t(i0 + rr) * C + c] : AT(0);
+      rs[rr][c] = (rr < rows && c < C) ? R[size_t(i0 + rr) * C + c] : AT(0);
     }
     __syncthreads();
-    if (j < p_pad)
-      for (int rr = 0; rr < rows; ++rr) {
-        const AT xv = AT(X[size_t(i0 + rr) * p_pad + j]);
+    if (!active) continue;
+    for (int rr = 0; rr < rows; rr += kUnroll) {
+      AT xv[kUnroll][FT];
 #pragma unroll
-        for (int c = 0; c < CB; ++c) g[c] = fma(xv, rs[rr][c], g[c]);
+      for (int u = 0; u < kUnroll; ++u) {
+        if (rr + u < rows) {
+          loadft<XT, AT, FT>(X + size_t(i0 + rr + u) * p_pad + j, xv[u]);
+        } else {
+#pragma unroll
+          for (int f = 0; f < FT; ++f) xv[u][f] = AT(0);
+        }
       }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          const AT rv = rs[rr + u][c];             // rows past `rows` are zero
+#pragma unroll
+          for (int f = 0; f < FT; ++f) g[f][c] = fma(xv[u][f], rv, g[f][c]);
+        }
+    }
   }
-  if (j < p_pad) {
-    const AT sc = xscale ? AT(xscale[j]) : AT(1);
-    AT* gp = gpart + size_t(q) * gpart_cstride;
+  if (!active) return;
+  AT* gp = gpart + size_t(q) * gpart_cstride;
+#pragma unroll
+  for (int f = 0; f < FT; ++f) {
+    const AT sc = xscale ? AT(xscale[j + f]) : AT(1);
 #pragma unroll
     for (int c = 0; c < CB; ++c)
-      if (c < C) gp[size_t(c) * p_pad + j] = g[c] * sc;
+      if (c < C) gp[size_t(c) * p_pad + j + f] = g[f][c] * sc;
   }
 }
 
 template <typename XT, typename AT, int CB>
-cudaError_t launch_cb(const Simt2Launch& L, cudaStream_t s) {
+cudaError_t launch_cb(const Simt2Launch& L, cudaStream_t s, cudaEvent_t between, bool capturing) {
   const XT* X = static_cast<const XT*>(L.X);
   const AT* beta = static_cast<const AT*>(L.beta);
   AT* R = static_cast<AT*>(L.rbuf);
-  constexpr int rows = kRowsPerBlock * rows_per_warp<AT, CB>();
-  const int64_t b1 = (L.n + rows - 1) / rows;
-  logits_kernel<XT, AT, CB><<<dim3(unsigned(b1)), 32 * kRowsPerBlock, 0, s>>>(X, L.y, beta, R, L.lrow, L.lrow_stride, L.n,
-                                                                              L.p_pad, L.C, L.Km1, L.chains, L.zlogit, L.err);
+  AT* zp = static_cast<AT*>(L.zpart);
+  constexpr int rows = kWarps * rows_per_warp<AT, CB>();
+  const int nchunks = (L.p_pad + kChunk - 1) / kChunk;
+  const int fs = std::max(1, std::min(L.FS, nchunks));
+  const int cps = (nchunks + fs - 1) / fs;
+  const int fs_used = (nchunks + cps - 1) / cps;
+  const size_t smem = size_t(2) * L.C * kChunk * sizeof(AT);   // within what simt2_prepare allowed
+  const dim3 g1(unsigned((L.n + rows - 1) / rows), unsigned(fs_used));
+  logits_kernel<XT, AT, CB><<<g1, 32 * kWarps, smem, s>>>(X, beta, zp, L.n, L.p_pad, L.C, cps);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nfb = (L.p_pad + 255) / 256;
-  grad_kernel<XT, AT, CB><<<dim3(unsigned(nfb * L.Q)), 256, 0, s>>>(X, R, static_cast<AT*>(L.gpart), L.gpart_cstride, L.n,
-                                                                     L.p_pad, L.C, L.Q, L.xscale);
+  softmax_kernel<AT><<<unsigned((L.n + kWarps - 1) / kWarps), 32 * kWarps, 0, s>>>(
+      zp, L.y, R, L.lrow, L.lrow_stride, L.n, L.C, L.Km1, L.chains, fs_used, L.zlogit, L.err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (between) {
+    e = capturing ? cudaEventRecordWithFlags(between, s, cudaEventRecordExternal) : cudaEventRecord(between, s);
+    if (e != cudaSuccess) return e;
+  }
+  constexpr int span = 32 * kWarps * features_per_thread<AT, CB>();
+  const int nfb = (L.p_pad + span - 1) / span;
+  grad_kernel<XT, AT, CB><<<dim3(unsigned(nfb * L.Q)), 32 * kWarps, 0, s>>>(X, R, static_cast<AT*>(L.gpart),
+                                                                           L.gpart_cstride, L.n, L.p_pad, L.C, L.Q,
+                                                                           L.xscale);
   return cudaGetLastError();
 }
 
 template <typename XT, typename AT>
-cudaError_t launch_t(const Simt2Launch& L, cudaStream_t s) {
-  if (L.C <= 8) return launch_cb<XT, AT, 8>(L, s);
-  if (L.C <= 16) return launch_cb<XT, AT, 16>(L, s);
-  if (L.C <= 32) return launch_cb<XT, AT, 32>(L, s);
-  return launch_cb<XT, AT, kMaxC>(L, s);
+cudaError_t launch_t(const Simt2Launch& L, cudaStream_t s, cudaEvent_t between, bool capturing) {
+  if (L.C <= 8) return launch_cb<XT, AT, 8>(L, s, between, capturing);
+  if (L.C <= 16) return launch_cb<XT, AT, 16>(L, s, between, capturing);
+  if (L.C <= 32) return launch_cb<XT, AT, 32>(L, s, between, capturing);
+  return launch_cb<XT, AT, kMaxC>(L, s, between, capturing);
+}
+
+template <typename XT, typename AT, int CB>
+cudaError_t prepare_cb() {
+  return cudaFuncSetAttribute(logits_kernel<XT, AT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(2 * CB * kChunk * sizeof(AT)));
 }
 
 }  // namespace simt2
 
 int simt2_max_c() { return simt2::kMaxC; }
 
-// Row ranges of pass 2: enough blocks for about two per SM.
-int simt2_row_ranges(int64_t n, int32_t p_pad, int nsm) {
-  const int nfb = (p_pad + 255) / 256;
-  const int64_t want = std::max<int64_t>(1, (2 * int64_t(nsm) + nfb - 1) / nfb);
-  return int(std::max<int64_t>(1, std::min<int64_t>({want, (n + 63) / 64, 64})));
+int64_t simt2_ll_blocks(int64_t n) { return (n + simt2::kWarps - 1) / simt2::kWarps; }
+
+cudaError_t simt2_prepare(int xt) {
+  using namespace simt2;
+  cudaError_t e = cudaSuccess;
+  if (xt == HMC_F64) {
+    for (cudaError_t r : {prepare_cb<double, double, 8>(), prepare_cb<double, double, 16>(),
+                          prepare_cb<double, double, 32>(), prepare_cb<double, double, kMaxC>()})
+      if (r != cudaSuccess) e = r;
+  } else {
+    for (cudaError_t r : {prepare_cb<float, float, 8>(), prepare_cb<float, float, 16>(), prepare_cb<float, float, 32>(),
+                          prepare_cb<float, float, kMaxC>()})
+      if (r != cudaSuccess) e = r;
+  }
+  return e;
 }
 
-cudaError_t simt2_launch(int xt, const Simt2Launch& L, cudaStream_t s) {
+// Row ranges of pass 2 (partial gradient slices): about four blocks per SM,
+// with the slices' bytes (Q C p_pad) kept to a quarter of X's (n p_pad).
+int simt2_row_ranges(int64_t n, int32_t p_pad, int32_t C, int nsm) {
+  const int64_t span = 4 * 256;                    // features of a block at FT = 4 (the fewest blocks)
+  const int64_t nfb = std::max<int64_t>(1, (p_pad + span - 1) / span);
+  const int64_t want = (4 * int64_t(nsm) + nfb - 1) / nfb;
+  const int64_t cap = std::max<int64_t>(1, n / (4 * int64_t(std::max(C, 1))));
+  return int(std::max<int64_t>(1, std::min<int64_t>({want, cap, 64})));
+}
+
+// Feature splits of pass 1a: enough blocks for two per SM at the largest row
+// block (32 rows).
+int simt2_feature_splits(int64_t n, int32_t p_pad, int nsm) {
+  const int64_t nchunks = (p_pad + simt2::kChunk - 1) / simt2::kChunk;
+  const int64_t rowblocks = std::max<int64_t>(1, (n + simt2::kRowsMax - 1) / simt2::kRowsMax);
+  const int64_t want = (2 * int64_t(nsm) + rowblocks - 1) / rowblocks;
+  return int(std::max<int64_t>(1, std::min<int64_t>(want, nchunks)));
+}
+
+cudaError_t simt2_launch(int xt, const Simt2Launch& L, cudaStream_t s, cudaEvent_t between, bool capturing) {
   if (L.n == 0) return cudaSuccess;
-  if (L.C > simt2::kMaxC || L.p_pad % 4) return cudaErrorInvalidValue;
-  if (xt == HMC_F64) return simt2::launch_t<double, double>(L, s);
-  return simt2::launch_t<float, float>(L, s);
+  if (L.C < 1 || L.C > simt2::kMaxC || L.p_pad % 4 || L.FS < 1 || L.Q < 1) return cudaErrorInvalidValue;
+  if (xt == HMC_F64) return simt2::launch_t<double, double>(L, s, between, capturing);
+  return simt2::launch_t<float, float>(L, s, between, capturing);
 }
 
 }  // namespace hmc

@@ -73,7 +73,15 @@ __device__ __forceinline__ void merge(double& s, double& c, double s2, double c2
 __device__ double block_sum_fixed(const double* v, int n, size_t stride) {
   __shared__ double ws[kThreads / 32][2];
   Neumaier acc;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc.add(v[size_t(i) * stride]);
+  int i = threadIdx.x;
+  for (; i + 3 * int(blockDim.x) < n; i += 4 * int(blockDim.x)) {   // four loads in flight, added in order
+    double t[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) t[u] = v[size_t(i + u * int(blockDim.x)) * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc.add(t[u]);
+  }
+  for (; i < n; i += blockDim.x) acc.add(v[size_t(i) * stride]);
   double s = acc.s, c = acc.c;
   for (int o = 16; o > 0; o >>= 1) {
     const double s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
@@ -105,6 +113,28 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket, unsigned int nb
   return is_last != 0;
 }
 
+// Split-K sum of coefficient `idx` over the partials [b0, b1), in order, eight
+// loads in flight.
+template <typename ST>
+__device__ __forceinline__ ST partial_range_sum(const ST* gpi, int64_t cstride, int b0, int b1) {
+  ST g = ST(0);
+  int b = b0;
+  for (; b + 8 <= b1; b += 8) {
+    ST v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = gpi[size_t(b + k) * cstride];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g += v[k];
+  }
+  for (; b < b1; ++b) g += gpi[size_t(b) * cstride];
+  return g;
+}
+
+// A group of G lanes (A.glanes, a power of two <= 32) shares each coefficient:
+// lane l of the group sums the partials [l nparts / G, (l + 1) nparts / G) in
+// order and the G range sums meet in a butterfly (every lane of the group ends
+// with the same bits: each step adds the same two values); lane 0 of the group
+// applies the update.  G = 1 is the plain in-order sum.
 template <typename ST>
 __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArgs A, int mode) {
   const int c = blockIdx.y;
@@ -116,28 +146,28 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
   ST* grad = static_cast<ST*>(A.grad);
   const ST ce = (mode & UPD_ETA_HALF) ? ST(0.5 * A.eps) : ST(A.eps);
   const ST eb = ST(A.eps);
+  const int G = A.glanes > 1 ? A.glanes : 1;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int b0 = int(int64_t(gl) * A.nparts / G), b1 = int(int64_t(gl + 1) * A.nparts / G);
   double prior_s = 0.0, kin_s = 0.0;
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < per_chain;
-       e += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / G; e < per_chain;
+       e += int64_t(gridDim.x) * blockDim.x / G) {
     const int j = int(e % A.p_pad);
-    if (j >= A.p) continue;  // padding columns stay zero
+    if (j >= A.p) continue;  // padding columns stay zero (the whole group skips)
     const size_t idx = base + size_t(e);
-    // Fixed-order sum over the partials (b ascending); the loads of a group
-    // of 8 are issued together, the additions stay in order.
-    ST g = ST(0);
-    const ST* gpi = gp + idx;
-    int b = 0;
-    for (; b + 8 <= A.nparts; b += 8) {
-      ST v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = gpi[size_t(b + k) * A.gpart_cstride];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) g += v[k];
-    }
-    for (; b < A.nparts; ++b) g += gpi[size_t(b) * A.gpart_cstride];
+    ST g = partial_range_sum(gp + idx, A.gpart_cstride, b0, b1);
+    for (int o = 1; o < G; o <<= 1) g += __shfl_xor_sync(gmask, g, o);
+    if (gl != 0) continue;
     const ST bv = beta[idx];
     g += prior_deriv(bv, A.prior_kind, A.prior_scale);
     grad[idx] = g;
+    if (A.ugrad) {
+      ST* ug = static_cast<ST*>(A.ugrad) + size_t(c) * A.ku * A.p;
+      const int k = int(e / A.p_pad);
+      ug[size_t(k) * A.p + j] = g;
+      if (k == 0 && A.ku > A.Km1) ug[size_t(A.Km1) * A.p + j] = ST(0);   // masked row K
+    }
     ST ev = ST(0);
     if (mode & (UPD_ETA_HALF | UPD_ETA_FULL)) {
       ev = eta[idx] + ce * g;
@@ -168,6 +198,7 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
   A.tickets[c] = 0u;
   if (!(mode & UPD_ACCEPT)) {
     A.logk[c] = logk;
+    if (A.ulogk) A.ulogk[c] = logk;
     return;
   }
   const int64_t it = *A.iter;
@@ -389,8 +420,18 @@ int grid_for(int64_t work, int cap = 4096) {
 
 }  // namespace
 
+int update_group_lanes(int64_t per_chain, int chains, int nparts, int nsm) {
+  // Lanes sharing one coefficient's split-K sum: more where few coefficients
+  // meet many partials (a small call waits for about nparts / 8 dependent load
+  // rounds), while the threads stay within half a wave.
+  int G = 1;
+  while (G < 32 && nparts >= 16 * G && per_chain * chains * G * 2 <= int64_t(nsm) * 2048) G *= 2;
+  return G;
+}
+
 int update_blocks_per_chain(int64_t per_chain) {
-  // About one coefficient per thread: the split-K sum is latency-bound.
+  // About one coefficient (times its group lanes) per thread: the split-K sum
+  // is latency-bound.
   int64_t g = (per_chain + kThreads - 1) / kThreads;
   if (g < 1) g = 1;
   if (g > 1024) g = 1024;
