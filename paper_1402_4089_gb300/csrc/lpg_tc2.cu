@@ -38,8 +38,10 @@
 // balanced over the SM count.
 //
 // Warp roles in both kernels: warp 0 bulk-copy producer (lane 0), warp 1 TMEM
-// owner and MMA issuer (lane 0), warps 2-5 epilogue (TMEM lane quarter
-// warp % 4).  Every wait is bounded; a wait that runs out sets an error bit
+// owner and MMA issuer (lane 0), then the epilogue warps: pass A two per TMEM
+// lane quarter (warps 2-9, quarter warp % 4, half (warp - 2) / 4: the softmax
+// of one row is a serial chain, so a second warp per scheduler hides its
+// latency), pass B one per quarter (warps 2-5).  Every wait is bounded; a wait that runs out sets an error bit
 // and an abort flag, and every role then leaves its loop.
 #include <algorithm>
 #include <vector>
@@ -63,7 +65,10 @@ using tc::tmem_ld16;
 constexpr int kRows = 128;
 constexpr int kBox = 64;                 // BF16 values per 128-byte row of a box
 constexpr int kBoxBytes = kRows * 128;   // one 128 x 64 BF16 box
-constexpr int kThreads = 192;
+constexpr int kEpiHalves = 2;                      // pass A: epilogue warps per TMEM lane quarter
+constexpr int kEpiThreads = 128 * kEpiHalves;
+constexpr int kThreadsA = 64 + kEpiThreads;        // pass A block
+constexpr int kThreads = 192;                      // pass B block
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, long long limit, volatile int* abort) {
   const uint32_t a = smem_u32(bar);
@@ -83,18 +88,19 @@ __device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity, long 
     if (mbar_test_cta(a, parity)) return;
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-// The epilogue warps' barrier, ANDing a flag over its 128 threads (so every
+// Pass A's epilogue barrier over its kEpiThreads threads.
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+// The same barrier, ANDing a flag over the epilogue threads (so every
 // epilogue warp leaves its loop at the same unit).
 __device__ __forceinline__ bool epi_bar_and(bool v) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred pi, po;\n\t"
       "setp.ne.u32 pi, %1, 0;\n\t"
-      "bar.red.and.pred po, 1, 128, pi;\n\t"
+      "bar.red.and.pred po, 1, %2, pi;\n\t"
       "selp.u32 %0, 1, 0, po;\n\t}"
       : "=r"(r)
-      : "r"(v ? 1u : 0u)
+      : "r"(v ? 1u : 0u), "n"(kEpiThreads)
       : "memory");
   return r != 0;
 }
@@ -160,7 +166,7 @@ __host__ __device__ inline LogitSmem logit_smem(int NST, uint32_t stage_bytes, i
   return L;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) {
+__global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -189,13 +195,13 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&zdone[a], 1);
-      mbar_init(&zfree[a], 4);
+      mbar_init(&zfree[a], kEpiThreads / 32);
     }
     mbar_init(mdrain, 1);
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
-  for (int c = tid; c < A.chains; c += kThreads) s_llc[c] = 0.0;
+  for (int c = tid; c < A.chains; c += kThreadsA) s_llc[c] = 0.0;
   if (warp == 1) tmem_alloc(tmem_slot, A.tmem_cols);
   fence_before_sync();
   __syncthreads();
@@ -293,8 +299,9 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
       wait_drain(mdrain, 0u, A.spin_limit);
     }
   } else {
-    // ------------------------------------------------------------ epilogue (warps 2-5)
+    // ------------------------------------------------------------ epilogue (warps 2-9)
     const int q = warp & 3;
+    const int hf = (warp - 2) >> 2;                // which half of the quarter's work
     const int r = 32 * q + lane;                   // tile row = TMEM lane
     const uint32_t tq = tmem + (uint32_t(32 * q) << 16);
     int64_t pos = s_begin;
@@ -311,13 +318,18 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
       const int g = int(u % A.ngroups);
       const int nch = min(gc, A.chains - g * gc);   // chains of this group
       const int Cg = nch * Km1;
+      // Sweeps 1-2 of half hf take chains [ch0, ch1); sweep 3 takes the 16-column
+      // blocks b with b % kEpiHalves == hf.
+      const int chm = (nch + kEpiHalves - 1) / kEpiHalves;
+      const int ch0 = min(nch, hf * chm), ch1 = min(nch, ch0 + chm);
+      const int cb = ch0 * Km1, ce = ch1 * Km1;
       if (sg.k0 > 0) {
         // The last boxes of a unit the previous CTA started: store the partial
         // logits for it and raise this CTA's flag.
         float* pp = A.spart + size_t(blockIdx.x) * U * N * kRows;
         for (int i = 0; i < nt; ++i) {
           const uint32_t acc = tq + uint32_t((a * U + i) * N);
-          for (int c0 = 0; c0 < Cg; c0 += 16) {
+          for (int c0 = 16 * hf; c0 < Cg; c0 += 16 * kEpiHalves) {
             float v[16];
             tmem_ld16(acc + uint32_t(c0), v);
 #pragma unroll
@@ -359,10 +371,10 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
         // running (chain, class) counters; per-chain results go to shared memory
         // once per chain.  Sweep 1: the maximum of every chain's logits (the
         // zero logit of class K included) and the logit of the observed class.
-        {
-          int c = 0, k = 0;
+        if (cb < ce) {
+          int c = ch0, k = 0;
           float m = zl ? 0.f : -INFINITY, zy = 0.f;
-          for (int c0 = 0; c0 < Cg; c0 += 16) {
+          for (int c0 = cb & ~15; c0 < ce; c0 += 16) {
             float v[16];
             tmem_ld16(acc + uint32_t(c0), v);
             if (head)
@@ -370,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
               for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              if (c0 + e < Cg) {
+              if (c0 + e >= cb && c0 + e < ce) {
                 m = fmaxf(m, v[e]);
                 if (k == yv) zy = v[e];
                 if (++k == Km1) {
@@ -386,10 +398,10 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
           }
         }
         // Sweep 2: the sum of exponentials of every chain, shifted by its maximum.
-        {
-          int c = 0, k = 0;
-          float mc = s_m[r], ss = zl ? expf(-mc) : 0.f;
-          for (int c0 = 0; c0 < Cg; c0 += 16) {
+        if (cb < ce) {
+          int c = ch0, k = 0;
+          float mc = s_m[c * kRows + r], ss = zl ? expf(-mc) : 0.f;
+          for (int c0 = cb & ~15; c0 < ce; c0 += 16) {
             float v[16];
             tmem_ld16(acc + uint32_t(c0), v);
             if (head)
@@ -397,13 +409,13 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
               for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              if (c0 + e < Cg) {
+              if (c0 + e >= cb && c0 + e < ce) {
                 ss += expf(v[e] - mc);
                 if (++k == Km1) {
                   s_s[c * kRows + r] = ss;
                   ++c;
                   k = 0;
-                  if (c < nch) {
+                  if (c < ch1) {
                     mc = s_m[c * kRows + r];
                     ss = zl ? expf(-mc) : 0.f;
                   }
@@ -412,64 +424,67 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
             }
           }
         }
-        // Sweep 3: R = Y - P for the group's columns (zero past Cg and on rows past
-        // n), written as BF16 in the MN-major 128-byte-swizzled boxes of pass B:
-        // 16-byte chunk j (8 columns) of row r of box b at chunk j ^ (r % 8).
-        unsigned char* rb = A.rout + (size_t(t) * A.ngroups + g) * A.NB * kBoxBytes;
-        {
-          int c = 0, k = 0;
-          float mc = s_m[r], inv = 1.f / s_s[r];
-          for (int c0 = 0; c0 < A.NB * kBox; c0 += 16) {
-            float v[16];
-            if (c0 < Cg) {
-              tmem_ld16(acc + uint32_t(c0), v);
-              if (head)
-#pragma unroll
-                for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
-            }
-            uint32_t w[8];
-#pragma unroll
-            for (int e = 0; e < 16; e += 2) {
-              float rv[2];
-#pragma unroll
-              for (int hh = 0; hh < 2; ++hh) {
-                rv[hh] = 0.f;
-                if (c0 + e + hh < Cg) {
-                  if (valid) rv[hh] = (k == yv ? 1.f : 0.f) - expf(v[e + hh] - mc) * inv;
-                  if (++k == Km1) {
-                    ++c;
-                    k = 0;
-                    if (c < nch) {
-                      mc = s_m[c * kRows + r];
-                      inv = 1.f / s_s[c * kRows + r];
-                    }
-                  }
-                }
-              }
-              const __nv_bfloat162 b2 = __floats2bfloat162_rn(rv[0], rv[1]);
-              w[e / 2] = *reinterpret_cast<const uint32_t*>(&b2);
-            }
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              const int cc = c0 + 8 * hh;                // first column of this 16-byte chunk
-              const int box = cc / kBox, chunk = (cc % kBox) / 8;
-              unsigned char* dst = rb + size_t(box) * kBoxBytes + size_t(r) * 128 + size_t((chunk ^ (r & 7)) << 4);
-              *reinterpret_cast<uint4*>(dst) = make_uint4(w[4 * hh], w[4 * hh + 1], w[4 * hh + 2], w[4 * hh + 3]);
-            }
-          }
-        }
-        // Row log-likelihoods summed per chain over the 128 rows in a fixed tree
-        // (within each warp's 32 rows, then the four warps in lane-quarter order),
-        // added to this CTA's per-chain sums in tile order.
-        for (int c = 0; c < nch; ++c) {
+        // Row log-likelihoods of this half's chains summed over the warp's 32 rows.
+        for (int c = ch0; c < ch1; ++c) {
           double l = valid ? double(s_zy[c * kRows + r] - s_m[c * kRows + r] - logf(s_s[c * kRows + r])) : 0.0;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
           if (lane == 0) s_wsum[c * 4 + q] = l;
         }
-        epi_bar();
-        if (r < nch) s_llc[g * gc + r] += ((s_wsum[r * 4] + s_wsum[r * 4 + 1]) + s_wsum[r * 4 + 2]) + s_wsum[r * 4 + 3];
-        epi_bar();
+        epi_bar();   // every chain's maximum and normaliser of this tile is in shared memory
+        // Sweep 3: R = Y - P for the group's columns (zero past Cg and on rows past
+        // n), written as BF16 in the MN-major 128-byte-swizzled boxes of pass B:
+        // 16-byte chunk j (8 columns) of row r of box b at chunk j ^ (r % 8).
+        unsigned char* rb = A.rout + (size_t(t) * A.ngroups + g) * A.NB * kBoxBytes;
+        for (int c0 = 16 * hf; c0 < A.NB * kBox; c0 += 16 * kEpiHalves) {
+          float v[16];
+          if (c0 < Cg) {
+            tmem_ld16(acc + uint32_t(c0), v);
+            if (head)
+#pragma unroll
+              for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
+          }
+          int c = c0 / Km1, k = c0 - c * Km1;
+          float mc = 0.f, inv = 0.f;
+          if (c < nch) {
+            mc = s_m[c * kRows + r];
+            inv = 1.f / s_s[c * kRows + r];
+          }
+          uint32_t w[8];
+#pragma unroll
+          for (int e = 0; e < 16; e += 2) {
+            float rv[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              rv[hh] = 0.f;
+              if (c0 + e + hh < Cg) {
+                if (valid) rv[hh] = (k == yv ? 1.f : 0.f) - expf(v[e + hh] - mc) * inv;
+                if (++k == Km1) {
+                  ++c;
+                  k = 0;
+                  if (c < nch) {
+                    mc = s_m[c * kRows + r];
+                    inv = 1.f / s_s[c * kRows + r];
+                  }
+                }
+              }
+            }
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(rv[0], rv[1]);
+            w[e / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+          }
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int cc = c0 + 8 * hh;                // first column of this 16-byte chunk
+            const int box = cc / kBox, chunk = (cc % kBox) / 8;
+            unsigned char* dst = rb + size_t(box) * kBoxBytes + size_t(r) * 128 + size_t((chunk ^ (r & 7)) << 4);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w[4 * hh], w[4 * hh + 1], w[4 * hh + 2], w[4 * hh + 3]);
+          }
+        }
+        // This CTA's per-chain sums, in tile order: the four quarters' 32-row sums
+        // in lane-quarter order.
+        if (hf == 0 && r < nch)
+          s_llc[g * gc + r] += ((s_wsum[r * 4] + s_wsum[r * 4 + 1]) + s_wsum[r * 4 + 2]) + s_wsum[r * 4 + 3];
+        epi_bar();   // shared state free for the next tile
       }
       // The unit's accumulators are read: the MMA issuer may start unit j + 2 in them.
       fence_before_sync();
@@ -481,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1) logits_kernel(const LogitArgs A) 
     }
   }
   __syncthreads();
-  for (int c = tid; c < A.chains; c += kThreads) A.lpart[size_t(blockIdx.x) * A.lpart_cstride + c] = s_llc[c];
+  for (int c = tid; c < A.chains; c += kThreadsA) A.lpart[size_t(blockIdx.x) * A.lpart_cstride + c] = s_llc[c];
   if (warp == 1) {
     fence_after_sync();
     tmem_dealloc(tmem, A.tmem_cols);
@@ -691,7 +706,7 @@ __global__ void beta_boxes_kernel(const float* beta, unsigned char* out, int32_t
 }  // namespace tc2
 
 // ------------------------------------------------------------------ host side
-int tc2_threads() { return tc2::kThreads; }
+int tc2_threads() { return tc2::kThreadsA; }
 
 static uint32_t logit_stage(int U, int N) {
   return uint32_t(tc2::al(size_t(U) * tc2::kBoxBytes + size_t(2 * N) * 128, 1024));
@@ -754,7 +769,7 @@ cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream
     a.stage_bytes = logit_stage(P.U, P.N);
     a.tmem_cols = pow2_cols(2 * P.U * P.N);
     a.spin_limit = L.spin_limit;
-    tc2::logits_kernel<<<P.gridA, tc2::kThreads, P.smemA, stream>>>(a);
+    tc2::logits_kernel<<<P.gridA, tc2::kThreadsA, P.smemA, stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (between) {
