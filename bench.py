@@ -61,7 +61,7 @@ def parse_args():
                     help="autodiff (default: n=1e5 p=2e4 K=10, 8 chains, BF16 X), precision, batched, highdim_fp32, "
                          "plain_fp64, mnist_shaped, batched_uneven, sweep")
     ap.add_argument("--engine", type=int, default=0, help="library engine (0 auto, 1 CUDA cores, 2 fused tcgen05, "
-                                                           "3 two-pass tcgen05)")
+                                                           "3 two-pass tcgen05, 4 two-pass CUDA cores)")
     ap.add_argument("--xdtype", default=None, help="override the workload's X storage (f32, bf16, fp8, f64)")
     ap.add_argument("--chains", type=int, default=None)
     ap.add_argument("--L", type=int, default=None)
@@ -511,14 +511,20 @@ def run_ours(args):
     x_bytes = n * p * xb
     grad_bytes = x_bytes + 4 * n + 8 * p * c_launch
     grad_flops = 4.0 * n * p * c_launch                       # two contractions, 2 n p C each
-    if eng_name == "tcgen05_2pass":
+    if eng_name in ("tcgen05_2pass", "simt_2pass"):
+        # residual bytes: BF16 operand boxes (tensor cores) or the state type (CUDA cores)
+        rb = 2 if eng_name == "tcgen05_2pass" else XBYTES[state]
         ta = (first_ms / 1e3) / max(fused_n, 1)
         tb = per_grad_s - ta
-        passes = {"A (logits, softmax, residual)": (ta, x_bytes + 4 * n + 4 * p * c_launch + 2 * n * c_launch),
-                  "B (X^T R)": (tb, x_bytes + 2 * n * c_launch + 4 * p * c_launch)}
+        passes = {"A (logits, softmax, residual)": (ta, x_bytes + 4 * n + 4 * p * c_launch + rb * n * c_launch),
+                  "B (X^T R)": (tb, x_bytes + rb * n * c_launch + 4 * p * c_launch)}
         dom = max(passes, key=lambda k: passes[k][0])
         t_dom, b_dom = passes[dom]
-        kernel = f"tc2::{'logits_kernel' if dom.startswith('A') else 'grad_kernel'} (tcgen05, pass {dom})"
+        if eng_name == "tcgen05_2pass":
+            kernel = f"tc2::{'logits_kernel' if dom.startswith('A') else 'grad_kernel'} (tcgen05, pass {dom})"
+        else:
+            kernel = (f"simt2::{'logits_kernel + softmax_kernel' if dom.startswith('A') else 'grad_kernel'} "
+                      f"(CUDA cores, pass {dom})")
         f_dom = 2.0 * n * p * c_launch
         traffic = recorded_traffic(args.workload, xdt, eng_name, "A" if dom.startswith("A") else "B")
         per_pass = {k: {"us": round(v[0] * 1e6, 2), "bytes": int(v[1]), "gbs": round(v[1] / v[0] / 1e9, 1),
@@ -526,8 +532,7 @@ def run_ours(args):
                         "tflops": round(2.0 * n * p * c_launch / v[0] / 1e12, 1)} for k, v in passes.items()}
     else:
         t_dom, b_dom, f_dom = per_grad_s, grad_bytes, grad_flops
-        kernel = {"tcgen05": "lpg_tc_kernel (tcgen05)", "simt": "lpg_kernel (CUDA cores)",
-                  "simt_2pass": "simt2::logits_kernel + simt2::grad_kernel (CUDA cores, both passes)"}[eng_name]
+        kernel = {"tcgen05": "lpg_tc_kernel (tcgen05)", "simt": "lpg_kernel (CUDA cores)"}[eng_name]
         traffic = recorded_traffic(args.workload, xdt, eng_name)
         per_pass = None
     achieved = b_dom / t_dom / 1e9

@@ -98,8 +98,8 @@ typedef struct {
                              engine 1, or on engine 4 where no engine-1 tile fits (wide problems with
                              many classes: FP32 X with K - 1 > 12 and p > 10240) or K - 1 exceeds
                              its class bound; FP8 on engine 2 when the chains' columns fit TMEM,
-                             else CUDA cores; BF16 on engine 2 when every chain fits one fused
-                             launch, else engine 3 */
+                             else CUDA cores; BF16 on engine 3 for a single problem, in a batch on
+                             engine 2 when every chain fits one fused launch, else engine 3 */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
   int32_t tile[4];        /* {cluster size 1..16, exchange depth, sweep lookahead, ring slots}; 0 =

@@ -8,20 +8,27 @@
 //
 //  pass 1a (logits_kernel): Z = X B^T for a block of 8 warps x RW rows over one
 //          feature split.  Coefficient chunks of 128 features x C columns are
-//          staged in shared memory by cp.async (double-buffered) and shared by
-//          the block's warps; lane l takes features 4l .. 4l + 3 of a chunk
-//          (float4 / 2 x double2 loads of X, prefetched one chunk ahead), a
-//          butterfly reduction gives the warp its rows' logits, written as one
-//          partial per feature split.  Feature splits give small N enough
-//          blocks.
+//          staged in shared memory by cp.async together with the block's rows
+//          of X for the same features, in a ring of 2 or 4 stages (the copies
+//          of the next chunks overlap the arithmetic of chunk k).  A warp's lanes are 8
+//          feature lanes x 4 class groups: lane (f, g) takes features 4f .. 4f+3
+//          of every 32-feature slice and the classes c = g, g + 4, ..., so one
+//          shared-memory vector load of coefficients feeds 4 RW FMAs and the
+//          four class groups read X as broadcasts; a butterfly over the feature
+//          lanes gives the rows' logits, written as one partial per feature
+//          split.
+//          Feature splits give small N enough blocks.  Launches of at most 16
+//          columns use logits_lanes_kernel instead (lane = 4 features, all
+//          classes, X straight from global memory), which measures faster there.
 //  pass 1b (softmax_kernel): one warp per row sums the splits in a fixed
 //          order, forms the softmax with the zero logit of class K (or
 //          without it, unconstrained layout), the residual R[i][C] and the row
 //          log-likelihoods (FP64), summed over the block's 8 rows in row order
 //          (the reduction sums the blocks in order).
 //  pass 2  (grad_kernel): G_q[c][j] = sum over row range q of X[i][j] R[i][c];
-//          a thread takes FT consecutive features, the residual rows are
-//          staged in shared memory, X loads are issued 8 rows at a time; one
+//          a thread takes FT consecutive features, 64 residual rows at a time
+//          are staged in shared memory, X loads are issued 8 rows at a time and
+//          the next 8 rows are loaded while the current ones are used; one
 //          partial slice per row range, summed in range order.
 //
 // X is read from HBM twice (once per pass).
@@ -36,9 +43,10 @@ namespace simt2 {
 constexpr int kMaxC = 64;       // coefficient columns of one launch
 constexpr int kWarps = 8;       // warps per block (both passes: 256 threads)
 constexpr int kChunk = 128;     // pass 1a: features per staged coefficient chunk
-constexpr int kStage = 32;      // pass 2: residual rows staged per step
+constexpr int kStage = 64;      // pass 2: residual rows staged per step
 constexpr int kUnroll = 8;      // pass 2: X rows loaded together
 constexpr int kRowsMax = 32;    // pass 1a: rows of a block at most (feature-split sizing)
+constexpr size_t kRing4Bytes = 110 * 1024;   // pass 1a: largest four-stage ring (two blocks per SM)
 
 template <typename AT>
 __device__ __forceinline__ AT ex(AT x);
@@ -94,17 +102,24 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Rows one warp takes in pass 1a: every staged coefficient value serves RW
-// rows, with RW x CB <= 32 logit accumulators per lane (64 at CB = 64; 16 for
-// FP64), so that two blocks fit an SM's registers.
+// rows; a lane holds RW x CB / 4 logit accumulators (at most 64 words).
 template <typename AT, int CB>
 __host__ __device__ constexpr int rows_per_warp() {
-  return sizeof(AT) == 8 ? (CB <= 8 ? 2 : 1) : (CB <= 8 ? 4 : CB <= 16 ? 2 : 1);
+  return sizeof(AT) == 8 ? 2 : 4;
 }
 
-// Features one thread takes in pass 2: FT x CB <= 32 accumulators (64 at CB = 64).
+// Rows one warp takes in the narrow pass-1a kernel: RW x CB logit accumulators
+// per lane, at most 32 words.
+template <typename AT, int CB>
+__host__ __device__ constexpr int lane_rows() {
+  return sizeof(AT) == 8 ? (CB <= 8 ? 2 : 1) : (CB <= 8 ? 4 : 2);
+}
+
+// Features one thread takes in pass 2: FT x CB <= 32 accumulator words (64 at
+// CB = 64), next to two batches of 8 rows x FT X values.
 template <typename AT, int CB>
 __host__ __device__ constexpr int features_per_thread() {
-  return CB <= 8 ? 4 : CB <= 16 ? 2 : 1;
+  return sizeof(AT) == 8 ? (CB <= 8 ? 2 : 1) : (CB <= 16 ? 2 : 1);
 }
 
 // Blocks per SM the register budget is sized for: two, except FP64 at 64 columns.
@@ -130,14 +145,35 @@ __device__ __forceinline__ void stage_chunk(AT* dst, const AT* __restrict__ beta
   }
 }
 
-// CB: class bound of the instantiation (>= C).  Grid: (row blocks, feature
-// splits); split s covers chunks [s * cps, min((s + 1) * cps, nchunks)).
-// zpart: [FS][n][C].  Dynamic shared memory: 2 x C x kChunk state values.
+// Stage X rows [i0, i0 + rows) of chunk k into `dst` [rows][kChunk] (rows past
+// n read row n - 1, features past p_pad are zero).
+template <typename XT>
+__device__ __forceinline__ void stage_x(XT* dst, const XT* __restrict__ X, int64_t i0, int rows, int64_t n, int k,
+                                        int32_t p_pad) {
+  constexpr int kVec = 16 / sizeof(XT);
+  constexpr int kPerRow = kChunk / kVec;
+  const int j0 = k * kChunk;
+  const int valid = min(kChunk, p_pad - j0);
+  for (int e = threadIdx.x; e < rows * kPerRow; e += blockDim.x) {
+    const int r = e / kPerRow, v = e - r * kPerRow;
+    if (v * kVec < valid)
+      cp_async16(dst + r * kChunk + v * kVec, X + size_t(min(i0 + r, n - 1)) * p_pad + j0 + v * kVec);
+    else
+      *reinterpret_cast<uint4*>(dst + r * kChunk + v * kVec) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// Pass 1a for narrow launches (CB <= 16), where it measures faster than the
+// class-split kernel below: lane l takes features 4l .. 4l + 3 of each chunk
+// and every class, X is loaded from global memory one chunk ahead into
+// registers, a butterfly over all 32 lanes gives the rows' logits.  Grid and
+// zpart as for logits_kernel; dynamic shared memory 2 x C x kChunk state
+// values.
 template <typename XT, typename AT, int CB>
-__global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) logits_kernel(const XT* __restrict__ X, const AT* __restrict__ beta,
+__global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) logits_lanes_kernel(const XT* __restrict__ X, const AT* __restrict__ beta,
                                                              AT* __restrict__ zpart, int64_t n, int32_t p_pad,
                                                              int32_t C, int32_t cps) {
-  constexpr int RW = rows_per_warp<AT, CB>();
+  constexpr int RW = lane_rows<AT, CB>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AT* bs = reinterpret_cast<AT*>(smem_raw);        // [2][C][kChunk]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -211,6 +247,97 @@ __global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) logits_kern
 #pragma unroll
     for (int c = 0; c < CB; ++c)
       if ((c & 31) == lane && c < C) zp[size_t(i0 + r) * C + c] = z[r][c];
+  }
+}
+
+// CB: class bound of the instantiation (>= C, a multiple of 4); NSTG: ring
+// stages.  Grid: (row blocks, feature splits); split s covers chunks
+// [s * cps, min((s + 1) * cps, nchunks)).  zpart: [FS][n][C].  Dynamic shared
+// memory: NSTG x (C coefficient rows x kChunk state values + 8 RW X rows x
+// kChunk X values).
+template <typename XT, typename AT, int CB, int NSTG>
+__global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) logits_kernel(const XT* __restrict__ X, const AT* __restrict__ beta,
+                                                             AT* __restrict__ zpart, int64_t n, int32_t p_pad,
+                                                             int32_t C, int32_t cps) {
+  constexpr int RW = rows_per_warp<AT, CB>();
+  constexpr int BR = kWarps * RW;                  // rows of the block
+  constexpr int TPL = CB / 4;                      // classes per lane
+  constexpr int kSlices = kChunk / 32;             // 32-feature slices per chunk
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AT* bs = reinterpret_cast<AT*>(smem_raw);        // [NSTG][C][kChunk]
+  XT* xs = reinterpret_cast<XT*>(bs + NSTG * C * kChunk);   // [NSTG][BR][kChunk]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int fl = lane & 7, cg = lane >> 3;          // feature lane, class group
+  const int nchunks = (p_pad + kChunk - 1) / kChunk;
+  const int k0 = blockIdx.y * cps, k1 = min(nchunks, k0 + cps);
+  const int64_t ib = int64_t(blockIdx.x) * BR;      // first row of the block
+  const int64_t i0 = ib + warp * RW;                // first row of the warp
+  AT z[RW][TPL];
+#pragma unroll
+  for (int r = 0; r < RW; ++r)
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) z[r][t] = AT(0);
+  if (k0 < k1) {
+    // Chunks k0 .. k0 + NSTG - 2 in flight, one commit group each (possibly empty).
+#pragma unroll
+    for (int q = 0; q < NSTG - 1; ++q) {
+      if (k0 + q < k1) {
+        stage_chunk<AT>(bs + q * C * kChunk, beta, k0 + q, p_pad, C);
+        stage_x<XT>(xs + q * BR * kChunk, X, ib, BR, n, k0 + q, p_pad);
+      }
+      cp_async_commit();
+    }
+    for (int k = k0; k < k1; ++k) {
+      const int buf = (k - k0) % NSTG;
+      const int kn = k + NSTG - 1;                 // the chunk refilling the slot freed by chunk k - 1
+      if (kn < k1) {
+        const int nb = (kn - k0) % NSTG;
+        stage_chunk<AT>(bs + nb * C * kChunk, beta, kn, p_pad, C);
+        stage_x<XT>(xs + nb * BR * kChunk, X, ib, BR, n, kn, p_pad);
+      }
+      cp_async_commit();
+      cp_async_wait<NSTG - 1>();                   // chunk k has landed (this thread's copies)
+      __syncthreads();                             // ... and every thread's
+      const AT* b = bs + buf * C * kChunk + 4 * fl;
+      const XT* xw = xs + (buf * BR + warp * RW) * kChunk + 4 * fl;
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        AT xv[RW][4];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) load4<XT, AT>(xw + r * kChunk + 32 * sl, xv[r]);   // broadcast over class groups
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+          const int c = cg + 4 * t;
+          if (c < C) {
+            AT bv[4];
+            load4<AT, AT>(b + c * kChunk + 32 * sl, bv);   // features past p_pad: X is 0 there
+#pragma unroll
+            for (int r = 0; r < RW; ++r)
+              z[r][t] = fma(xv[r][0], bv[0], fma(xv[r][1], bv[1], fma(xv[r][2], bv[2], fma(xv[r][3], bv[3], z[r][t]))));
+          }
+        }
+      }
+      __syncthreads();                             // slot buf is refilled in the next iteration
+    }
+    cp_async_wait<0>();
+  }
+  // Sum over the 8 feature lanes of each class group (lane bits 0-2).
+#pragma unroll
+  for (int r = 0; r < RW; ++r)
+#pragma unroll
+    for (int t = 0; t < TPL; ++t)
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) z[r][t] += __shfl_xor_sync(0xffffffffu, z[r][t], o);
+  if (fl != 0) return;
+  AT* zp = zpart + size_t(blockIdx.y) * n * C;
+#pragma unroll
+  for (int r = 0; r < RW; ++r) {
+    if (i0 + r >= n) break;
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int c = cg + 4 * t;
+      if (c < C) zp[size_t(i0 + r) * C + c] = z[r][t];
+    }
   }
 }
 
@@ -306,17 +433,22 @@ __global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) grad_kernel
     }
     __syncthreads();
     if (!active) continue;
-    for (int rr = 0; rr < rows; rr += kUnroll) {
-      AT xv[kUnroll][FT];
+    AT xv[kUnroll][FT];
+    auto load_batch = [&](int rr, AT (*o)[FT]) {
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         if (rr + u < rows) {
-          loadft<XT, AT, FT>(X + size_t(i0 + rr + u) * p_pad + j, xv[u]);
+          loadft<XT, AT, FT>(X + size_t(i0 + rr + u) * p_pad + j, o[u]);
         } else {
 #pragma unroll
-          for (int f = 0; f < FT; ++f) xv[u][f] = AT(0);
+          for (int f = 0; f < FT; ++f) o[u][f] = AT(0);
         }
       }
+    };
+    load_batch(0, xv);
+    for (int rr = 0; rr < rows; rr += kUnroll) {
+      AT xn[kUnroll][FT];
+      if (rr + kUnroll < rows) load_batch(rr + kUnroll, xn);   // the next 8 rows while these are used
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
@@ -325,6 +457,12 @@ __global__ void __launch_bounds__(32 * kWarps, min_blocks<AT, CB>()) grad_kernel
 #pragma unroll
           for (int f = 0; f < FT; ++f) g[f][c] = fma(xv[u][f], rv, g[f][c]);
         }
+      if (rr + kUnroll < rows) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+          for (int f = 0; f < FT; ++f) xv[u][f] = xn[u][f];
+      }
     }
   }
   if (!active) return;
@@ -344,14 +482,23 @@ cudaError_t launch_cb(const Simt2Launch& L, cudaStream_t s, cudaEvent_t between,
   const AT* beta = static_cast<const AT*>(L.beta);
   AT* R = static_cast<AT*>(L.rbuf);
   AT* zp = static_cast<AT*>(L.zpart);
-  constexpr int rows = kWarps * rows_per_warp<AT, CB>();
+  constexpr bool narrow = CB <= 16;
+  constexpr int rows = kWarps * (narrow ? lane_rows<AT, CB>() : rows_per_warp<AT, CB>());
   const int nchunks = (L.p_pad + kChunk - 1) / kChunk;
   const int fs = std::max(1, std::min(L.FS, nchunks));
   const int cps = (nchunks + fs - 1) / fs;
   const int fs_used = (nchunks + cps - 1) / cps;
-  const size_t smem = size_t(2) * L.C * kChunk * sizeof(AT);   // within what simt2_prepare allowed
   const dim3 g1(unsigned((L.n + rows - 1) / rows), unsigned(fs_used));
-  logits_kernel<XT, AT, CB><<<g1, 32 * kWarps, smem, s>>>(X, beta, zp, L.n, L.p_pad, L.C, cps);
+  if constexpr (narrow) {
+    const size_t smem = size_t(2) * L.C * kChunk * sizeof(AT);
+    logits_lanes_kernel<XT, AT, CB><<<g1, 32 * kWarps, smem, s>>>(X, beta, zp, L.n, L.p_pad, L.C, cps);
+  } else {
+    const size_t stage = size_t(kChunk) * (L.C * sizeof(AT) + kWarps * rows_per_warp<AT, CB>() * sizeof(XT));
+    if (4 * stage <= kRing4Bytes)   // four stages where two blocks still fit an SM (within what simt2_prepare allowed)
+      logits_kernel<XT, AT, CB, 4><<<g1, 32 * kWarps, 4 * stage, s>>>(X, beta, zp, L.n, L.p_pad, L.C, cps);
+    else
+      logits_kernel<XT, AT, CB, 2><<<g1, 32 * kWarps, 2 * stage, s>>>(X, beta, zp, L.n, L.p_pad, L.C, cps);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   softmax_kernel<AT><<<unsigned((L.n + kWarps - 1) / kWarps), 32 * kWarps, 0, s>>>(
@@ -379,8 +526,16 @@ cudaError_t launch_t(const Simt2Launch& L, cudaStream_t s, cudaEvent_t between, 
 
 template <typename XT, typename AT, int CB>
 cudaError_t prepare_cb() {
-  return cudaFuncSetAttribute(logits_kernel<XT, AT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(2 * CB * kChunk * sizeof(AT)));
+  if constexpr (CB <= 16) {
+    return cudaFuncSetAttribute(logits_lanes_kernel<XT, AT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(2 * CB * kChunk * sizeof(AT)));
+  } else {
+    const int two = int(2 * kChunk * (CB * sizeof(AT) + kWarps * rows_per_warp<AT, CB>() * sizeof(XT)));
+    cudaError_t e = cudaFuncSetAttribute(logits_kernel<XT, AT, CB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, two);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(logits_kernel<XT, AT, CB, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kRing4Bytes));
+  }
 }
 
 }  // namespace simt2

@@ -113,29 +113,28 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket, unsigned int nb
   return is_last != 0;
 }
 
-// Split-K sum of coefficient `idx` over the partials [b0, b1), in order, eight
+// Split-K sum of coefficient `idx` over the partials [b0, b1), in order, four
 // loads in flight.
 template <typename ST>
 __device__ __forceinline__ ST partial_range_sum(const ST* gpi, int64_t cstride, int b0, int b1) {
   ST g = ST(0);
-  int b = b0;
-  for (; b + 8 <= b1; b += 8) {
-    ST v[8];
+  for (int b = b0; b < b1; b += 4) {
+    ST v[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = gpi[size_t(b + k) * cstride];
+    for (int k = 0; k < 4; ++k) v[k] = (b + k < b1) ? gpi[size_t(b + k) * cstride] : ST(0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) g += v[k];
+    for (int k = 0; k < 4; ++k)
+      if (b + k < b1) g += v[k];
   }
-  for (; b < b1; ++b) g += gpi[size_t(b) * cstride];
   return g;
 }
 
-// A group of G lanes (A.glanes, a power of two <= 32) shares each coefficient:
+// GRP: a group of G lanes (A.glanes, a power of two <= 32) shares each coefficient:
 // lane l of the group sums the partials [l nparts / G, (l + 1) nparts / G) in
 // order and the G range sums meet in a butterfly (every lane of the group ends
 // with the same bits: each step adds the same two values); lane 0 of the group
 // applies the update.  G = 1 is the plain in-order sum.
-template <typename ST>
+template <typename ST, bool GRP>
 __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArgs A, int mode) {
   const int c = blockIdx.y;
   const int64_t per_chain = int64_t(A.Km1) * A.p_pad;
@@ -146,19 +145,22 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
   ST* grad = static_cast<ST*>(A.grad);
   const ST ce = (mode & UPD_ETA_HALF) ? ST(0.5 * A.eps) : ST(A.eps);
   const ST eb = ST(A.eps);
-  const int G = A.glanes > 1 ? A.glanes : 1;
+  const int G = GRP ? A.glanes : 1;                 // a power of two
+  const int gsh = GRP ? __ffs(G) - 1 : 0;
   const int lane = threadIdx.x & 31, gl = lane & (G - 1);
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  const int b0 = int(int64_t(gl) * A.nparts / G), b1 = int(int64_t(gl + 1) * A.nparts / G);
+  const int b0 = (gl * A.nparts) >> gsh, b1 = ((gl + 1) * A.nparts) >> gsh;
+  const int64_t stride = (int64_t(gridDim.x) * blockDim.x) >> gsh;
   double prior_s = 0.0, kin_s = 0.0;
-  for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / G; e < per_chain;
-       e += int64_t(gridDim.x) * blockDim.x / G) {
+  for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> gsh; e < per_chain; e += stride) {
     const int j = int(e % A.p_pad);
     if (j >= A.p) continue;  // padding columns stay zero (the whole group skips)
     const size_t idx = base + size_t(e);
     ST g = partial_range_sum(gp + idx, A.gpart_cstride, b0, b1);
-    for (int o = 1; o < G; o <<= 1) g += __shfl_xor_sync(gmask, g, o);
-    if (gl != 0) continue;
+    if (GRP) {
+      for (int o = 1; o < G; o <<= 1) g += __shfl_xor_sync(gmask, g, o);
+      if (gl != 0) continue;
+    }
     const ST bv = beta[idx];
     g += prior_deriv(bv, A.prior_kind, A.prior_scale);
     grad[idx] = g;
@@ -440,10 +442,14 @@ int update_blocks_per_chain(int64_t per_chain) {
 
 cudaError_t launch_reduce_update(int st, const UpdateArgs& a, int mode, cudaStream_t s) {
   dim3 grid(a.nblk, a.chains);
-  if (st == HMC_F64)
-    reduce_update_kernel<double><<<grid, kThreads, 0, s>>>(a, mode);
-  else
-    reduce_update_kernel<float><<<grid, kThreads, 0, s>>>(a, mode);
+  const bool grp = a.glanes > 1;
+  if (st == HMC_F64) {
+    if (grp) reduce_update_kernel<double, true><<<grid, kThreads, 0, s>>>(a, mode);
+    else reduce_update_kernel<double, false><<<grid, kThreads, 0, s>>>(a, mode);
+  } else {
+    if (grp) reduce_update_kernel<float, true><<<grid, kThreads, 0, s>>>(a, mode);
+    else reduce_update_kernel<float, false><<<grid, kThreads, 0, s>>>(a, mode);
+  }
   return cudaGetLastError();
 }
 

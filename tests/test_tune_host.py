@@ -38,8 +38,9 @@ def test_picks_the_fastest_and_caches_it(fake):
     X, y = _xy()
     eng, tile, table = tune.autotune(X, y, 3, chains=2)
     assert (eng, tile) == (1, (2, 0, 0, 2))
-    # every CUDA-core candidate was tried: cluster sizes x ring depths
-    assert len(calls) == len(tune.SIMT_S) * len(tune.RING)
+    # every CUDA-core candidate was tried: cluster sizes x ring depths, and the two-pass CUDA-core engine
+    assert len(calls) == len(tune.SIMT_S) * len(tune.RING) + 1
+    assert [c for c in calls if c[0] == 4] == [(4, (0, 0, 0, 0), "free")]
     assert sorted(r["us"] for r in table) == [40.0, 50.0, 90.0]
     d = json.load(open(cache))
     (key, entry), = d.items()
@@ -65,6 +66,13 @@ def test_two_pass_engine_can_win(fake):
     X, y = _xy()
     assert tune.autotune(X, y, 3, x_storage="bf16", chains=4)[:2] == (3, (0, 0, 0, 0))
     assert [c for c in calls if c[0] == 3] == [(3, (0, 0, 0, 0), "free")]
+
+
+def test_two_pass_cuda_core_engine_can_win(fake):
+    calls, timer, _ = fake
+    timer({(1, 4, 3): 50.0, (4, 0, 0): 35.0})
+    X, y = _xy()
+    assert tune.autotune(X, y, 3, chains=1)[:2] == (4, (0, 0, 0, 0))
 
 
 def test_no_tile_runs_leaves_the_choice_to_the_library(fake):
