@@ -96,8 +96,9 @@ typedef struct {
                              and residual in a first pass, X^T R in a second; up to 64 coefficient
                              columns per launch, no tile options).  Auto: FP32 / FP64 storage on
                              engine 1, or on engine 4 where no engine-1 tile fits (wide problems with
-                             many classes: FP32 X with K - 1 > 12 and p > 10240) or K - 1 exceeds
-                             its class bound; FP8 on engine 2 when the chains' columns fit TMEM,
+                             many classes: FP32 X with K - 1 > 12 and p > 10240), K - 1 exceeds
+                             its class bound, or a single problem of n p >= 4e6 has chains (K - 1)
+                             >= 19 columns (>= 14 at p >= 2048); FP8 on engine 2 when the chains' columns fit TMEM,
                              else CUDA cores; BF16 on engine 3 for a single problem, in a batch on
                              engine 2 when every chain fits one fused launch, else engine 3 */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */

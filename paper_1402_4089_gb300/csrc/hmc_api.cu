@@ -393,8 +393,15 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
       P.ntiles = (P.n + kSimtRows - 1) / kSimtRows;
       HMC_CUDA(simt_choose(h->xt, P.ct_launch, P.p, P.ntiles, h->tile[0], h->tile[3], 0, &tc));
     }
+    // By default also for a single problem with many coefficient columns, where
+    // its class-split passes beat the fused pass's register-held columns
+    // (measured: all chains' columns C >= 14 at p >= 2048, or C >= 19, on X of
+    // at least 4e6 elements; e.g. n=2e4 p=1e4 K=15, one chain: 619 against 985 us).
+    const int64_t c_all = int64_t(h->max_chains) * P.Km1;
+    const bool wide = h->probs.size() == 1 && P.n * P.p >= 4000000 &&
+                      (c_all >= 19 || (c_all >= 14 && P.p >= 2048));
     const bool two = (h->xt == HMC_F32 || h->xt == HMC_F64) && P.n > 0 && P.Km1 <= simt2_max_c() &&
-                     (h->engine == 4 || (h->engine == 0 && !tc.S && !h->tile[0] && !h->tile[3]));
+                     (h->engine == 4 || (h->engine == 0 && !h->tile[0] && !h->tile[3] && (!tc.S || wide)));
     if (two) {
       P.engine = 4;
       P.group_chains = balanced_group(h->max_chains, std::max(1, std::min(h->max_chains, simt2_max_c() / P.Km1)));
