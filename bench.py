@@ -642,7 +642,7 @@ def run_batch_uneven(args):
     probs = [synthetic.make_problem(n, p, K, seed=0, sub=100 + i) for i, (n, p, K) in enumerate(shapes)]
     stream = torch.cuda.Stream(device=dev)
     h = hmc.create_batch([pr[0] for pr in probs], [pr[1] for pr in probs], [K for (_, _, K) in shapes], kind, scale,
-                         x_storage=xdt, max_chains=chains, stream=stream)
+                         x_storage=xdt, max_chains=chains, stream=stream, engine=args.engine)
     desc = h.describe()
     seed = 20140217
     h.sample(chains, L, eps, args.warmup, seed)
@@ -683,8 +683,11 @@ def run_batch_uneven(args):
                    "l2": "inputs larger than L2: X of all problems re-streamed every gradient"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": recorded_traffic("batched_uneven", xdt, "tcgen05"),
-                     "kernel": ("lpg_tc_kernel_batched (tcgen05)" if desc.get("engine") == "tcgen05" else
-                                "lpg_kernel_batched (CUDA cores)") + ", all problems per launch",
+                     "kernel": ({"tcgen05": "lpg_tc_kernel_batched (tcgen05), all problems per launch",
+                                 "simt": "lpg_kernel_batched (CUDA cores), all problems per launch",
+                                 "tcgen05_2pass": "tc2 passes A + B (tcgen05), one pair per problem"}.get(
+                                     desc.get("engine"), desc.get("engine")) if desc.get("batched_launch") or
+                                desc.get("engine") == "tcgen05_2pass" else f"{desc.get('engine')}, one launch per problem"),
                      "avg_launch_us": round(per_launch * 1e6, 2), "launches_timed": fused_n,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "cpu_baseline": None, "e2e": None, "gpu_launches": None,

@@ -136,3 +136,50 @@ def test_leapfrog_fp64_matches_oracle(cuda):
     assert np.max(np.abs(bg - bo)) <= 1e-11 * max(1.0, np.max(np.abs(bo)))
     assert np.max(np.abs(eg - eo)) <= 1e-10 * max(1.0, np.max(np.abs(eo)))
     assert lk_err(lp.item(), lko) <= 1e-11
+
+
+@pytest.mark.parametrize("layout", ["free", "unconstrained"])
+def test_sample_fp64_matches_oracle(cuda, layout):
+    """HMC iterations (one captured graph each) on engine 4 in FP64: samples,
+    accept decisions and log K against the oracle's sampler, two chains, then a
+    continuation from the saved state."""
+    import torch
+    n, p, K, chains, iters, seed, L, eps = 300, 24, 6, 2, 12, 4321, 8, 0.02
+    X, y, _ = synthetic.make_problem(n, p, K, seed=69, dtype=np.float64)
+    rows = K - 1 if layout == "free" else K
+    with hmc.create(X, y, K, "gaussian", 5.0, x_storage="f64", state="f64", max_chains=chains, engine=4,
+                    layout=layout) as h:
+        assert h.describe()["engine"] == "simt_2pass"
+        samples = torch.empty((iters, chains, rows, p), dtype=torch.float64, device=cuda)
+        b0 = torch.zeros((chains, rows, p), dtype=torch.float64, device=cuda)
+        stats = h.sample(chains, L, eps, iters, seed, beta0=b0, samples=samples)
+        ref = ohmc.sample(X, y, K, "gaussian", 5.0, chains, L, eps, iters, seed, layout=layout)
+        assert np.max(np.abs(samples.cpu().numpy() - ref["samples"])) <= 1e-9
+        for c in range(chains):
+            assert stats[c]["accepted"] == int(ref["accept"][:, c].sum())
+            assert lk_err(stats[c]["logpost"], ref["logk"][-1, c]) <= 1e-10
+        more = torch.empty((4, chains, rows, p), dtype=torch.float64, device=cuda)
+        h.sample(chains, L, eps, 4, seed, samples=more)
+        ref2 = ohmc.sample(X, y, K, "gaussian", 5.0, chains, L, eps, 4, seed, beta0=ref["beta"], iter0=iters,
+                           layout=layout)
+        assert np.max(np.abs(more.cpu().numpy() - ref2["samples"])) <= 1e-9
+
+
+def test_sample_fp32_wide_default_engine(cuda):
+    """The default engine for a wide FP32 problem (engine 4) samples within FP32
+    rounding of the fused CUDA-core engine over a few iterations: same accept
+    decisions where |dH| is not near the threshold, samples close."""
+    import torch
+    n, p, K, chains, iters, seed = 2000, 2100, 8, 3, 4, 99      # C = 21 columns: the default is engine 4
+    X, y, _ = synthetic.make_problem(n, p, K, seed=70)
+    out = {}
+    for engine in (0, 1):
+        with hmc.create(X, y, K, "gaussian", 1.0, max_chains=chains, engine=engine) as h:
+            out[engine] = [h.describe()["engine"]]
+            s = torch.empty((iters, chains, K - 1, p), dtype=torch.float32, device=cuda)
+            st = h.sample(chains, 5, 0.002, iters, seed, beta0=torch.zeros((chains, K - 1, p), device=cuda), samples=s)
+            out[engine] += [s.cpu().numpy(), [x["accepted"] for x in st]]
+    assert out[0][0] == "simt_2pass" and out[1][0] == "simt"
+    assert out[0][2] == out[1][2]
+    scale = max(1e-6, np.abs(out[1][1]).max())
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= 1e-4 * scale
