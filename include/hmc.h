@@ -89,18 +89,20 @@ typedef struct {
   int32_t max_chains;     /* largest `chains` any later call may pass (default 1) */
   int32_t engine;         /* 0 auto, 1 CUDA-core fused kernel, 2 tensor-core fused kernel (BF16 or
                              FP8 storage; MMA operands BF16, FP32 accumulation), 3 tensor-core
-                             two-pass kernels (BF16 storage: logits, softmax and residual of every
-                             row tile in a first pass, X^T R in a second; no TMEM limit on the
-                             chains of one launch; X crosses HBM twice when larger than L2), 4
+                             two-pass kernels (BF16 or FP8 storage, FP8 codes widened to BF16 in
+                             shared memory: logits, softmax and residual of every row tile in a
+                             first pass, X^T R in a second; no TMEM limit on the chains of one
+                             launch; X crosses HBM twice when larger than L2), 4
                              CUDA-core two-pass kernels (FP32 / FP64 storage: row logits, softmax
                              and residual in a first pass, X^T R in a second; up to 64 coefficient
                              columns per launch, no tile options).  Auto: FP32 / FP64 storage on
                              engine 1, or on engine 4 where no engine-1 tile fits (wide problems with
                              many classes: FP32 X with K - 1 > 12 and p > 10240), K - 1 exceeds
                              its class bound, or a single problem of n p >= 4e6 has chains (K - 1)
-                             >= 19 columns (>= 14 at p >= 2048); FP8 on engine 2 when the chains' columns fit TMEM,
-                             else CUDA cores; BF16 on engine 3 for a single problem, in a batch on
-                             engine 2 when every chain fits one fused launch, else engine 3 */
+                             >= 19 columns (>= 14 at p >= 2048); BF16 and FP8 on engine 3 for a
+                             single problem; in a batch, FP8 on engine 2 when the chains' columns
+                             fit TMEM, else CUDA cores, and BF16 on engine 2 when every chain fits
+                             one fused launch, else engine 3 */
   int64_t spin_limit;     /* iterations of every bounded device wait (0: default)  */
   void* stream;           /* cudaStream_t for all work of the handle (NULL: default stream) */
   int32_t tile[4];        /* {cluster size 1..16, exchange depth, sweep lookahead, ring slots}; 0 =

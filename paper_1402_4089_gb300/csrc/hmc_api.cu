@@ -338,15 +338,18 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
   if (h->engine == 2 && !tc_ok)
     return fail(HMC_EUNSUPPORTED, "the tensor-core engine needs BF16 or FP8 storage of X, n > 0 and chains * (K-1) "
                                   "columns that fit TMEM next to the cluster's gradient slice");
-  // Two-pass tensor-core engine: on request, or by default for BF16 X: always
-  // for a single problem (its two passes stream X at a higher rate than the
-  // fused pass's tile pipeline: n=5e4 p=1e4 K=20, 4 chains, 402 against 614 us
-  // per gradient), and in a batch when the fused engine cannot take every chain
-  // in one launch (each launch would stream X again) or cannot run the problem.
+  // Two-pass tensor-core engine: on request, or by default for BF16 / FP8 X:
+  // always for a single problem (its two passes stream X at a higher rate than
+  // the fused pass's tile pipeline: n=5e4 p=1e4 K=20, 4 chains, BF16 402 against
+  // 614 us per gradient, FP8 806 against 1017 us), and, BF16, in a batch when the
+  // fused engine cannot take every chain in one launch (each launch would stream
+  // X again) or cannot run the problem.
   const bool single = h->probs.size() == 1;
-  const bool want2 = h->xt == HMC_BF16 && P.n > 0 && P.Km1 <= 32 &&
+  const bool tcx = h->xt == HMC_BF16 || h->xt == HMC_FP8E4M3;
+  const bool want2 = tcx && P.n > 0 && P.Km1 <= 32 &&
                      (h->engine == 3 ||
-                      (h->engine == 0 && !h->tile[0] && (single || !tc_ok || P.group_chains < h->max_chains)));
+                      (h->engine == 0 && !h->tile[0] &&
+                       (single || (h->xt == HMC_BF16 && (!tc_ok || P.group_chains < h->max_chains)))));
   if (want2) {
     int dev = 0, nsm = 0, smem_max = 0;
     HMC_CUDA(cudaGetDevice(&dev));
@@ -364,7 +367,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
       P.p_pad = p2.p_pad;
       P.BM = 128;
       P.CR = 128;
-      P.NT = tc2_threads();
+      P.NT = tc2_threads(h->xt == HMC_FP8E4M3);
       P.NSTAGE = p2.nstA;
       P.smem = p2.smemA;
       P.ntiles = (P.n + 127) / 128;
@@ -373,7 +376,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     }
   }
   if (h->engine == 3 && P.engine != 3)
-    return fail(HMC_EUNSUPPORTED, "the two-pass tensor-core engine needs BF16 storage of X, n > 0, at most 32 free "
+    return fail(HMC_EUNSUPPORTED, "the two-pass tensor-core engine needs BF16 or FP8 storage of X, n > 0, at most 32 free "
                                   "classes per chain and (opts.tile[0]) row tiles per unit that fit TMEM");
   if (!tc_ok) {
     if (h->tile[1] || h->tile[2])
@@ -467,7 +470,7 @@ hmc_status setup_problem(hmc_ctx* h, Problem& P, const void* X, int x_dtype, con
     HMC_CUDA(launch_fp8_scales(x_dtype, Xd, P.xscale, P.n, P.p, P.p_pad, h->stream));
   }
   if (P.n > 0) {
-    if (P.engine == 2 && h->xt == HMC_FP8E4M3)
+    if ((P.engine == 2 || P.engine == 3) && h->xt == HMC_FP8E4M3)
       HMC_CUDA(tc_x_to_tiles_fp8(x_dtype, Xd, P.xscale, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
     else if (tiled)
       HMC_CUDA(tc_x_to_tiles(x_dtype, Xd, P.X, P.n, P.p, P.p_pad, h->err_d, h->stream));
@@ -591,7 +594,7 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     // Both passes for every chain of the call (the chain groups are inside the launches).
     const Tc2Plan& t2 = P.tp2;
     const int ngroups = (chains + t2.gc - 1) / t2.gc;
-    HMC_CUDA(tc2_beta_boxes(static_cast<const float*>(S.beta), P.bbf, P.Km1, t2.gc, chains, t2.N, t2.p_pad, ngroups,
+    HMC_CUDA(tc2_beta_boxes(static_cast<const float*>(S.beta), P.xscale, P.bbf, P.Km1, t2.gc, chains, t2.N, t2.p_pad, ngroups,
                             stream));
     const bool inject = h->inject_timeout;
     h->inject_timeout = false;
@@ -606,6 +609,8 @@ hmc_status run_lpg(hmc_ctx* h, Problem& P, StateSet& S, int chains, cudaStream_t
     }
     Tc2Launch L{};
     L.xs = P.X;
+    L.xscale = P.xscale;
+    L.fp8 = h->xt == HMC_FP8E4M3 ? 1 : 0;
     L.bs = P.bbf;
     L.y = P.y;
     L.rbuf = P.rbuf;

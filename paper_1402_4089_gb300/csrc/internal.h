@@ -145,7 +145,9 @@ struct Tc2Plan {
   size_t smemB = 0;
 };
 struct Tc2Launch {
-  const void* xs;           // X boxes (tc_x_to_tiles layout with p_pad columns)
+  const void* xs;           // X boxes (tc_x_to_tiles layout with p_pad columns; FP8: tc_x_to_tiles_fp8)
+  const float* xscale;      // FP8: per-column scales (folded into the gradient); else unused
+  int32_t fp8;              // X boxes hold FP8 E4M3 codes
   const void* bs;           // coefficient operand of every group (tc2_beta_boxes)
   const int32_t* y;
   void* rbuf;               // R boxes [ntiles][groups][NB][16 KB]
@@ -162,10 +164,11 @@ struct Tc2Launch {
 };
 // force_U: 0, or the row tiles per pass-A unit to use (false if they do not fit).
 bool tc2_plan(int64_t n, int64_t p, int Km1, int chains, int nsm, int smem_max, int force_U, Tc2Plan* out);
-int tc2_threads();
+int tc2_threads(bool fp8);
 cudaError_t tc2_prepare();
-cudaError_t tc2_beta_boxes(const float* beta, void* out, int Km1, int gc, int chains, int N, int p_pad, int ngroups,
-                           cudaStream_t s);
+// scales: FP8 column scales folded into the coefficients, or nullptr.
+cudaError_t tc2_beta_boxes(const float* beta, const float* scales, void* out, int Km1, int gc, int chains, int N,
+                           int p_pad, int ngroups, cudaStream_t s);
 // `between` (or nullptr): an event recorded between the two passes (a graph node when capturing).
 cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream, cudaEvent_t between, bool capturing);
 

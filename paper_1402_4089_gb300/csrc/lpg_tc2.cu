@@ -67,8 +67,14 @@ constexpr int kBox = 64;                 // BF16 values per 128-byte row of a bo
 constexpr int kBoxBytes = kRows * 128;   // one 128 x 64 BF16 box
 constexpr int kEpiHalves = 2;                      // pass A: epilogue warps per TMEM lane quarter
 constexpr int kEpiThreads = 128 * kEpiHalves;
-constexpr int kThreadsA = 64 + kEpiThreads;        // pass A block
-constexpr int kThreads = 192;                      // pass B block
+constexpr int kConvWarps = 4;                      // FP8 X: converter warps (both passes)
+constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kFp8BoxBytes = kRows * 64;           // FP8 box: 128 rows x 64 E4M3 codes, row-major
+// Blocks: pass A producer, MMA issuer, epilogue warps [, converters]; pass B
+// producer, MMA issuer, four drain warps [, converters].
+__host__ __device__ constexpr int threads_a(bool fp8) { return 64 + kEpiThreads + (fp8 ? kConvThreads : 0); }
+__host__ __device__ constexpr int threads_b(bool fp8) { return 192 + (fp8 ? kConvThreads : 0); }
+constexpr int kThreadsA = threads_a(false);
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, long long limit, volatile int* abort) {
   const uint32_t a = smem_u32(bar);
@@ -105,11 +111,65 @@ __device__ __forceinline__ bool epi_bar_and(bool v) {
   return r != 0;
 }
 
+// The FP8 converter warps' barrier (named barrier 2), and the same barrier
+// ANDing a flag over them (so every converter leaves its loop together).
+__device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kConvThreads) : "memory"); }
+__device__ __forceinline__ bool conv_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 2, %2, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u), "n"(kConvThreads)
+      : "memory");
+  return r != 0;
+}
+
+// Widen nbox FP8 boxes (128 x 64 E4M3 codes, row-major) that landed in the
+// upper halves of `slot`'s BF16 box areas (box i's codes at i * in_stride +
+// in_off) into the 128-byte-swizzled BF16 boxes the MMAs read (box i at
+// i * kBoxBytes of `slot`), exactly (every E4M3 value is a BF16 value).  Every
+// converter thread reads all its input chunks before the group barrier and
+// writes only after it, so the in-place widening never overwrites unread
+// input.  ct: thread index within the converter group.
+template <int kMaxBoxes>
+__device__ __forceinline__ void widen_fp8_boxes(unsigned char* slot, int nbox, uint32_t in_stride, uint32_t in_off,
+                                                int ct) {
+  constexpr int kChunks = kFp8BoxBytes / 16;                 // 16-byte input chunks per box
+  constexpr int kPer = kMaxBoxes * kChunks / kConvThreads;   // chunks per thread at most
+  uint4 w[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int g = ct + kConvThreads * i;
+    if (g < nbox * kChunks)
+      w[i] = *reinterpret_cast<const uint4*>(slot + size_t(g / kChunks) * in_stride + in_off + size_t(g % kChunks) * 16);
+  }
+  conv_bar();
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int g = ct + kConvThreads * i;
+    if (g >= nbox * kChunks) break;
+    const int bx = g / kChunks, ci = g % kChunks;
+    const int r = ci >> 2, qq = ci & 3;                      // row, 16-code quarter of the row
+    uint32_t o[8];
+    fp8x4_to_bf16x4(w[i].x, o[0], o[1]);
+    fp8x4_to_bf16x4(w[i].y, o[2], o[3]);
+    fp8x4_to_bf16x4(w[i].z, o[4], o[5]);
+    fp8x4_to_bf16x4(w[i].w, o[6], o[7]);
+    unsigned char* rowp = slot + size_t(bx) * kBoxBytes + size_t(r) * 128;
+    *reinterpret_cast<uint4*>(rowp + (((2 * qq) ^ (r & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4*>(rowp + (((2 * qq + 1) ^ (r & 7)) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
+  }
+  fence_proxy_async_smem();
+}
+
 __host__ __device__ inline size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ------------------------------------------------------------------ pass A
 struct LogitArgs {
-  const unsigned char* xs;   // X boxes [ntiles][nkb][16 KB]
+  const unsigned char* xs;   // X boxes [ntiles][nkb][16 KB BF16 | 8 KB FP8 codes]
   const unsigned char* bs;   // coefficient operand [ngroups][nkb][2N rows x 128 B] (hi rows, then lo rows)
   const int32_t* y;
   unsigned char* rout;       // R boxes [ntiles][ngroups][NB][16 KB]
@@ -161,12 +221,14 @@ __host__ __device__ inline LogitSmem logit_smem(int NST, uint32_t stage_bytes, i
   L.zy = off;    off = al(off + size_t(gc) * kRows * 4, 16);
   L.llr = off;   off = al(off + size_t(gc) * 4 * 8, 16);
   L.llc = off;   off = al(off + size_t(chains) * 8, 16);
-  L.bars = off;  off = al(off + size_t(2 * NST + 5) * 8 + 16, 16);
+  // full, empty [NST]; zdone, zfree [2]; mdrain; TMEM slot; abort flag; (pad); conv [NST]
+  L.bars = off;  off = al(off + size_t(3 * NST + 8) * 8 + 16, 16);
   L.total = off + 1024;   // slack for aligning the dynamic base to 1024
   return L;
 }
 
-__global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A) {
+template <bool kFP8>
+__global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitArgs A) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -187,6 +249,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A)
   uint64_t* mdrain = zfree + 2;          // every MMA of this CTA complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdrain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(mdrain + 2);
+  uint64_t* conv = mdrain + 4;           // FP8: [NST] ring slot widened to BF16 (kConvWarps arrivals)
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -198,10 +261,12 @@ __global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A)
       mbar_init(&zfree[a], kEpiThreads / 32);
     }
     mbar_init(mdrain, 1);
+    if (kFP8)
+      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps);
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
-  for (int c = tid; c < A.chains; c += kThreadsA) s_llc[c] = 0.0;
+  for (int c = tid; c < A.chains; c += int(blockDim.x)) s_llc[c] = 0.0;
   if (warp == 1) tmem_alloc(tmem_slot, A.tmem_cols);
   fence_before_sync();
   __syncthreads();
@@ -241,10 +306,13 @@ __global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A)
             break;
           }
           unsigned char* sp = ring + size_t(st) * A.stage_bytes;
-          mbar_arrive_expect_tx(&full[st], uint32_t(nt * kBoxBytes) + coef_bytes);
+          // BF16 boxes land in place; FP8 boxes in the upper half of each box area
+          // (the converter warps widen them in place).
+          constexpr uint32_t xbox = kFP8 ? uint32_t(kFp8BoxBytes) : uint32_t(kBoxBytes);
+          constexpr uint32_t xoff = kFP8 ? uint32_t(kBoxBytes - kFp8BoxBytes) : 0u;
+          mbar_arrive_expect_tx(&full[st], uint32_t(nt) * xbox + coef_bytes);
           for (int i = 0; i < nt; ++i)
-            bulk_g2s(sp + size_t(i) * kBoxBytes, A.xs + (size_t(t0 + i) * A.nkb + kb) * kBoxBytes, uint32_t(kBoxBytes),
-                     &full[st]);
+            bulk_g2s(sp + size_t(i) * kBoxBytes + xoff, A.xs + (size_t(t0 + i) * A.nkb + kb) * xbox, xbox, &full[st]);
           bulk_g2s(sp + size_t(U) * kBoxBytes, bt + size_t(kb) * coef_bytes, coef_bytes, &full[st]);
           issued = s + 1;
         }
@@ -270,7 +338,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A)
         const int nt = int(min(int64_t(U), A.ntiles - (u / A.ngroups) * U));
         for (int kb = sg.k0; kb < sg.k1; ++kb, ++s) {
           const int st = int(s % NST);
-          if (!wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag)) {
+          if (!wait_bounded(kFP8 ? &conv[st] : &full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag)) {
             fail(ERR_TIMEOUT_STAGE);
             break;
           }
@@ -297,6 +365,28 @@ __global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A)
       // TMEM and shared memory stay allocated until every MMA has completed.
       mma_commit(mdrain);
       wait_drain(mdrain, 0u, A.spin_limit);
+    }
+  } else if (kFP8 && warp >= 2 + kEpiThreads / 32) {
+    // ------------------------------------------------------------ FP8 converters
+    const int ct = tid - (64 + kEpiThreads);
+    int64_t s = 0, pos = s_begin;
+    Seg sg;
+    bool ok = true;
+    while (ok && next_seg(pos, s_end, A.nkb, sg)) {
+      const int nt = int(min(int64_t(U), A.ntiles - (sg.u / A.ngroups) * U));
+      for (int kb = sg.k0; kb < sg.k1; ++kb, ++s) {
+        const int st = int(s % NST);
+        const bool got = wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag);
+        if (!conv_bar_and(got && !*abort_flag)) {   // every converter agrees before the group barrier below
+          if (!got) fail(ERR_TIMEOUT_STAGE);
+          ok = false;
+          break;
+        }
+        widen_fp8_boxes<4>(ring + size_t(st) * A.stage_bytes, nt, uint32_t(kBoxBytes),
+                           uint32_t(kBoxBytes - kFp8BoxBytes), ct);
+        __syncwarp();
+        if (lane == 0) mbar_arrive_local(&conv[st]);
+      }
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 2-9)
@@ -496,7 +586,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A)
     }
   }
   __syncthreads();
-  for (int c = tid; c < A.chains; c += kThreadsA) A.lpart[size_t(blockIdx.x) * A.lpart_cstride + c] = s_llc[c];
+  for (int c = tid; c < A.chains; c += int(blockDim.x)) A.lpart[size_t(blockIdx.x) * A.lpart_cstride + c] = s_llc[c];
   if (warp == 1) {
     fence_after_sync();
     tmem_dealloc(tmem, A.tmem_cols);
@@ -505,7 +595,8 @@ __global__ void __launch_bounds__(kThreadsA, 1) logits_kernel(const LogitArgs A)
 
 // ------------------------------------------------------------------ pass B
 struct GradArgs {
-  const unsigned char* xs;   // X boxes [ntiles][nkb][16 KB]
+  const unsigned char* xs;   // X boxes [ntiles][nkb][16 KB BF16 | 8 KB FP8 codes]
+  const float* xscale;       // FP8: per-column scales s_j (G = diag(s) X_q^T R); nullptr for BF16
   const unsigned char* rs;   // R boxes [ntiles][ngroups][NB][16 KB]
   float* gpart;              // [Q][C][p_pad] partial gradient slices
   int64_t gpart_cstride;
@@ -526,12 +617,14 @@ __host__ __device__ inline GradSmem grad_smem(int NST, int NRS, int NB) {
   size_t off = 0;
   L.ring = off;   off = al(off + size_t(NST) * 2 * kBoxBytes, 1024);
   L.rring = off;  off = al(off + size_t(NRS) * NB * kBoxBytes, 1024);
-  L.bars = off;   off = al(off + size_t(2 * NST + 2 * NRS + 2) * 8 + 16, 16);
+  // full, empty [NST]; rfull, rempty [NRS]; gdone; TMEM slot; abort flag; (pad); conv [NST]
+  L.bars = off;   off = al(off + size_t(3 * NST + 2 * NRS + 4) * 8 + 16, 16);
   L.total = off + 1024;
   return L;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
+template <bool kFP8>
+__global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs A) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -547,6 +640,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
   uint64_t* gdone = rempty + NRS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gdone + 2);
+  uint64_t* conv = gdone + 4;            // FP8: [NST] ring slot widened to BF16 (kConvWarps arrivals)
 
   // This CTA's unit: feature group f, chain group g, row range q.
   const int b = blockIdx.x;
@@ -568,6 +662,8 @@ __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
       mbar_init(&rempty[s], 1);
     }
     mbar_init(gdone, 1);
+    if (kFP8)
+      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps);
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
@@ -595,16 +691,19 @@ __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
         mbar_arrive_expect_tx(&rfull[rsl], rbytes);
         bulk_g2s(rring + size_t(rsl) * rbytes, A.rs + (size_t(t) * A.ngroups + g) * rbytes, rbytes, &rfull[rsl]);
         rissued = i + 1;
-        const unsigned char* xt = A.xs + size_t(t) * A.nkb * kBoxBytes;
+        // Two X boxes per step: BF16 in place, FP8 (two consecutive 8 KB boxes) in
+        // the upper half of the slot, widened in place by the converter warps.
+        constexpr uint32_t xbox = kFP8 ? uint32_t(kFp8BoxBytes) : uint32_t(kBoxBytes);
+        constexpr uint32_t xoff = kFP8 ? uint32_t(2 * (kBoxBytes - kFp8BoxBytes)) : 0u;
+        const unsigned char* xt = A.xs + size_t(t) * A.nkb * xbox;
         for (int mb = 0; mb < mbn; ++mb, ++s) {
           const int st = int(s % NST);
           if (!wait_bounded(&empty[st], uint32_t(((s / NST) & 1) ^ 1), A.spin_limit, abort_flag)) {
             fail(ERR_TIMEOUT_STAGE);
             break;
           }
-          mbar_arrive_expect_tx(&full[st], uint32_t(2 * kBoxBytes));
-          bulk_g2s(ring + size_t(st) * 2 * kBoxBytes, xt + size_t(2 * (mb0 + mb)) * kBoxBytes, uint32_t(2 * kBoxBytes),
-                   &full[st]);
+          mbar_arrive_expect_tx(&full[st], 2 * xbox);
+          bulk_g2s(ring + size_t(st) * 2 * kBoxBytes + xoff, xt + size_t(2 * (mb0 + mb)) * xbox, 2 * xbox, &full[st]);
           issued = s + 1;
         }
       }
@@ -627,7 +726,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
         const uint32_t rb = smem_u32(rring + size_t(rsl) * rbytes);
         for (int mb = 0; mb < mbn; ++mb, ++s) {
           const int st = int(s % NST);
-          if (!wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag)) {
+          if (!wait_bounded(kFP8 ? &conv[st] : &full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag)) {
             fail(ERR_TIMEOUT_STAGE);
             break;
           }
@@ -648,6 +747,27 @@ __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
       mma_commit(gdone);
       wait_drain(gdone, 0u, A.spin_limit);   // every MMA complete before TMEM is released
     }
+  } else if (kFP8 && warp >= 6) {
+    // ------------------------------------------------------------ FP8 converters (warps 6-9)
+    const int ct = tid - 192;
+    int64_t s = 0;
+    bool ok = true;
+    for (int64_t i = 0; i < T && ok && mbn > 0; ++i) {
+      for (int mb = 0; mb < mbn; ++mb, ++s) {
+        const int st = int(s % NST);
+        const bool got = wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag);
+        if (!conv_bar_and(got && !*abort_flag)) {   // every converter agrees before the group barrier below
+          if (!got) fail(ERR_TIMEOUT_STAGE);
+          ok = false;
+          break;
+        }
+        // The two 8 KB boxes sit back to back in the slot's upper 16 KB.
+        widen_fp8_boxes<2>(ring + size_t(st) * 2 * kBoxBytes, 2, uint32_t(kFp8BoxBytes),
+                           uint32_t(2 * (kBoxBytes - kFp8BoxBytes)), ct);
+        __syncwarp();
+        if (lane == 0) mbar_arrive_local(&conv[st]);
+      }
+    }
   } else {
     // ------------------------------------------------------------ drain (warps 2-5)
     const int qd = warp & 3;
@@ -664,8 +784,9 @@ __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
         float v[16];
         if (ok && T > 0) tmem_ld16(tq + uint32_t(mb * N + c0), v);
 #pragma unroll
+        const float sc = A.xscale ? A.xscale[col] : 1.f;
         for (int e = 0; e < 16; ++e)
-          if (c0 + e < Cg) gp[size_t(c0 + e) * A.p_pad + col] = (ok && T > 0) ? v[e] : 0.f;
+          if (c0 + e < Cg) gp[size_t(c0 + e) * A.p_pad + col] = (ok && T > 0) ? v[e] * sc : 0.f;
       }
     }
     fence_before_sync();
@@ -679,9 +800,10 @@ __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const GradArgs A) {
 
 // Coefficients [chains][Km1][p_pad] (FP32) -> operand boxes of every chain group,
 // [group][p_pad / 64][2N rows x 128 B]: rows [0, N) the hi term bf16(v), rows
-// [N, 2N) the lo term bf16(v - hi); columns past the group's C are zero.
-__global__ void beta_boxes_kernel(const float* beta, unsigned char* out, int32_t Km1, int32_t gc, int32_t chains,
-                                  int32_t N, int32_t p_pad) {
+// [N, 2N) the lo term bf16(v - hi); columns past the group's C are zero.  With
+// FP8 X the column scales are folded in: X B = X_q (diag(s) B).
+__global__ void beta_boxes_kernel(const float* beta, const float* scales, unsigned char* out, int32_t Km1, int32_t gc,
+                                  int32_t chains, int32_t N, int32_t p_pad) {
   const int g = blockIdx.y;
   const int nch = min(gc, chains - g * gc);
   const int Cg = nch * Km1;
@@ -691,7 +813,7 @@ __global__ void beta_boxes_kernel(const float* beta, unsigned char* out, int32_t
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int k = int(i / p_pad);
     const int64_t col = i - int64_t(k) * p_pad;
-    const float v = (k < Cg) ? bg[size_t(k) * p_pad + col] : 0.f;
+    const float v = (k < Cg) ? bg[size_t(k) * p_pad + col] * (scales ? scales[col] : 1.f) : 0.f;
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
     unsigned char* box = og + size_t(col / kBox) * 2 * N * 128;
@@ -706,7 +828,7 @@ __global__ void beta_boxes_kernel(const float* beta, unsigned char* out, int32_t
 }  // namespace tc2
 
 // ------------------------------------------------------------------ host side
-int tc2_threads() { return tc2::kThreadsA; }
+int tc2_threads(bool fp8) { return tc2::threads_a(fp8); }
 
 static uint32_t logit_stage(int U, int N) {
   return uint32_t(tc2::al(size_t(U) * tc2::kBoxBytes + size_t(2 * N) * 128, 1024));
@@ -722,17 +844,19 @@ cudaError_t tc2_prepare() {
   int dev = 0, smem_max = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(tc2::logits_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(tc2::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  for (auto fn : {tc2::logits_kernel<false>, tc2::logits_kernel<true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  for (auto fn : {tc2::grad_kernel<false>, tc2::grad_kernel<true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   return e;
 }
 
-cudaError_t tc2_beta_boxes(const float* beta, void* out, int Km1, int gc, int chains, int N, int p_pad, int ngroups,
-                           cudaStream_t s) {
+cudaError_t tc2_beta_boxes(const float* beta, const float* scales, void* out, int Km1, int gc, int chains, int N,
+                           int p_pad, int ngroups, cudaStream_t s) {
   const int64_t total = int64_t(N) * p_pad;
   const int gx = std::max(1, int(std::min<int64_t>(1024, (total + 255) / 256)));
-  tc2::beta_boxes_kernel<<<dim3(gx, ngroups), 256, 0, s>>>(beta, static_cast<unsigned char*>(out), Km1, gc, chains, N,
-                                                            p_pad);
+  tc2::beta_boxes_kernel<<<dim3(gx, ngroups), 256, 0, s>>>(beta, scales, static_cast<unsigned char*>(out), Km1, gc,
+                                                            chains, N, p_pad);
   return cudaGetLastError();
 }
 
@@ -769,7 +893,10 @@ cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream
     a.stage_bytes = logit_stage(P.U, P.N);
     a.tmem_cols = pow2_cols(2 * P.U * P.N);
     a.spin_limit = L.spin_limit;
-    tc2::logits_kernel<<<P.gridA, tc2::kThreadsA, P.smemA, stream>>>(a);
+    if (L.fp8)
+      tc2::logits_kernel<true><<<P.gridA, tc2::threads_a(true), P.smemA, stream>>>(a);
+    else
+      tc2::logits_kernel<false><<<P.gridA, tc2::threads_a(false), P.smemA, stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (between) {
@@ -779,6 +906,7 @@ cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream
   }
   tc2::GradArgs b{};
   b.xs = static_cast<const unsigned char*>(L.xs);
+  b.xscale = L.fp8 ? L.xscale : nullptr;
   b.rs = static_cast<const unsigned char*>(L.rbuf);
   b.gpart = static_cast<float*>(L.gpart);
   b.gpart_cstride = L.gpart_cstride;
@@ -799,7 +927,10 @@ cudaError_t tc2_launch(const Tc2Plan& P, const Tc2Launch& L, cudaStream_t stream
   b.NRS = P.nrsB;
   b.tmem_cols = pow2_cols(P.MB * P.N);
   b.spin_limit = L.spin_limit;
-  tc2::grad_kernel<<<P.nfg * b.ngroups * P.Q, tc2::kThreads, P.smemB, stream>>>(b);
+  if (L.fp8)
+    tc2::grad_kernel<true><<<P.nfg * b.ngroups * P.Q, tc2::threads_b(true), P.smemB, stream>>>(b);
+  else
+    tc2::grad_kernel<false><<<P.nfg * b.ngroups * P.Q, tc2::threads_b(false), P.smemB, stream>>>(b);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ tile that fits fewer chains per launch pays for more launches).
 
 Candidates: CUDA-core engine, S in {1, 2, 3, 4, 5, 6, 8, 10, 12, 16} x ring
 slots {2, 3, 4}; fused tensor-core engine (BF16 or FP8 X), S in {16, 8, 4, 2,
-1} x ring slots {2, 3, 4}; two-pass tensor-core engine (BF16 X) and two-pass
+1} x ring slots {2, 3, 4}; two-pass tensor-core engine (BF16 or FP8 X) and two-pass
 CUDA-core engine (FP32 / FP64 X), whose plans the library derives from the
 shape (one candidate each).  With engine 0 every engine the
 storage type allows is a candidate.  Tiles the library rejects for the shape
@@ -101,7 +101,7 @@ def autotune(X, y, K, prior="gaussian", prior_scale=1.0, x_storage="f32", state=
     if engine:
         engines = (engine,)
     else:
-        engines = {"bf16": (2, 3, 1), "fp8": (2, 1)}.get(x_storage, (1, 4))
+        engines = {"bf16": (2, 3, 1), "fp8": (3, 2, 1)}.get(x_storage, (1, 4))
     key = _key(torch.cuda.get_device_name(), n, p, K, x_storage, state, chains, engine) + \
         ("" if layout == "free" else f"|layout={layout}")
     cache = _load() if use_cache else {}

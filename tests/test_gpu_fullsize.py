@@ -2,10 +2,10 @@
 the library chooses for them (the one the bench runs unless its autotuner finds a
 faster tile), against the FP64 oracle evaluated on the same stored X values.
 
-* precision workload, n=50000 p=10000 K=20, 4 chains, X stored in BF16 (the
-  default two-pass engine and the fused engine, all chains in one launch) and
-  in per-column-scaled FP8 (fused engine; codes and scales bit-exact against
-  the oracle's quantisation);
+* precision workload, n=50000 p=10000 K=20, 4 chains, X stored in BF16 and in
+  per-column-scaled FP8 (codes and scales bit-exact against the oracle's
+  quantisation), on the default two-pass engine and on the fused engine (all
+  chains in one launch);
 * batched workload's shared problem, n=20000 p=2000 K=10, 64 chains;
 * batched workload's 32 uneven problems (n ~ U[500, 20000], p ~ U[100, 4000],
   K ~ U{3..20}) in one handle, one fused launch per gradient;
@@ -43,7 +43,7 @@ def _errs(Xq, y, beta, lp, g, kind, scale, chains, X=None):
     return out
 
 
-@pytest.mark.parametrize("storage,engine", [("bf16", 0), ("fp8", 0), ("bf16", 2)])
+@pytest.mark.parametrize("storage,engine", [("bf16", 0), ("fp8", 0), ("bf16", 2), ("fp8", 2)])
 def test_precision_workload_full_size(cuda, storage, engine):
     import torch
     X, y, btrue, spec = synthetic.make_workload("precision")
@@ -53,8 +53,8 @@ def test_precision_workload_full_size(cuda, storage, engine):
     beta = (0.01 * rng.standard_normal((chains, K - 1, X.shape[1]))).astype(np.float32)
     with hmc.create(X, y, K, kind, scale, x_storage=storage, max_chains=chains, engine=engine) as h:
         d = h.describe()
-        # BF16 by default: the two-pass engine; FP8: the fused engine
-        assert d["engine"] == ("tcgen05_2pass" if (engine, storage) == (0, "bf16") else "tcgen05"), d
+        # a single problem defaults to the two-pass engine (BF16 and FP8)
+        assert d["engine"] == ("tcgen05_2pass" if engine == 0 else "tcgen05"), d
         assert d["problems"][0]["group_chains"] == chains, d
         bits, scales = h.get_x()
         lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))

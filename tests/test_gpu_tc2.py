@@ -1,6 +1,9 @@
-"""The two-pass tensor-core engine (opts.engine = 3, BF16 X): pass A forms the
-logits, softmax and residual of every (row tile, chain group), pass B the
-partial gradients X^T R; against the FP64 oracle on the stored BF16 X.
+"""The two-pass tensor-core engine (opts.engine = 3, BF16 or per-column-scaled
+FP8 X): pass A forms the logits, softmax and residual of every (row tile, chain
+group), pass B the partial gradients X^T R; against the FP64 oracle on the
+stored X (FP8: codes and scales bit-exact against the oracle's quantisation,
+the codes widened to BF16 in shared memory, the scales folded into the
+coefficients and the gradient).
 
 Same operand precision as the fused tensor-core engine (two-term BF16
 coefficients, BF16 residual, FP32 accumulation), so the same gates: gradient
@@ -19,20 +22,25 @@ pytestmark = pytest.mark.gpu
 TOL_G, TOL_L = 3e-3, 1e-4
 
 
-def _run(cuda, n, p, K, chains, seed, layout="free", prior=("gaussian", 10.0), bscale=0.05, U=0):
+def _run(cuda, n, p, K, chains, seed, layout="free", prior=("gaussian", 10.0), bscale=0.05, U=0, storage="bf16"):
     import torch
     X, y, _ = synthetic.make_problem(n, p, K, seed=seed)
     rows = K - 1 if layout == "free" else K
     beta = (bscale * np.random.default_rng(seed + 1).standard_normal((chains, rows, p))).astype(np.float32)
-    with hmc.create(X, y, K, prior[0], prior[1], x_storage="bf16", max_chains=chains, engine=3, layout=layout,
+    with hmc.create(X, y, K, prior[0], prior[1], x_storage=storage, max_chains=chains, engine=3, layout=layout,
                     tile=(U, 0, 0, 0)) as h:
         d = h.describe()
         assert d["engine"] == "tcgen05_2pass", d
-        bits, _ = h.get_x()
+        bits, scales = h.get_x()
         lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
         torch.cuda.synchronize()
         lp, g = lp.cpu().numpy(), g.cpu().numpy()
-    Xq = quant.bf16_decode(bits).astype(np.float64)
+    if storage == "fp8":
+        c_o, s_o = quant.fp8_quantize(X)
+        assert np.array_equal(scales, s_o) and np.array_equal(bits, c_o)
+        Xq = quant.fp8_dequantize(bits, scales).astype(np.float64)
+    else:
+        Xq = quant.bf16_decode(bits).astype(np.float64)
     for c in range(chains):
         lk_o = model.log_kernel_layout(Xq, y, beta[c], prior[0], prior[1], layout)
         g_o = model.grad_log_kernel_layout(Xq, y, beta[c], prior[0], prior[1], layout)
@@ -64,6 +72,20 @@ def test_tc2_units_split_over_two_ctas(cuda, U, n, p):
     d = _run(cuda, n, p, 4, 2, seed=80 + U, U=U)
     pa = d["problems"][0]["pass_a"]
     assert pa["tiles_per_unit"] == U and pa["grid"] < (n + 128 * U - 1) // (128 * U)
+
+
+@pytest.mark.parametrize("n,p,K,chains,U", [(1000, 700, 6, 2, 0), (333, 129, 3, 1, 0), (2049, 1000, 20, 4, 0),
+                                            (5000, 2000, 10, 7, 0), (10 * 128 + 5, 1000, 6, 2, 4),
+                                            (200 * 128 + 37, 512, 4, 2, 1), (3000, 500, 10, 40, 0)])
+def test_tc2_fp8_matches_oracle(cuda, n, p, K, chains, U):
+    """FP8 X: ragged rows and features, up to four tiles per unit (the widest
+    converter load), units split over two CTAs, several chain groups."""
+    _run(cuda, n, p, K, chains, seed=n + 11 * p, U=U, storage="fp8")
+
+
+@pytest.mark.parametrize("layout", ["masked", "unconstrained"])
+def test_tc2_fp8_layouts(cuda, layout):
+    _run(cuda, 1500, 400, 6, 3, seed=73, layout=layout, prior=("cauchy", 1.0), storage="fp8")
 
 
 def test_tc2_many_chains_in_groups(cuda):
