@@ -39,10 +39,12 @@
 //
 // Warp roles in both kernels: warp 0 bulk-copy producer (lane 0), warp 1 TMEM
 // owner and MMA issuer (lane 0), then the epilogue warps: pass A two per TMEM
-// lane quarter (warps 2-9, quarter warp % 4, half (warp - 2) / 4: the softmax
-// of one row is a serial chain, so a second warp per scheduler hides its
-// latency), pass B one per quarter (warps 2-5).  Every wait is bounded; a wait that runs out sets an error bit
-// and an abort flag, and every role then leaves its loop.
+// lane quarter for BF16 X (warps 2-9, quarter warp % 4, half (warp - 2) / 4:
+// the softmax of one row is a serial chain, so a second warp per scheduler
+// hides its latency), one for FP8 X (warps 2-5); pass B one per quarter (warps
+// 2-5); with FP8 X, eight converter warps follow in both kernels.  Every wait
+// is bounded; a wait that runs out sets an error bit and an abort flag, and
+// every role then leaves its loop.
 #include <algorithm>
 #include <vector>
 
@@ -65,16 +67,18 @@ using tc::tmem_ld16;
 constexpr int kRows = 128;
 constexpr int kBox = 64;                 // BF16 values per 128-byte row of a box
 constexpr int kBoxBytes = kRows * 128;   // one 128 x 64 BF16 box
-constexpr int kEpiHalves = 2;                      // pass A: epilogue warps per TMEM lane quarter
-constexpr int kEpiThreads = 128 * kEpiHalves;
-constexpr int kConvWarps = 4;                      // FP8 X: converter warps (both passes)
+// Pass A: epilogue warps per TMEM lane quarter, two for BF16 X, one for FP8 X
+// (whose eight converter warps need the registers).
+__host__ __device__ constexpr int epi_halves(bool fp8) { return fp8 ? 1 : 2; }
+constexpr int kConvWarps = 8;                      // FP8 X: converter warps (both passes)
 constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kConvGroups = 2;                     // converter groups, taking alternate ring steps
+constexpr int kGroupThreads = kConvThreads / kConvGroups;
 constexpr int kFp8BoxBytes = kRows * 64;           // FP8 box: 128 rows x 64 E4M3 codes, row-major
 // Blocks: pass A producer, MMA issuer, epilogue warps [, converters]; pass B
 // producer, MMA issuer, four drain warps [, converters].
-__host__ __device__ constexpr int threads_a(bool fp8) { return 64 + kEpiThreads + (fp8 ? kConvThreads : 0); }
+__host__ __device__ constexpr int threads_a(bool fp8) { return 64 + 128 * epi_halves(fp8) + (fp8 ? kConvThreads : 0); }
 __host__ __device__ constexpr int threads_b(bool fp8) { return 192 + (fp8 ? kConvThreads : 0); }
-constexpr int kThreadsA = threads_a(false);
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, long long limit, volatile int* abort) {
   const uint32_t a = smem_u32(bar);
@@ -94,10 +98,12 @@ __device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity, long 
     if (mbar_test_cta(a, parity)) return;
 }
 
-// Pass A's epilogue barrier over its kEpiThreads threads.
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+// Pass A's epilogue barrier over its T threads.
+template <int T>
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(T) : "memory"); }
 // The same barrier, ANDing a flag over the epilogue threads (so every
 // epilogue warp leaves its loop at the same unit).
+template <int T>
 __device__ __forceinline__ bool epi_bar_and(bool v) {
   uint32_t r;
   asm volatile(
@@ -106,23 +112,26 @@ __device__ __forceinline__ bool epi_bar_and(bool v) {
       "bar.red.and.pred po, 1, %2, pi;\n\t"
       "selp.u32 %0, 1, 0, po;\n\t}"
       : "=r"(r)
-      : "r"(v ? 1u : 0u), "n"(kEpiThreads)
+      : "r"(v ? 1u : 0u), "n"(T)
       : "memory");
   return r != 0;
 }
 
-// The FP8 converter warps' barrier (named barrier 2), and the same barrier
-// ANDing a flag over them (so every converter leaves its loop together).
-__device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kConvThreads) : "memory"); }
-__device__ __forceinline__ bool conv_bar_and(bool v) {
+// The barrier of FP8 converter group cg (named barrier 2 + cg), and the same
+// barrier ANDing a flag over the group (so all its warps leave their loop
+// together).
+__device__ __forceinline__ void conv_bar(int cg) {
+  asm volatile("bar.sync %0, %1;" ::"r"(2 + cg), "n"(kGroupThreads) : "memory");
+}
+__device__ __forceinline__ bool conv_bar_and(int cg, bool v) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred pi, po;\n\t"
       "setp.ne.u32 pi, %1, 0;\n\t"
-      "bar.red.and.pred po, 2, %2, pi;\n\t"
+      "bar.red.and.pred po, %2, %3, pi;\n\t"
       "selp.u32 %0, 1, 0, po;\n\t}"
       : "=r"(r)
-      : "r"(v ? 1u : 0u), "n"(kConvThreads)
+      : "r"(v ? 1u : 0u), "r"(2 + cg), "n"(kGroupThreads)
       : "memory");
   return r != 0;
 }
@@ -133,23 +142,23 @@ __device__ __forceinline__ bool conv_bar_and(bool v) {
 // i * kBoxBytes of `slot`), exactly (every E4M3 value is a BF16 value).  Every
 // converter thread reads all its input chunks before the group barrier and
 // writes only after it, so the in-place widening never overwrites unread
-// input.  ct: thread index within the converter group.
+// input.  cg: converter group, ct: thread index within it.
 template <int kMaxBoxes>
 __device__ __forceinline__ void widen_fp8_boxes(unsigned char* slot, int nbox, uint32_t in_stride, uint32_t in_off,
-                                                int ct) {
-  constexpr int kChunks = kFp8BoxBytes / 16;                 // 16-byte input chunks per box
-  constexpr int kPer = kMaxBoxes * kChunks / kConvThreads;   // chunks per thread at most
+                                                int cg, int ct) {
+  constexpr int kChunks = kFp8BoxBytes / 16;                  // 16-byte input chunks per box
+  constexpr int kPer = kMaxBoxes * kChunks / kGroupThreads;   // chunks per thread at most
   uint4 w[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
-    const int g = ct + kConvThreads * i;
+    const int g = ct + kGroupThreads * i;
     if (g < nbox * kChunks)
       w[i] = *reinterpret_cast<const uint4*>(slot + size_t(g / kChunks) * in_stride + in_off + size_t(g % kChunks) * 16);
   }
-  conv_bar();
+  conv_bar(cg);
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
-    const int g = ct + kConvThreads * i;
+    const int g = ct + kGroupThreads * i;
     if (g >= nbox * kChunks) break;
     const int bx = g / kChunks, ci = g % kChunks;
     const int r = ci >> 2, qq = ci & 3;                      // row, 16-code quarter of the row
@@ -229,6 +238,8 @@ __host__ __device__ inline LogitSmem logit_smem(int NST, uint32_t stage_bytes, i
 
 template <bool kFP8>
 __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitArgs A) {
+  constexpr int kEpiHalves = epi_halves(kFP8);
+  constexpr int kEpiThreads = 128 * kEpiHalves;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
   uint64_t* mdrain = zfree + 2;          // every MMA of this CTA complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdrain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(mdrain + 2);
-  uint64_t* conv = mdrain + 4;           // FP8: [NST] ring slot widened to BF16 (kConvWarps arrivals)
+  uint64_t* conv = mdrain + 4;           // FP8: [NST] ring slot widened to BF16 (one group's warps arrive)
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -262,7 +273,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
     }
     mbar_init(mdrain, 1);
     if (kFP8)
-      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps);
+      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps / kConvGroups);
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
@@ -368,22 +379,28 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
     }
   } else if (kFP8 && warp >= 2 + kEpiThreads / 32) {
     // ------------------------------------------------------------ FP8 converters
-    const int ct = tid - (64 + kEpiThreads);
+    // Group cg widens the ring steps s with s % kConvGroups == cg, so the
+    // groups' steps overlap.
+    const int cv = tid - (64 + kEpiThreads);
+    const int cg = cv / kGroupThreads, ct = cv % kGroupThreads;
     int64_t s = 0, pos = s_begin;
     Seg sg;
     bool ok = true;
     while (ok && next_seg(pos, s_end, A.nkb, sg)) {
       const int nt = int(min(int64_t(U), A.ntiles - (sg.u / A.ngroups) * U));
       for (int kb = sg.k0; kb < sg.k1; ++kb, ++s) {
+        if (int(s % kConvGroups) != cg) continue;
         const int st = int(s % NST);
-        const bool got = wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag);
-        if (!conv_bar_and(got && !*abort_flag)) {   // every converter agrees before the group barrier below
+        // One thread per group polls the copies' barrier; the group barrier
+        // passes the result (and orders the landed bytes) to the others.
+        const bool got = ct == 0 ? wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag) : true;
+        if (!conv_bar_and(cg, got && !*abort_flag)) {   // the group agrees before its barrier below
           if (!got) fail(ERR_TIMEOUT_STAGE);
           ok = false;
           break;
         }
         widen_fp8_boxes<4>(ring + size_t(st) * A.stage_bytes, nt, uint32_t(kBoxBytes),
-                           uint32_t(kBoxBytes - kFp8BoxBytes), ct);
+                           uint32_t(kBoxBytes - kFp8BoxBytes), cg, ct);
         __syncwarp();
         if (lane == 0) mbar_arrive_local(&conv[st]);
       }
@@ -400,7 +417,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
       const int a = int(j & 1);
       bool ok = (lane == 0) ? wait_bounded(&zdone[a], uint32_t((j >> 1) & 1), A.spin_limit, abort_flag) : true;
       if (!ok) fail(ERR_TIMEOUT_MMA);
-      if (!epi_bar_and(ok)) break;
+      if (!epi_bar_and<kEpiThreads>(ok)) break;
       fence_after_sync();
       const int64_t u = sg.u;
       const int64_t t0 = (u / A.ngroups) * U;
@@ -430,7 +447,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
         __syncwarp();
         if (lane == 0) mbar_arrive_local(&zfree[a]);
         __threadfence();
-        epi_bar();
+        epi_bar<kEpiThreads>();
         if (warp == 2 && lane == 0) st_release(A.sflag + blockIdx.x, 1);
         continue;
       }
@@ -447,7 +464,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
           }
           if (!got) fail(ERR_TIMEOUT_EXCHANGE);
         }
-        if (!epi_bar_and(got)) break;
+        if (!epi_bar_and<kEpiThreads>(got)) break;
         (void)ld_acquire(A.sflag + blockIdx.x + 1);   // every thread's own acquire of the stored partial
       }
       for (int i = 0; i < nt; ++i) {
@@ -521,7 +538,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
           for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
           if (lane == 0) s_wsum[c * 4 + q] = l;
         }
-        epi_bar();   // every chain's maximum and normaliser of this tile is in shared memory
+        epi_bar<kEpiThreads>();   // every chain's maximum and normaliser of this tile is in shared memory
         // Sweep 3: R = Y - P for the group's columns (zero past Cg and on rows past
         // n), written as BF16 in the MN-major 128-byte-swizzled boxes of pass B:
         // 16-byte chunk j (8 columns) of row r of box b at chunk j ^ (r % 8).
@@ -574,7 +591,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
         // in lane-quarter order.
         if (hf == 0 && r < nch)
           s_llc[g * gc + r] += ((s_wsum[r * 4] + s_wsum[r * 4 + 1]) + s_wsum[r * 4 + 2]) + s_wsum[r * 4 + 3];
-        epi_bar();   // shared state free for the next tile
+        epi_bar<kEpiThreads>();   // shared state free for the next tile
       }
       // The unit's accumulators are read: the MMA issuer may start unit j + 2 in them.
       fence_before_sync();
@@ -640,7 +657,7 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
   uint64_t* gdone = rempty + NRS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gdone + 2);
-  uint64_t* conv = gdone + 4;            // FP8: [NST] ring slot widened to BF16 (kConvWarps arrivals)
+  uint64_t* conv = gdone + 4;            // FP8: [NST] ring slot widened to BF16 (one group's warps arrive)
 
   // This CTA's unit: feature group f, chain group g, row range q.
   const int b = blockIdx.x;
@@ -663,7 +680,7 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
     }
     mbar_init(gdone, 1);
     if (kFP8)
-      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps);
+      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps / kConvGroups);
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
@@ -749,21 +766,26 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
     }
   } else if (kFP8 && warp >= 6) {
     // ------------------------------------------------------------ FP8 converters (warps 6-9)
-    const int ct = tid - 192;
+    // Group cg widens the ring steps s with s % kConvGroups == cg.
+    const int cv = tid - 192;
+    const int cg = cv / kGroupThreads, ct = cv % kGroupThreads;
     int64_t s = 0;
     bool ok = true;
     for (int64_t i = 0; i < T && ok && mbn > 0; ++i) {
       for (int mb = 0; mb < mbn; ++mb, ++s) {
+        if (int(s % kConvGroups) != cg) continue;
         const int st = int(s % NST);
-        const bool got = wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag);
-        if (!conv_bar_and(got && !*abort_flag)) {   // every converter agrees before the group barrier below
+        // One thread per group polls the copies' barrier; the group barrier
+        // passes the result (and orders the landed bytes) to the others.
+        const bool got = ct == 0 ? wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag) : true;
+        if (!conv_bar_and(cg, got && !*abort_flag)) {   // the group agrees before its barrier below
           if (!got) fail(ERR_TIMEOUT_STAGE);
           ok = false;
           break;
         }
         // The two 8 KB boxes sit back to back in the slot's upper 16 KB.
         widen_fp8_boxes<2>(ring + size_t(st) * 2 * kBoxBytes, 2, uint32_t(kFp8BoxBytes),
-                           uint32_t(2 * (kBoxBytes - kFp8BoxBytes)), ct);
+                           uint32_t(2 * (kBoxBytes - kFp8BoxBytes)), cg, ct);
         __syncwarp();
         if (lane == 0) mbar_arrive_local(&conv[st]);
       }
