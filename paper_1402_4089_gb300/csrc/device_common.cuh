@@ -214,18 +214,4 @@ __device__ __forceinline__ double accept_uniform(uint64_t seed, uint64_t iterati
   return word_to_uniform(w.x);
 }
 
-// Neumaier-compensated accumulation in double.
-struct Neumaier {
-  double s = 0.0, c = 0.0;
-  __device__ __forceinline__ void add(double x) {
-    const double t = s + x;
-    if (fabs(s) >= fabs(x))
-      c += (s - t) + x;
-    else
-      c += (x - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return s + c; }
-};
-
 }  // namespace hmc

@@ -5,8 +5,8 @@
 // keep-or-restore select, and the upload / layout conversions.
 //
 // Scalars (log K, kinetic energy) are summed in FP64: per-block partials in
-// fixed slots, combined by the last block of each chain (ticket counter) in
-// block order with Neumaier compensation, so results are bitwise repeatable.
+// fixed slots, combined by the last block of each chain (ticket counter) in a
+// fixed tree, so results are bitwise repeatable.
 #include <cmath>
 
 #include "device_common.cuh"
@@ -38,68 +38,49 @@ __device__ __forceinline__ ST prior_deriv(ST b, int kind, double s) {
   return -b / ST(s * s);
 }
 
-// Fixed-order block sum of two doubles; result valid in thread 0.
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kThreads / 32], sb[kThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    sa[w] = a;
-    sb[w] = b;
-  }
+// Fixed-order block sums of N doubles: a butterfly within each warp (every
+// lane ends with the same bits), then the warps' sums in a butterfly of warp 0;
+// the results are valid in thread 0.  Plain FP64 additions in a fixed tree:
+// the trees here meet at most a few thousand partials, whose rounding stays far
+// below what the accept test or the oracle comparisons can see, and every
+// dependent FP64 step is slow on this GPU (its FP64 units are few), so the
+// chains are kept short and the N sums interleave.
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N]) {
+  constexpr int kWarps = kThreads / 32;
+  __shared__ double ws[N][kWarps];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();   // ws may still be read by a previous call
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) ws[k][w] = v[k];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    a = 0.0;
-    b = 0.0;
-    for (int i = 0; i < int(blockDim.x >> 5); ++i) {
-      a += sa[i];
-      b += sb[i];
-    }
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = lane < kWarps ? ws[k][lane] : 0.0;
+#pragma unroll
+    for (int o = kWarps / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < N; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   }
 }
 
-// Neumaier-compensated sum of v[i * stride], i < n, by every thread of the
-// block in a fixed order: thread t adds i = t, t + blockDim, ...; the per-thread
-// sums meet in a fixed tree (shuffles within a warp, then warps in order).
-// The result is valid in thread 0.
-__device__ __forceinline__ void merge(double& s, double& c, double s2, double c2) {
-  const double t = s + s2;
-  c += (fabs(s) >= fabs(s2) ? (s - t) + s2 : (s2 - t) + s) + c2;
-  s = t;
-}
-__device__ double block_sum_fixed(const double* v, int n, size_t stride) {
-  __shared__ double ws[kThreads / 32][2];
-  Neumaier acc;
+// Thread t's in-order share of v[i * stride], i = t, t + blockDim, ...: four
+// interleaved accumulators (fixed assignment, combined in order) keep the
+// dependent FP64 chain a quarter as long.
+__device__ __forceinline__ double thread_share(const double* v, int n, size_t stride) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   int i = threadIdx.x;
-  for (; i + 3 * int(blockDim.x) < n; i += 4 * int(blockDim.x)) {   // four loads in flight, added in order
-    double t[4];
+  for (; i + 3 * int(blockDim.x) < n; i += 4 * int(blockDim.x)) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) t[u] = v[size_t(i + u * int(blockDim.x)) * stride];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc.add(t[u]);
+    for (int u = 0; u < 4; ++u) acc[u] += v[size_t(i + u * int(blockDim.x)) * stride];
   }
-  for (; i < n; i += blockDim.x) acc.add(v[size_t(i) * stride]);
-  double s = acc.s, c = acc.c;
-  for (int o = 16; o > 0; o >>= 1) {
-    const double s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
-    merge(s, c, s2, c2);
-  }
-  const int w = threadIdx.x >> 5;
-  __syncthreads();   // ws may still be read by a previous call
-  if ((threadIdx.x & 31) == 0) {
-    ws[w][0] = s;
-    ws[w][1] = c;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    s = ws[0][0];
-    c = ws[0][1];
-    for (int i = 1; i < int(blockDim.x >> 5); ++i) merge(s, c, ws[i][0], ws[i][1]);
-  }
-  return s + c;
+  for (; i < n; i += blockDim.x) acc[0] += v[size_t(i) * stride];
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 // Ticket: true in exactly one block (the last to finish) of chain c.
@@ -182,19 +163,21 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
     if (mode & UPD_BETA) beta[idx] = bv + eb * ev;
   }
   if (!(mode & UPD_SCALARS)) return;
-  block_sum2(prior_s, kin_s);
+  double bs[2] = {prior_s, kin_s};
+  block_sum<2>(bs);
   if (threadIdx.x == 0) {
     double* sl = A.scal + (size_t(c) * A.nblk + blockIdx.x) * 2;
-    sl[0] = prior_s;
-    sl[1] = kin_s;
+    sl[0] = bs[0];
+    sl[1] = bs[1];
   }
   if (!last_block(A.tickets + c, gridDim.x)) return;
   // The whole last block sums the block partials and the log-likelihood
-  // partials of the fused pass, each in a fixed order.
+  // partials of the gradient pass, each in a fixed order, in one tree.
   const double* sl = A.scal + size_t(c) * A.nblk * 2;
-  const double prv = block_sum_fixed(sl, int(gridDim.x), 2);
-  const double kiv = block_sum_fixed(sl + 1, int(gridDim.x), 2);
-  const double liv = block_sum_fixed(A.lpart + c, A.nlparts, size_t(A.lpart_cstride));
+  double tot[3] = {thread_share(sl, int(gridDim.x), 2), thread_share(sl + 1, int(gridDim.x), 2),
+                   thread_share(A.lpart + c, A.nlparts, size_t(A.lpart_cstride))};
+  block_sum<3>(tot);
+  const double prv = tot[0], kiv = tot[1], liv = tot[2];
   if (threadIdx.x != 0) return;
   const double logk = liv + prv;
   A.tickets[c] = 0u;
@@ -238,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) traj_start_kernel(const UpdateArgs A
   const uint64_t seed = *A.seed;
   const uint64_t chain_word = uint64_t(c) | (uint64_t(A.chains_word_hi) << 32);
   const ST half = ST(0.5 * A.eps), full = ST(A.eps);
-  double kin = 0.0, unused = 0.0;
+  double kin = 0.0;
   for (int64_t qb = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; qb < nqb; qb += int64_t(gridDim.x) * blockDim.x) {
     double z[4];
     momentum_block(seed, it, chain_word, uint64_t(qb), z);
@@ -258,10 +241,13 @@ __global__ void __launch_bounds__(kThreads) traj_start_kernel(const UpdateArgs A
       beta[idx] = b + full * eh;
     }
   }
-  block_sum2(kin, unused);
-  if (threadIdx.x == 0) A.scal[(size_t(c) * A.nblk + blockIdx.x) * 2 + 1] = kin;
+  double kb[1] = {kin};
+  block_sum<1>(kb);
+  if (threadIdx.x == 0) A.scal[(size_t(c) * A.nblk + blockIdx.x) * 2 + 1] = kb[0];
   if (!last_block(A.tickets + c, gridDim.x)) return;
-  const double kiv = block_sum_fixed(A.scal + size_t(c) * A.nblk * 2 + 1, int(gridDim.x), 2);
+  double kt[1] = {thread_share(A.scal + size_t(c) * A.nblk * 2 + 1, int(gridDim.x), 2)};
+  block_sum<1>(kt);
+  const double kiv = kt[0];
   if (threadIdx.x != 0) return;
   A.tickets[c] = 0u;
   A.logk0[c] = A.logk[c];
