@@ -146,3 +146,37 @@ def test_tc2_timeout_is_reported_and_handle_recovers(cuda):
     b = beta.cpu().numpy()[0].astype(np.float64)
     assert lk_err(lp[0], model.log_kernel(Xq, y, b, "gaussian", 1.0)) <= TOL_L
     assert max(grad_errs(g[0], model.grad_log_kernel(Xq, y, b, "gaussian", 1.0))) <= TOL_G
+
+
+@pytest.mark.parametrize("engine", [3, 2])
+def test_fp8_every_code_widened_exactly(cuda, engine):
+    """Column 5 of X holds every finite E4M3 code (zeros, subnormals, both signs,
+    +-448): the stored codes match the oracle's quantisation bit for bit and the
+    gradient matches the oracle on the dequantised X, so every widening path
+    (the field arithmetic for normal codes, the exact conversion otherwise) is
+    exact."""
+    import torch
+    n, p, K, chains = 700, 130, 4, 2
+    X, y, _ = synthetic.make_problem(n, p, K, seed=91)
+    codes = np.array([c for c in range(256) if c not in (0x7F, 0xFF)])
+    s = np.float32(0.01)
+    col = (quant.e4m3_table()[codes] * s).astype(np.float32)
+    X[:, 5] = np.resize(col, n)
+    rng = np.random.default_rng(92)
+    beta = (0.05 * rng.standard_normal((chains, K - 1, p))).astype(np.float32)
+    with hmc.create(X, y, K, "gaussian", 10.0, x_storage="fp8", max_chains=chains, engine=engine) as h:
+        bits, scales = h.get_x()
+        lp, g = h.logpost_grad(torch.from_numpy(beta).to(cuda))
+        torch.cuda.synchronize()
+        lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    c_o, s_o = quant.fp8_quantize(X)
+    assert np.array_equal(scales, s_o) and np.array_equal(bits, c_o)
+    assert set(np.unique(bits[:, 5])) == set(codes.tolist())
+    Xq = quant.fp8_dequantize(bits, scales).astype(np.float64)
+    for c in range(chains):
+        lk_o = model.log_kernel(Xq, y, beta[c], "gaussian", 10.0)
+        g_o = model.grad_log_kernel(Xq, y, beta[c], "gaussian", 10.0)
+        eg, ee = grad_errs(g[c], g_o)
+        assert lk_err(lp[c], lk_o) <= TOL_L and eg <= TOL_G and ee <= TOL_G, (c, eg, ee)
+        # column 5 alone: its gradient entries depend on every code's value
+        assert np.max(np.abs(g[c][:, 5] - g_o[:, 5])) <= TOL_G * max(np.abs(g_o[:, 5]).max(), 1e-30)
