@@ -72,8 +72,11 @@ constexpr int kBoxBytes = kRows * 128;   // one 128 x 64 BF16 box
 __host__ __device__ constexpr int epi_halves(bool fp8) { return fp8 ? 1 : 2; }
 constexpr int kConvWarps = 8;                      // FP8 X: converter warps (both passes)
 constexpr int kConvThreads = 32 * kConvWarps;
-constexpr int kConvGroups = 2;                     // converter groups, taking alternate ring steps
-constexpr int kGroupThreads = kConvThreads / kConvGroups;
+// Converter groups taking alternate ring steps: one in pass A (its steps carry
+// U boxes), two in pass B (two boxes a step) -- measured on n=5e4 p=1e4 K=20:
+// pass A 383 us with one group against 402-445 with two, pass B 250-259 with
+// two against 296 with one.
+constexpr int kConvGroupsA = 1, kConvGroupsB = 2;
 constexpr int kFp8BoxBytes = kRows * 64;           // FP8 box: 128 rows x 64 E4M3 codes, row-major
 // Blocks: pass A producer, MMA issuer, epilogue warps [, converters]; pass B
 // producer, MMA issuer, four drain warps [, converters].
@@ -117,12 +120,14 @@ __device__ __forceinline__ bool epi_bar_and(bool v) {
   return r != 0;
 }
 
-// The barrier of FP8 converter group cg (named barrier 2 + cg), and the same
-// barrier ANDing a flag over the group (so all its warps leave their loop
-// together).
+// The barrier of FP8 converter group cg of T threads (named barrier 2 + cg),
+// and the same barrier ANDing a flag over the group (so all its warps leave
+// their loop together).
+template <int T>
 __device__ __forceinline__ void conv_bar(int cg) {
-  asm volatile("bar.sync %0, %1;" ::"r"(2 + cg), "n"(kGroupThreads) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"r"(2 + cg), "n"(T) : "memory");
 }
+template <int T>
 __device__ __forceinline__ bool conv_bar_and(int cg, bool v) {
   uint32_t r;
   asm volatile(
@@ -131,7 +136,7 @@ __device__ __forceinline__ bool conv_bar_and(int cg, bool v) {
       "bar.red.and.pred po, %2, %3, pi;\n\t"
       "selp.u32 %0, 1, 0, po;\n\t}"
       : "=r"(r)
-      : "r"(v ? 1u : 0u), "r"(2 + cg), "n"(kGroupThreads)
+      : "r"(v ? 1u : 0u), "r"(2 + cg), "n"(T)
       : "memory");
   return r != 0;
 }
@@ -142,10 +147,11 @@ __device__ __forceinline__ bool conv_bar_and(int cg, bool v) {
 // i * kBoxBytes of `slot`), exactly (every E4M3 value is a BF16 value).  Every
 // converter thread reads all its input chunks before the group barrier and
 // writes only after it, so the in-place widening never overwrites unread
-// input.  cg: converter group, ct: thread index within it.
-template <int kMaxBoxes>
+// input.  cg: converter group of T threads, ct: thread index within it.
+template <int kMaxBoxes, int T>
 __device__ __forceinline__ void widen_fp8_boxes(unsigned char* slot, int nbox, uint32_t in_stride, uint32_t in_off,
                                                 int cg, int ct) {
+  constexpr int kGroupThreads = T;
   constexpr int kChunks = kFp8BoxBytes / 16;                  // 16-byte input chunks per box
   constexpr int kPer = kMaxBoxes * kChunks / kGroupThreads;   // chunks per thread at most
   uint4 w[kPer];
@@ -155,7 +161,7 @@ __device__ __forceinline__ void widen_fp8_boxes(unsigned char* slot, int nbox, u
     if (g < nbox * kChunks)
       w[i] = *reinterpret_cast<const uint4*>(slot + size_t(g / kChunks) * in_stride + in_off + size_t(g % kChunks) * 16);
   }
-  conv_bar(cg);
+  conv_bar<T>(cg);
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int g = ct + kGroupThreads * i;
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
     }
     mbar_init(mdrain, 1);
     if (kFP8)
-      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps / kConvGroups);
+      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps / kConvGroupsA);
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
@@ -379,8 +385,8 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
     }
   } else if (kFP8 && warp >= 2 + kEpiThreads / 32) {
     // ------------------------------------------------------------ FP8 converters
-    // Group cg widens the ring steps s with s % kConvGroups == cg, so the
-    // groups' steps overlap.
+    // Group cg widens the ring steps s with s % kConvGroups == cg.
+    constexpr int kConvGroups = kConvGroupsA, kGroupThreads = kConvThreads / kConvGroupsA;
     const int cv = tid - (64 + kEpiThreads);
     const int cg = cv / kGroupThreads, ct = cv % kGroupThreads;
     int64_t s = 0, pos = s_begin;
@@ -394,13 +400,13 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
         // One thread per group polls the copies' barrier; the group barrier
         // passes the result (and orders the landed bytes) to the others.
         const bool got = ct == 0 ? wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag) : true;
-        if (!conv_bar_and(cg, got && !*abort_flag)) {   // the group agrees before its barrier below
+        if (!conv_bar_and<kGroupThreads>(cg, got && !*abort_flag)) {   // the group agrees before its barrier below
           if (!got) fail(ERR_TIMEOUT_STAGE);
           ok = false;
           break;
         }
-        widen_fp8_boxes<4>(ring + size_t(st) * A.stage_bytes, nt, uint32_t(kBoxBytes),
-                           uint32_t(kBoxBytes - kFp8BoxBytes), cg, ct);
+        widen_fp8_boxes<4, kGroupThreads>(ring + size_t(st) * A.stage_bytes, nt, uint32_t(kBoxBytes),
+                                          uint32_t(kBoxBytes - kFp8BoxBytes), cg, ct);
         __syncwarp();
         if (lane == 0) mbar_arrive_local(&conv[st]);
       }
@@ -680,7 +686,7 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
     }
     mbar_init(gdone, 1);
     if (kFP8)
-      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps / kConvGroups);
+      for (int s = 0; s < NST; ++s) mbar_init(&conv[s], kConvWarps / kConvGroupsB);
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
@@ -767,6 +773,7 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
   } else if (kFP8 && warp >= 6) {
     // ------------------------------------------------------------ FP8 converters (warps 6-9)
     // Group cg widens the ring steps s with s % kConvGroups == cg.
+    constexpr int kConvGroups = kConvGroupsB, kGroupThreads = kConvThreads / kConvGroupsB;
     const int cv = tid - 192;
     const int cg = cv / kGroupThreads, ct = cv % kGroupThreads;
     int64_t s = 0;
@@ -778,14 +785,14 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
         // One thread per group polls the copies' barrier; the group barrier
         // passes the result (and orders the landed bytes) to the others.
         const bool got = ct == 0 ? wait_bounded(&full[st], uint32_t((s / NST) & 1), A.spin_limit, abort_flag) : true;
-        if (!conv_bar_and(cg, got && !*abort_flag)) {   // the group agrees before its barrier below
+        if (!conv_bar_and<kGroupThreads>(cg, got && !*abort_flag)) {   // the group agrees before its barrier below
           if (!got) fail(ERR_TIMEOUT_STAGE);
           ok = false;
           break;
         }
         // The two 8 KB boxes sit back to back in the slot's upper 16 KB.
-        widen_fp8_boxes<2>(ring + size_t(st) * 2 * kBoxBytes, 2, uint32_t(kFp8BoxBytes),
-                           uint32_t(2 * (kBoxBytes - kFp8BoxBytes)), cg, ct);
+        widen_fp8_boxes<2, kGroupThreads>(ring + size_t(st) * 2 * kBoxBytes, 2, uint32_t(kFp8BoxBytes),
+                                          uint32_t(2 * (kBoxBytes - kFp8BoxBytes)), cg, ct);
         __syncwarp();
         if (lane == 0) mbar_arrive_local(&conv[st]);
       }
