@@ -183,3 +183,20 @@ def test_sample_fp32_wide_default_engine(cuda):
     assert out[0][2] == out[1][2]
     scale = max(1e-6, np.abs(out[1][1]).max())
     assert np.max(np.abs(out[0][1] - out[1][1])) <= 1e-4 * scale
+
+
+def test_tempered_sampling_fp32_follows_the_fused_engine(cuda):
+    """Annealed iterations on engine 4 (FP32) against the fused CUDA-core engine."""
+    import torch
+    n, p, K, iters = 1200, 150, 6, 8
+    X, y, _ = synthetic.make_problem(n, p, K, seed=95)
+    temps = hmc.annealing_temperatures(iters, t0=20.0, r=0.6)
+    out = []
+    for engine in (4, 1):
+        with hmc.create(X, y, K, "gaussian", 2.0, max_chains=2, engine=engine) as h:
+            s = torch.empty((iters, 2, K - 1, p), dtype=torch.float32, device=cuda)
+            st = h.sample(2, 6, 0.01, iters, 23, beta0=torch.zeros((2, K - 1, p), device=cuda), samples=s, temps=temps)
+            out.append((s.cpu().numpy(), [x["accepted"] for x in st]))
+    assert out[0][1] == out[1][1]
+    scale = max(1e-6, np.abs(out[1][0]).max())
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-4 * scale

@@ -180,3 +180,42 @@ def test_fp8_every_code_widened_exactly(cuda, engine):
         assert lk_err(lp[c], lk_o) <= TOL_L and eg <= TOL_G and ee <= TOL_G, (c, eg, ee)
         # column 5 alone: its gradient entries depend on every code's value
         assert np.max(np.abs(g[c][:, 5] - g_o[:, 5])) <= TOL_G * max(np.abs(g_o[:, 5]).max(), 1e-30)
+
+
+def test_tc2_sample_64_chains_follows_the_fused_engine(cuda):
+    """64 chains in one launch pair (two-pass) against the fused engine, which
+    needs several launches for them: same momenta and accept draws, gradients
+    equal to rounding, so every chain's samples and accept counts agree."""
+    import torch
+    n, p, K, chains, iters = 3000, 256, 4, 64, 4
+    X, y, _ = synthetic.make_problem(n, p, K, seed=93)
+    out = []
+    for engine in (3, 2):
+        with hmc.create(X, y, K, "gaussian", 10.0, x_storage="bf16", max_chains=chains, engine=engine) as h:
+            d = h.describe()
+            if engine == 2:
+                assert d["problems"][0]["group_chains"] < chains        # several fused launches
+            s = torch.empty((iters, chains, K - 1, p), dtype=torch.float32, device=cuda)
+            st = h.sample(chains, 8, 0.004, iters, 17, beta0=torch.zeros((chains, K - 1, p), device=cuda), samples=s)
+            out.append((s.cpu().numpy(), [x["accepted"] for x in st]))
+    assert out[0][1] == out[1][1]
+    scale = np.abs(out[1][0]).max()
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-3 * scale
+
+
+def test_tc2_tempered_sampling_follows_the_fused_engine(cuda):
+    """Annealed iterations (Sec. 3.2 schedule through the library) on the two-pass
+    engine against the fused engine: same accept decisions, close samples."""
+    import torch
+    X, y, _ = synthetic.make_problem(1500, 200, 5, seed=94)
+    iters = 8
+    temps = hmc.annealing_temperatures(iters, t0=20.0, r=0.6)
+    out = []
+    for engine in (3, 2):
+        with hmc.create(X, y, 5, "cauchy", 1.0, x_storage="bf16", max_chains=2, engine=engine) as h:
+            s = torch.empty((iters, 2, 4, 200), dtype=torch.float32, device=cuda)
+            st = h.sample(2, 6, 0.01, iters, 21, beta0=torch.zeros((2, 4, 200), device=cuda), samples=s, temps=temps)
+            out.append((s.cpu().numpy(), [x["accepted"] for x in st]))
+    assert out[0][1] == out[1][1]
+    scale = np.abs(out[1][0]).max()
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-3 * scale
