@@ -67,6 +67,7 @@ using tc::tmem_ld16;
 constexpr int kRows = 128;
 constexpr int kBox = 64;                 // BF16 values per 128-byte row of a box
 constexpr int kBoxBytes = kRows * 128;   // one 128 x 64 BF16 box
+constexpr int kMaxCols = 256;            // accumulator columns of one row tile (chains x classes of a group), at most
 // Pass A: epilogue warps per TMEM lane quarter, two for BF16 X, one for FP8 X
 // (whose eight converter warps need the registers).
 __host__ __device__ constexpr int epi_halves(bool fp8) { return fp8 ? 1 : 2; }
@@ -118,6 +119,57 @@ __device__ __forceinline__ bool epi_bar_and(bool v) {
       : "r"(v ? 1u : 0u), "n"(T)
       : "memory");
   return r != 0;
+}
+
+// Whole warp: store 16 consecutive 32-bit columns of this warp's 32 TMEM lanes
+// (one lane per thread); tmem_st_wait() waits for this thread's stores.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Predicated shared-memory store and load (PTX predicates, so a sweep over a
+// row's columns has no branch at a chain's last column).
+__device__ __forceinline__ void st_shared_if(float* p, float v, bool pred) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.f32 [%0], %1;\n\t}" ::"r"(smem_u32(p)),
+               "f"(v), "r"(uint32_t(pred))
+               : "memory");
+}
+__device__ __forceinline__ float ld_shared_if(const float* p, float old, bool pred) {
+  float v = old;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.f32 %0, [%1];\n\t}"
+               : "+f"(v)
+               : "r"(smem_u32(p)), "r"(uint32_t(pred))
+               : "memory");
+  return v;
+}
+
+// Bits e of a 16-column block whose column offset lies in [lo, hi).
+__device__ __forceinline__ uint32_t col_bits(int lo, int hi) {
+  lo = max(lo, 0);
+  hi = min(hi, 16);
+  return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
+}
+
+// (hi, lo) += (bh, bl) for unevaluated float pairs (value hi + lo, |lo| below
+// half an ulp of hi): Knuth's TwoSum of the leading parts, the trailing parts
+// and the rounding error added, and a Dekker FastTwoSum renormalisation.  Row
+// log-likelihood sums carried this way keep about twice FP32's precision
+// without FP64 arithmetic, which this part runs at a small fraction of FP32's rate.
+__device__ __forceinline__ void add_pair(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bv = s - hi;
+  const float e = (hi - (s - bv)) + (bh - bv);
+  const float t = e + (lo + bl);
+  hi = s + t;
+  lo = t - (hi - s);
 }
 
 // The barrier of FP8 converter group cg of T threads (named barrier 2 + cg),
@@ -224,7 +276,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 struct LogitSmem {
-  size_t ring, mx, sm, zy, llr, llc, bars, total;
+  size_t ring, mx, sm, zy, llr, llc, tab, bars, total;
 };
 
 __host__ __device__ inline LogitSmem logit_smem(int NST, uint32_t stage_bytes, int gc, int chains) {
@@ -236,6 +288,7 @@ __host__ __device__ inline LogitSmem logit_smem(int NST, uint32_t stage_bytes, i
   L.zy = off;    off = al(off + size_t(gc) * kRows * 4, 16);
   L.llr = off;   off = al(off + size_t(gc) * 4 * 8, 16);
   L.llc = off;   off = al(off + size_t(chains) * 8, 16);
+  L.tab = off;   off = al(off + size_t(kMaxCols + kMaxCols / 16) * 4, 16);
   // full, empty [NST]; zdone, zfree [2]; mdrain; TMEM slot; abort flag; (pad); conv [NST]
   L.bars = off;  off = al(off + size_t(3 * NST + 8) * 8 + 16, 16);
   L.total = off + 1024;   // slack for aligning the dynamic base to 1024
@@ -246,6 +299,7 @@ template <bool kFP8>
 __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitArgs A) {
   constexpr int kEpiHalves = epi_halves(kFP8);
   constexpr int kEpiThreads = 128 * kEpiHalves;
+  constexpr int kFold = kFP8 ? 1 : 3;           // partial-logit blocks in flight when folding (no spills)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -253,11 +307,13 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
   const bool zl = A.zlogit != 0;
   const LogitSmem Lo = logit_smem(NST, A.stage_bytes, gc, A.chains);
   unsigned char* ring = smem + Lo.ring;
-  float* s_m = reinterpret_cast<float*>(smem + Lo.mx);     // [gc][128] maximum logit of each chain, per row
+  float* s_m = reinterpret_cast<float*>(smem + Lo.mx);     // [gc][128] maximum logit of each chain, then its log-normaliser
   float* s_s = reinterpret_cast<float*>(smem + Lo.sm);     // [gc][128] sum of shifted exponentials
   float* s_zy = reinterpret_cast<float*>(smem + Lo.zy);    // [gc][128] logit of the observed class
-  double* s_wsum = reinterpret_cast<double*>(smem + Lo.llr);  // [gc][4] log-likelihood sums of each warp's rows
-  double* s_llc = reinterpret_cast<double*>(smem + Lo.llc);  // [chains] this CTA's sums
+  float2* s_wsum = reinterpret_cast<float2*>(smem + Lo.llr);  // [gc][4] log-likelihood sums of each warp's rows (pairs)
+  float2* s_llc = reinterpret_cast<float2*>(smem + Lo.llc);   // [chains] this CTA's sums (pairs)
+  int* s_cm = reinterpret_cast<int*>(smem + Lo.tab);          // [N] column j: chain c * 128 | class k << 16
+  uint32_t* s_cend = reinterpret_cast<uint32_t*>(s_cm + kMaxCols);  // [N / 16] bit e: column 16b + e ends a chain
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lo.bars);
   uint64_t* full = bars;
   uint64_t* empty = bars + NST;
@@ -283,7 +339,16 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
     *abort_flag = 0;
     fence_mbar_init_cluster();
   }
-  for (int c = tid; c < A.chains; c += int(blockDim.x)) s_llc[c] = 0.0;
+  for (int c = tid; c < A.chains; c += int(blockDim.x)) s_llc[c] = make_float2(0.f, 0.f);
+  for (int j = tid; j < N; j += int(blockDim.x)) {
+    const int c = j / Km1;   // columns past the group's last chain point at chain gc - 1 (masked where read)
+    s_cm[j] = min(c, gc - 1) * kRows | (j - c * Km1) << 16;
+  }
+  for (int b = tid; b < N / 16; b += int(blockDim.x)) {
+    uint32_t m = 0;
+    for (int e = 0; e < 16; ++e) m |= ((16 * b + e + 1) % Km1 == 0 ? 1u : 0u) << e;
+    s_cend[b] = m;
+  }
   if (warp == 1) tmem_alloc(tmem_slot, A.tmem_cols);
   fence_before_sync();
   __syncthreads();
@@ -479,111 +544,139 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
         const bool valid = grow < A.n;
         const int yv = valid ? __ldg(A.y + grow) : -1;
         const uint32_t acc = tq + uint32_t((a * U + i) * N);
-        const float* hpi = hp + size_t(i) * N * kRows + r;   // stored partial of column col: hpi[col * kRows]
-        // Three sweeps over the row's logits in column order, chains walked with
-        // running (chain, class) counters; per-chain results go to shared memory
-        // once per chain.  Sweep 1: the maximum of every chain's logits (the
-        // zero logit of class K included) and the logit of the observed class.
+        if (head) {
+          // Add the next CTA's partial logits to the accumulator in place (16-column
+          // blocks interleaved over the quarter's warps, kFold blocks in flight), so
+          // the sweeps below read TMEM only.
+          const float* hpi = hp + size_t(i) * N * kRows + r;   // partial of column col: hpi[col * kRows]
+          for (int c0 = 16 * hf; c0 < Cg; c0 += 16 * kFold * kEpiHalves) {
+            float h[kFold][16], v[16];
+#pragma unroll
+            for (int j = 0; j < kFold; ++j)
+              if (c0 + 16 * kEpiHalves * j < Cg)
+#pragma unroll
+                for (int e = 0; e < 16; ++e) h[j][e] = hpi[size_t(c0 + 16 * kEpiHalves * j + e) * kRows];
+#pragma unroll
+            for (int j = 0; j < kFold; ++j)
+              if (c0 + 16 * kEpiHalves * j < Cg) {
+                const uint32_t ta = acc + uint32_t(c0 + 16 * kEpiHalves * j);
+                tmem_ld16(ta, v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] += h[j][e];
+                tmem_st16(ta, v);
+              }
+          }
+          tmem_st_wait();
+          fence_before_sync();
+          epi_bar<kEpiThreads>();   // every column of the tile holds the whole unit's logits
+          fence_after_sync();
+        }
+        // Sweeps 1-2 over the half's columns [cb, ce) in order, branch-free: bit e
+        // of s_cend marks a chain's last column, where the chain's result is stored
+        // (predicated) and the running value restarts.
+        // Sweep 1: the maximum of every chain's logits (the zero logit of class K
+        // included) and the logit of the observed class (at column d of the chain).
         if (cb < ce) {
-          int c = ch0, k = 0;
-          float m = zl ? 0.f : -INFINITY, zy = 0.f;
+          const float m0 = zl ? 0.f : -INFINITY;
+          float m = m0, zy = 0.f;
+          int ix = ch0 * kRows + r;
+          int d = ch0 * Km1 + (yv >= 0 && yv < Km1 ? yv : -32);   // -32: no column of any chain
           for (int c0 = cb & ~15; c0 < ce; c0 += 16) {
             float v[16];
             tmem_ld16(acc + uint32_t(c0), v);
-            if (head)
-#pragma unroll
-              for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
+            const uint32_t in = col_bits(cb - c0, ce - c0), ends = s_cend[c0 >> 4] & in;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              if (c0 + e >= cb && c0 + e < ce) {
-                m = fmaxf(m, v[e]);
-                if (k == yv) zy = v[e];
-                if (++k == Km1) {
-                  s_m[c * kRows + r] = m;
-                  s_zy[c * kRows + r] = zy;
-                  ++c;
-                  k = 0;
-                  m = zl ? 0.f : -INFINITY;
-                  zy = 0.f;
-                }
-              }
+              const bool last = (ends >> e) & 1u;
+              m = fmaxf(m, (in >> e) & 1u ? v[e] : -INFINITY);
+              zy = c0 + e == d ? v[e] : zy;
+              st_shared_if(s_m + ix, m, last);
+              st_shared_if(s_zy + ix, zy, last);
+              ix += last ? kRows : 0;
+              d += last ? Km1 : 0;
+              m = last ? m0 : m;
             }
           }
         }
-        // Sweep 2: the sum of exponentials of every chain, shifted by its maximum.
+        // Sweep 2: every chain's sum of exponentials shifted by its maximum (the
+        // next chain's maximum is loaded one chain ahead).
         if (cb < ce) {
-          int c = ch0, k = 0;
-          float mc = s_m[c * kRows + r], ss = zl ? expf(-mc) : 0.f;
+          int ix = ch0 * kRows + r, cn = ch0 + 2;
+          float mc = s_m[ix], mn = ch0 + 1 < ch1 ? s_m[ix + kRows] : 0.f, ss = 0.f;
           for (int c0 = cb & ~15; c0 < ce; c0 += 16) {
             float v[16];
             tmem_ld16(acc + uint32_t(c0), v);
-            if (head)
-#pragma unroll
-              for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
+            const uint32_t in = col_bits(cb - c0, ce - c0), ends = s_cend[c0 >> 4] & in;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              if (c0 + e >= cb && c0 + e < ce) {
-                ss += expf(v[e] - mc);
-                if (++k == Km1) {
-                  s_s[c * kRows + r] = ss;
-                  ++c;
-                  k = 0;
-                  if (c < ch1) {
-                    mc = s_m[c * kRows + r];
-                    ss = zl ? expf(-mc) : 0.f;
-                  }
-                }
-              }
+              const bool last = (ends >> e) & 1u;
+              const float x = expf(v[e] - mc);
+              ss += (in >> e) & 1u ? x : 0.f;
+              st_shared_if(s_s + ix, ss, last);
+              ix += last ? kRows : 0;
+              mc = last ? mn : mc;
+              mn = ld_shared_if(s_m + cn * kRows + r, mn, last && cn < ch1);
+              cn += last ? 1 : 0;
+              ss = last ? 0.f : ss;
             }
           }
         }
-        // Row log-likelihoods of this half's chains summed over the warp's 32 rows.
-        for (int c = ch0; c < ch1; ++c) {
-          double l = valid ? double(s_zy[c * kRows + r] - s_m[c * kRows + r] - logf(s_s[c * kRows + r])) : 0.0;
+        // Per chain: the log-normaliser lse = m + log(sum) (the zero logit's term
+        // added to the sum last) replaces the maximum, the row's log-likelihood
+        // zy - lse replaces the observed logit, and the log-likelihoods are summed
+        // over the warp's 32 rows as float pairs, two chains at a time.
+        for (int c = ch0; c < ch1; c += 2) {
+          const bool two = c + 1 < ch1;
+          float ll[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-          if (lane == 0) s_wsum[c * 4 + q] = l;
+          for (int j = 0; j < 2; ++j)
+            if (j == 0 || two) {
+              const int ix = (c + j) * kRows + r;
+              const float mx = s_m[ix], ssum = s_s[ix] + (zl ? expf(-mx) : 0.f);
+              const float lse = mx + logf(ssum);
+              s_m[ix] = lse;
+              ll[j] = valid ? s_zy[ix] - lse : 0.f;
+            }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float a0 = __shfl_down_sync(0xffffffffu, ll[0], o), b0 = __shfl_down_sync(0xffffffffu, lo[0], o);
+            const float a1 = __shfl_down_sync(0xffffffffu, ll[1], o), b1 = __shfl_down_sync(0xffffffffu, lo[1], o);
+            add_pair(ll[0], lo[0], a0, b0);
+            add_pair(ll[1], lo[1], a1, b1);
+          }
+          if (lane == 0) {
+            s_wsum[c * 4 + q] = make_float2(ll[0], lo[0]);
+            if (two) s_wsum[(c + 1) * 4 + q] = make_float2(ll[1], lo[1]);
+          }
         }
-        epi_bar<kEpiThreads>();   // every chain's maximum and normaliser of this tile is in shared memory
-        // Sweep 3: R = Y - P for the group's columns (zero past Cg and on rows past
-        // n), written as BF16 in the MN-major 128-byte-swizzled boxes of pass B:
-        // 16-byte chunk j (8 columns) of row r of box b at chunk j ^ (r % 8).
+        epi_bar<kEpiThreads>();   // every chain's log-normaliser of this tile is in shared memory
+        // Sweep 3: R = Y - P, P = exp(z - lse), for the group's columns (zero past Cg
+        // and on rows past n), written as BF16 in the MN-major 128-byte-swizzled
+        // boxes of pass B: 16-byte chunk j (8 columns) of row r of box b at chunk
+        // j ^ (r % 8).  Each column's chain and class come from s_cm, so the 16
+        // columns of a block are independent.  R is rounded to BF16, whose
+        // precision (2^-9) the fast exponential's error (a few ulp of FP32) is far below.
         unsigned char* rb = A.rout + (size_t(t) * A.ngroups + g) * A.NB * kBoxBytes;
         for (int c0 = 16 * hf; c0 < A.NB * kBox; c0 += 16 * kEpiHalves) {
-          float v[16];
-          if (c0 < Cg) {
-            tmem_ld16(acc + uint32_t(c0), v);
-            if (head)
-#pragma unroll
-              for (int e = 0; e < 16; ++e) v[e] += hpi[size_t(c0 + e) * kRows];
-          }
-          int c = c0 / Km1, k = c0 - c * Km1;
-          float mc = 0.f, inv = 0.f;
-          if (c < nch) {
-            mc = s_m[c * kRows + r];
-            inv = 1.f / s_s[c * kRows + r];
-          }
           uint32_t w[8];
+          if (c0 < Cg) {
+            float v[16];
+            tmem_ld16(acc + uint32_t(c0), v);
 #pragma unroll
-          for (int e = 0; e < 16; e += 2) {
-            float rv[2];
+            for (int e = 0; e < 16; e += 2) {
+              float rv[2];
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              rv[hh] = 0.f;
-              if (c0 + e + hh < Cg) {
-                if (valid) rv[hh] = (k == yv ? 1.f : 0.f) - expf(v[e + hh] - mc) * inv;
-                if (++k == Km1) {
-                  ++c;
-                  k = 0;
-                  if (c < nch) {
-                    mc = s_m[c * kRows + r];
-                    inv = 1.f / s_s[c * kRows + r];
-                  }
-                }
+              for (int hh = 0; hh < 2; ++hh) {
+                const int ck = s_cm[c0 + e + hh];
+                const float x = ((ck >> 16) == yv ? 1.f : 0.f) - __expf(v[e + hh] - s_m[(ck & 0xffff) + r]);
+                rv[hh] = valid && c0 + e + hh < Cg ? x : 0.f;
               }
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(rv[0], rv[1]);
+              w[e / 2] = *reinterpret_cast<const uint32_t*>(&b2);
             }
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(rv[0], rv[1]);
-            w[e / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) w[e] = 0u;
           }
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
@@ -595,8 +688,14 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
         }
         // This CTA's per-chain sums, in tile order: the four quarters' 32-row sums
         // in lane-quarter order.
-        if (hf == 0 && r < nch)
-          s_llc[g * gc + r] += ((s_wsum[r * 4] + s_wsum[r * 4 + 1]) + s_wsum[r * 4 + 2]) + s_wsum[r * 4 + 3];
+        if (hf == 0 && r < nch) {
+          float hi = s_wsum[r * 4].x, lo = s_wsum[r * 4].y;
+#pragma unroll
+          for (int k = 1; k < 4; ++k) add_pair(hi, lo, s_wsum[r * 4 + k].x, s_wsum[r * 4 + k].y);
+          float2 cs = s_llc[g * gc + r];
+          add_pair(cs.x, cs.y, hi, lo);
+          s_llc[g * gc + r] = cs;
+        }
         epi_bar<kEpiThreads>();   // shared state free for the next tile
       }
       // The unit's accumulators are read: the MMA issuer may start unit j + 2 in them.
@@ -609,7 +708,8 @@ __global__ void __launch_bounds__(threads_a(kFP8), 1) logits_kernel(const LogitA
     }
   }
   __syncthreads();
-  for (int c = tid; c < A.chains; c += int(blockDim.x)) A.lpart[size_t(blockIdx.x) * A.lpart_cstride + c] = s_llc[c];
+  for (int c = tid; c < A.chains; c += int(blockDim.x))
+    A.lpart[size_t(blockIdx.x) * A.lpart_cstride + c] = double(s_llc[c].x) + double(s_llc[c].y);
   if (warp == 1) {
     fence_after_sync();
     tmem_dealloc(tmem, A.tmem_cols);
@@ -812,8 +912,8 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
       for (int c0 = 0; c0 < Cg; c0 += 16) {
         float v[16];
         if (ok && T > 0) tmem_ld16(tq + uint32_t(mb * N + c0), v);
-#pragma unroll
         const float sc = A.xscale ? A.xscale[col] : 1.f;
+#pragma unroll
         for (int e = 0; e < 16; ++e)
           if (c0 + e < Cg) gp[size_t(c0 + e) * A.p_pad + col] = (ok && T > 0) ? v[e] * sc : 0.f;
       }
