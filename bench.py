@@ -361,13 +361,32 @@ def oracle_accuracy(h, X, y, spec, xdt, tdt, dev, chains_to_check):
     return out
 
 
+def _mean_z(sa, sb):
+    """|m_a - m_b| / sqrt(MCSE_a^2 + MCSE_b^2) per coordinate for draws [N, chains, coords]
+    (MCSE = sd / sqrt(ESS), ESS as in the throughput report)."""
+    from paper_1402_4089_gb300 import diagnostics
+    out = []
+    for s_ in (sa, sb):
+        flat = s_.reshape(-1, s_.shape[2])
+        out.append((flat.mean(axis=0), flat.std(axis=0) / np.sqrt(np.maximum(diagnostics.ess(s_), 1.0))))
+    return np.abs(out[0][0] - out[1][0]) / np.sqrt(out[0][1] ** 2 + out[1][1] ** 2 + 1e-300)
+
+
+def _zsum(z):
+    return {"frac_above_3": round(float(np.mean(z > 3.0)), 4), "max_z": round(float(z.max()), 2)}
+
+
 def ess_comparison(args, dev):
     """ESS/s of the FP32 single-chain CUDA-core path and of the BF16 multi-chain
     tensor-core path on the high-dimensional problem (n=1e4, p=5000, K=10), both
     from stationary chains: `ess_burn` iterations from beta = 0 (not timed), then
     `ess_iters` timed iterations whose draws are kept on the device.  ESS
     (Geyer, chains pooled) and MCSE on a seeded subset of coordinates; the two
-    posteriors' means are compared per coordinate within 3 combined MCSE."""
+    posteriors' means are compared per coordinate within 3 combined MCSE, next to
+    two controls at one precision (the BF16 chains split in two groups, the FP32
+    chain's first and second halves) that show how often the same criterion
+    fails between runs of one sampler on this problem (the chains' mixing, not the
+    precision), and the split-free R-hat of the BF16 chains."""
     import torch
     from paper_1402_4089_gb300 import diagnostics, hmc, synthetic
     X, y, _, spec = synthetic.make_workload("highdim_fp32")
@@ -377,6 +396,7 @@ def ess_comparison(args, dev):
     coords = np.sort(rng.choice((K - 1) * p, size=min(args.ess_coords, (K - 1) * p), replace=False))
     idx = torch.from_numpy(coords).to(dev)
     runs = {}
+    rhat = np.ones(1)
     for tag, xs, chains, engine in (("fp32_1chain", "f32", 1, 1), (f"bf16_{args.ess_chains}chains", "bf16", args.ess_chains, 0)):
         stream = torch.cuda.Stream(device=dev)
         h = hmc.create(X, y, K, kind, scale, x_storage=xs, max_chains=chains, engine=engine, stream=stream)
@@ -392,6 +412,16 @@ def ess_comparison(args, dev):
         sub = draws.reshape(args.ess_iters, chains, -1)[:, :, idx].double().cpu().numpy()
         del draws
         e = diagnostics.ess(sub)
+        if chains > 1:
+            h2 = chains // 2
+            ctrl = (f"{tag}: chains 0-{h2 - 1} against {h2}-{chains - 1}", _mean_z(sub[:, :h2], sub[:, h2:]))
+            n_ = sub.shape[0]
+            cm, cv = sub.mean(axis=0), sub.var(axis=0, ddof=1)
+            W, B = cv.mean(axis=0), n_ * cm.var(axis=0, ddof=1)
+            rhat = np.sqrt(((n_ - 1) / n_ * W + B / n_) / np.where(W > 0, W, 1.0))
+        else:
+            h2 = sub.shape[0] // 2
+            ctrl = (f"{tag}: first {h2} draws against the last {sub.shape[0] - h2}", _mean_z(sub[:h2], sub[h2:]))
         flat = sub.reshape(-1, sub.shape[2])
         mean, sd = flat.mean(axis=0), flat.std(axis=0)
         runs[tag] = {"x_storage": xs, "chains": chains, "engine": h.describe()["engine"], "iters": args.ess_iters,
@@ -399,12 +429,14 @@ def ess_comparison(args, dev):
                      "ess_median": round(float(np.median(e)), 2), "ess_min_per_s": round(float(e.min()) / secs, 3),
                      "ess_median_per_s": round(float(np.median(e)) / secs, 3),
                      "accept_rate": round(sum(s["accepted"] for s in st) / max(1, sum(s["iterations"] for s in st)), 4),
-                     "_m": mean, "_se": sd / np.sqrt(np.maximum(e, 1.0))}
+                     "_m": mean, "_se": sd / np.sqrt(np.maximum(e, 1.0)), "_ctrl": ctrl}
         h.close()
     a, b = list(runs.values())
     z = np.abs(a["_m"] - b["_m"]) / np.sqrt(a["_se"] ** 2 + b["_se"] ** 2 + 1e-300)
+    controls = {}
     for r in runs.values():
-        del r["_m"], r["_se"]
+        controls[r["_ctrl"][0]] = _zsum(r["_ctrl"][1])
+        del r["_m"], r["_se"], r["_ctrl"]
     tags = list(runs)
     return {"problem": "highdim_fp32: n=10000 p=5000 K=10, N(0,1) prior, L=100, eps=2e-3", "coords": int(coords.size),
             **runs,
@@ -414,7 +446,9 @@ def ess_comparison(args, dev):
             "equal_accuracy": {"criterion": "|m_a - m_b| <= 3 sqrt(MCSE_a^2 + MCSE_b^2) per coordinate; pass if at most "
                                             "1% of coordinates exceed it and none exceeds 5",
                                "frac_above_3": round(float(np.mean(z > 3.0)), 4), "max_z": round(float(z.max()), 2),
-                               "pass": bool(np.mean(z > 3.0) <= 0.01 and z.max() <= 5.0)}}
+                               "pass": bool(np.mean(z > 3.0) <= 0.01 and z.max() <= 5.0),
+                               "controls_same_precision": controls,
+                               "bf16_rhat": {"median": round(float(np.median(rhat)), 3), "max": round(float(rhat.max()), 3)}}}
 
 
 # ---------------------------------------------------------------- our arm

@@ -56,6 +56,17 @@ def test_tc2_matches_oracle(cuda, n, p, K, chains):
     _run(cuda, n, p, K, chains, seed=n + 7 * p)
 
 
+@pytest.mark.parametrize("n,p,K,chains,U", [(700, 300, 2, 40, 0), (600, 200, 33, 8, 0), (900, 250, 17, 5, 0),
+                                            (500 * 128 + 77, 300, 11, 6, 3)])
+def test_tc2_epilogue_chain_layouts(cuda, n, p, K, chains, U):
+    """Chain layouts of the softmax epilogue: one column per chain (K = 2, 40
+    chains: a chain ends at every column), 32 columns per chain (K = 33, each
+    chain over two or three 16-column blocks, 8 chains in groups), chains of
+    exactly one block (K = 17), and units split over two CTAs with 60 columns
+    (the other CTA's partial logits added to four blocks per tile)."""
+    _run(cuda, n, p, K, chains, seed=n + 13 * K, U=U)
+
+
 @pytest.mark.parametrize("U,n", [(2, 10 * 128 + 5), (3, 10 * 128 + 5), (3, 9 * 128), (4, 3 * 128 + 1)])
 def test_tc2_row_tiles_per_unit(cuda, U, n):
     """Several row tiles per first-pass unit sharing each coefficient box, with a
