@@ -931,6 +931,9 @@ __global__ void __launch_bounds__(threads_b(kFP8), 1) grad_kernel(const GradArgs
 // [group][p_pad / 64][2N rows x 128 B]: rows [0, N) the hi term bf16(v), rows
 // [N, 2N) the lo term bf16(v - hi); columns past the group's C are zero.  With
 // FP8 X the column scales are folded in: X B = X_q (diag(s) B).
+// One thread per (row k, 8 consecutive columns): two 16-byte loads, one
+// 16-byte chunk of each term stored (8 columns of a 128-byte box row are one
+// swizzled chunk).
 __global__ void beta_boxes_kernel(const float* beta, const float* scales, unsigned char* out, int32_t Km1, int32_t gc,
                                   int32_t chains, int32_t N, int32_t p_pad) {
   const int g = blockIdx.y;
@@ -938,19 +941,38 @@ __global__ void beta_boxes_kernel(const float* beta, const float* scales, unsign
   const int Cg = nch * Km1;
   const float* bg = beta + size_t(g) * gc * Km1 * p_pad;
   unsigned char* og = out + size_t(g) * (p_pad / kBox) * 2 * N * 128;
-  const int64_t total = int64_t(N) * p_pad;
+  const int p8 = p_pad / 8;
+  const int64_t total = int64_t(N) * p8;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    const int k = int(i / p_pad);
-    const int64_t col = i - int64_t(k) * p_pad;
-    const float v = (k < Cg) ? bg[size_t(k) * p_pad + col] * (scales ? scales[col] : 1.f) : 0.f;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const int k = int(i / p8);
+    const int col = 8 * int(i - int64_t(k) * p8);
+    float v[8];
+    if (k < Cg) {
+      const float4 a = *reinterpret_cast<const float4*>(bg + size_t(k) * p_pad + col);
+      const float4 c = *reinterpret_cast<const float4*>(bg + size_t(k) * p_pad + col + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
+      if (scales) {
+        const float4 s0 = *reinterpret_cast<const float4*>(scales + col);
+        const float4 s1 = *reinterpret_cast<const float4*>(scales + col + 4);
+        v[0] *= s0.x; v[1] *= s0.y; v[2] *= s0.z; v[3] *= s0.w; v[4] *= s1.x; v[5] *= s1.y; v[6] *= s1.z; v[7] *= s1.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = 0.f;
+    }
+    uint32_t wh[4], wl[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * j] - __low2float(h2), v[2 * j + 1] - __high2float(h2));
+      wh[j] = *reinterpret_cast<const uint32_t*>(&h2);
+      wl[j] = *reinterpret_cast<const uint32_t*>(&l2);
+    }
     unsigned char* box = og + size_t(col / kBox) * 2 * N * 128;
-    const int cc = int(col % kBox);
-    const uint32_t off_h = uint32_t(k) * 128u + uint32_t(((cc >> 3) ^ (k & 7)) << 4) + uint32_t((cc & 7) * 2);
-    const uint32_t off_l = uint32_t(N + k) * 128u + uint32_t(((cc >> 3) ^ ((N + k) & 7)) << 4) + uint32_t((cc & 7) * 2);
-    *reinterpret_cast<__nv_bfloat16*>(box + off_h) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(box + off_l) = lo;
+    const int chunk = (col % kBox) >> 3;
+    *reinterpret_cast<uint4*>(box + size_t(k) * 128 + ((chunk ^ (k & 7)) << 4)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4*>(box + size_t(N + k) * 128 + ((chunk ^ ((N + k) & 7)) << 4)) =
+        make_uint4(wl[0], wl[1], wl[2], wl[3]);
   }
 }
 
@@ -982,7 +1004,7 @@ cudaError_t tc2_prepare() {
 
 cudaError_t tc2_beta_boxes(const float* beta, const float* scales, void* out, int Km1, int gc, int chains, int N,
                            int p_pad, int ngroups, cudaStream_t s) {
-  const int64_t total = int64_t(N) * p_pad;
+  const int64_t total = int64_t(N) * (p_pad / 8);
   const int gx = std::max(1, int(std::min<int64_t>(1024, (total + 255) / 256)));
   tc2::beta_boxes_kernel<<<dim3(gx, ngroups), 256, 0, s>>>(beta, scales, static_cast<unsigned char*>(out), Km1, gc,
                                                             chains, N, p_pad);
