@@ -110,12 +110,46 @@ __device__ __forceinline__ ST partial_range_sum(const ST* gpi, int64_t cstride, 
   return g;
 }
 
+// The update of coefficient idx (column j of row k = e / p_pad of chain c) from
+// its split-K gradient sum g: prior derivative, gradient (also in the user
+// layout when asked), momentum and coefficient steps, and the FP64 scalar terms.
+template <typename ST>
+__device__ __forceinline__ void update_one(const UpdateArgs& A, int mode, int c, int64_t e, int j, size_t idx, ST g,
+                                           ST ce, ST eb, double& prior_s, double& kin_s) {
+  ST* beta = static_cast<ST*>(A.beta);
+  ST* eta = static_cast<ST*>(A.eta);
+  ST* grad = static_cast<ST*>(A.grad);
+  const ST bv = beta[idx];
+  g += prior_deriv(bv, A.prior_kind, A.prior_scale);
+  grad[idx] = g;
+  if (A.ugrad) {
+    ST* ug = static_cast<ST*>(A.ugrad) + size_t(c) * A.ku * A.p;
+    const int k = int(e / A.p_pad);
+    ug[size_t(k) * A.p + j] = g;
+    if (k == 0 && A.ku > A.Km1) ug[size_t(A.Km1) * A.p + j] = ST(0);   // masked row K
+  }
+  ST ev = ST(0);
+  if (mode & (UPD_ETA_HALF | UPD_ETA_FULL)) {
+    ev = eta[idx] + ce * g;
+    eta[idx] = ev;
+  }
+  if (mode & UPD_SCALARS) {
+    prior_s += prior_term(bv, A.prior_kind, A.prior_scale);
+    if (mode & UPD_ACCEPT) kin_s += double(ev) * double(ev);
+  }
+  if (mode & UPD_BETA) beta[idx] = bv + eb * ev;
+}
+
 // GRP: a group of G lanes (A.glanes, a power of two <= 32) shares each coefficient:
 // lane l of the group sums the partials [l nparts / G, (l + 1) nparts / G) in
 // order and the G range sums meet in a butterfly (every lane of the group ends
 // with the same bits: each step adds the same two values); lane 0 of the group
-// applies the update.  G = 1 is the plain in-order sum.
-template <typename ST, bool GRP>
+// applies the update.  G = 1 is the plain in-order sum.  V4 (FP32, G = 1, p_pad,
+// the slice stride and the state buffers 16-byte aligned): each thread takes four
+// consecutive coefficients of one row with 16-byte loads and stores, the same
+// arithmetic per coefficient (the gradient sums identical bit for bit); a row's
+// last four columns holding padding go through the per-coefficient path.
+template <typename ST, bool GRP, bool V4>
 __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArgs A, int mode) {
   const int c = blockIdx.y;
   const int64_t per_chain = int64_t(A.Km1) * A.p_pad;
@@ -133,34 +167,85 @@ __global__ void __launch_bounds__(kThreads) reduce_update_kernel(const UpdateArg
   const int b0 = (gl * A.nparts) >> gsh, b1 = ((gl + 1) * A.nparts) >> gsh;
   const int64_t stride = (int64_t(gridDim.x) * blockDim.x) >> gsh;
   double prior_s = 0.0, kin_s = 0.0;
-  for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> gsh; e < per_chain; e += stride) {
-    const int j = int(e % A.p_pad);
-    if (j >= A.p) continue;  // padding columns stay zero (the whole group skips)
-    const size_t idx = base + size_t(e);
-    ST g = partial_range_sum(gp + idx, A.gpart_cstride, b0, b1);
-    if (GRP) {
-      for (int o = 1; o < G; o <<= 1) g += __shfl_xor_sync(gmask, g, o);
-      if (gl != 0) continue;
+  if constexpr (V4) {
+    const int64_t n4 = per_chain / 4;
+    for (int64_t e4 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e4 < n4; e4 += int64_t(gridDim.x) * blockDim.x) {
+      const int64_t e = 4 * e4;
+      const int j = int(e % A.p_pad);
+      if (j >= A.p) continue;  // padding columns stay zero
+      const size_t idx = base + size_t(e);
+      if (j + 4 > A.p) {
+        for (int i = 0; j + i < A.p; ++i)
+          update_one<ST>(A, mode, c, e + i, j + i, idx + i, partial_range_sum(gp + idx + i, A.gpart_cstride, 0, A.nparts),
+                         ce, eb, prior_s, kin_s);
+        continue;
+      }
+      // Split-K sums of the four coefficients, slices in order, four slices in flight.
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int b = 0; b < A.nparts; b += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          v[k] = (b + k < A.nparts) ? *reinterpret_cast<const float4*>(gp + idx + size_t(b + k) * A.gpart_cstride)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (b + k < A.nparts) {
+            g.x += v[k].x;
+            g.y += v[k].y;
+            g.z += v[k].z;
+            g.w += v[k].w;
+          }
+      }
+      const float4 bv = *reinterpret_cast<const float4*>(beta + idx);
+      float4 gg;
+      gg.x = g.x + prior_deriv(bv.x, A.prior_kind, A.prior_scale);
+      gg.y = g.y + prior_deriv(bv.y, A.prior_kind, A.prior_scale);
+      gg.z = g.z + prior_deriv(bv.z, A.prior_kind, A.prior_scale);
+      gg.w = g.w + prior_deriv(bv.w, A.prior_kind, A.prior_scale);
+      *reinterpret_cast<float4*>(grad + idx) = gg;
+      if (A.ugrad) {
+        ST* ug = static_cast<ST*>(A.ugrad) + size_t(c) * A.ku * A.p;
+        const int k = int(e / A.p_pad);
+        ST* row = ug + size_t(k) * A.p + j;
+        row[0] = gg.x;
+        row[1] = gg.y;
+        row[2] = gg.z;
+        row[3] = gg.w;
+        if (k == 0 && A.ku > A.Km1)   // masked row K
+          for (int i = 0; i < 4; ++i) ug[size_t(A.Km1) * A.p + j + i] = ST(0);
+      }
+      float4 ev = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (mode & (UPD_ETA_HALF | UPD_ETA_FULL)) {
+        const float4 e0 = *reinterpret_cast<const float4*>(eta + idx);
+        ev = make_float4(e0.x + ce * gg.x, e0.y + ce * gg.y, e0.z + ce * gg.z, e0.w + ce * gg.w);
+        *reinterpret_cast<float4*>(eta + idx) = ev;
+      }
+      if (mode & UPD_SCALARS) {
+        prior_s += prior_term(bv.x, A.prior_kind, A.prior_scale);
+        prior_s += prior_term(bv.y, A.prior_kind, A.prior_scale);
+        prior_s += prior_term(bv.z, A.prior_kind, A.prior_scale);
+        prior_s += prior_term(bv.w, A.prior_kind, A.prior_scale);
+        if (mode & UPD_ACCEPT)
+          kin_s += ((double(ev.x) * double(ev.x) + double(ev.y) * double(ev.y)) + double(ev.z) * double(ev.z)) +
+                   double(ev.w) * double(ev.w);
+      }
+      if (mode & UPD_BETA)
+        *reinterpret_cast<float4*>(beta + idx) =
+            make_float4(bv.x + eb * ev.x, bv.y + eb * ev.y, bv.z + eb * ev.z, bv.w + eb * ev.w);
     }
-    const ST bv = beta[idx];
-    g += prior_deriv(bv, A.prior_kind, A.prior_scale);
-    grad[idx] = g;
-    if (A.ugrad) {
-      ST* ug = static_cast<ST*>(A.ugrad) + size_t(c) * A.ku * A.p;
-      const int k = int(e / A.p_pad);
-      ug[size_t(k) * A.p + j] = g;
-      if (k == 0 && A.ku > A.Km1) ug[size_t(A.Km1) * A.p + j] = ST(0);   // masked row K
+  } else {
+    for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> gsh; e < per_chain; e += stride) {
+      const int j = int(e % A.p_pad);
+      if (j >= A.p) continue;  // padding columns stay zero (the whole group skips)
+      const size_t idx = base + size_t(e);
+      ST g = partial_range_sum(gp + idx, A.gpart_cstride, b0, b1);
+      if (GRP) {
+        for (int o = 1; o < G; o <<= 1) g += __shfl_xor_sync(gmask, g, o);
+        if (gl != 0) continue;
+      }
+      update_one<ST>(A, mode, c, e, j, idx, g, ce, eb, prior_s, kin_s);
     }
-    ST ev = ST(0);
-    if (mode & (UPD_ETA_HALF | UPD_ETA_FULL)) {
-      ev = eta[idx] + ce * g;
-      eta[idx] = ev;
-    }
-    if (mode & UPD_SCALARS) {
-      prior_s += prior_term(bv, A.prior_kind, A.prior_scale);
-      if (mode & UPD_ACCEPT) kin_s += double(ev) * double(ev);
-    }
-    if (mode & UPD_BETA) beta[idx] = bv + eb * ev;
   }
   if (!(mode & UPD_SCALARS)) return;
   double bs[2] = {prior_s, kin_s};
@@ -429,12 +514,20 @@ int update_blocks_per_chain(int64_t per_chain) {
 cudaError_t launch_reduce_update(int st, const UpdateArgs& a, int mode, cudaStream_t s) {
   dim3 grid(a.nblk, a.chains);
   const bool grp = a.glanes > 1;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
   if (st == HMC_F64) {
-    if (grp) reduce_update_kernel<double, true><<<grid, kThreads, 0, s>>>(a, mode);
-    else reduce_update_kernel<double, false><<<grid, kThreads, 0, s>>>(a, mode);
+    if (grp) reduce_update_kernel<double, true, false><<<grid, kThreads, 0, s>>>(a, mode);
+    else reduce_update_kernel<double, false, false><<<grid, kThreads, 0, s>>>(a, mode);
+  } else if (grp) {
+    reduce_update_kernel<float, true, false><<<grid, kThreads, 0, s>>>(a, mode);
+  } else if (a.p_pad % 4 == 0 && a.gpart_cstride % 4 == 0 && al16(a.gpart) && al16(a.beta) && al16(a.eta) &&
+             al16(a.grad)) {
+    // four coefficients per thread: a quarter of the blocks (their partial
+    // slots and the last-block ticket follow gridDim.x)
+    grid.x = std::max(1, (a.nblk + 3) / 4);
+    reduce_update_kernel<float, false, true><<<grid, kThreads, 0, s>>>(a, mode);
   } else {
-    if (grp) reduce_update_kernel<float, true><<<grid, kThreads, 0, s>>>(a, mode);
-    else reduce_update_kernel<float, false><<<grid, kThreads, 0, s>>>(a, mode);
+    reduce_update_kernel<float, false, false><<<grid, kThreads, 0, s>>>(a, mode);
   }
   return cudaGetLastError();
 }
