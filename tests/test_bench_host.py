@@ -62,3 +62,32 @@ def test_reference_arm_sweep_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_mean_z_separates_equal_from_shifted_posteriors():
+    """The equal-accuracy statistic of the ESS block on AR(1) draws (known
+    autocorrelation): two runs of one stationary process stay within 3 combined
+    MCSE on nearly every coordinate, while a shift of 10 MCSE is flagged on every
+    one; chain-split and half-split controls take the same statistic."""
+    import numpy as np
+    b = _bench()
+    rng = np.random.default_rng(5)
+
+    def ar1(n, chains, m, phi=0.8):
+        x = np.zeros((n, chains, m))
+        x[0] = rng.standard_normal((chains, m))
+        e = rng.standard_normal((n, chains, m))
+        for t in range(1, n):
+            x[t] = phi * x[t - 1] + np.sqrt(1 - phi ** 2) * e[t]
+        return x
+
+    a, c = ar1(2000, 4, 3000), ar1(2000, 4, 3000)
+    z = b._mean_z(a, c)
+    s = b._zsum(z)
+    assert z.shape == (3000,) and s["frac_above_3"] <= 0.01 and s["max_z"] < 5.0
+    # the MCSE of a mean of 8000 draws with tau = (1 + phi) / (1 - phi) = 9 is about sqrt(9 / 8000)
+    shift = 10 * np.sqrt(2 * 9 / 8000)
+    assert b._zsum(b._mean_z(a, c + shift))["frac_above_3"] >= 0.99
+    # controls: two chain groups of one run, and its two halves
+    assert b._zsum(b._mean_z(a[:, :2], a[:, 2:]))["frac_above_3"] <= 0.02
+    assert b._zsum(b._mean_z(a[:1000], a[1000:]))["frac_above_3"] <= 0.02
